@@ -1,0 +1,386 @@
+"""Benchmark: Richardson-Lucy iterations per second on the large light-field
+workload (2025x2025 px sensor, Nnum 15, 51 depths, PSF 345 px; 5000 beads + 200
+filaments, y = Poisson(1000 Hv) + 10), one step = one RL iteration (forward
+projection, ratio, backprojection, update + MIP + flux, DCT-entropy metric).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl lfd|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun, one process per GPU)
+every rank reconstructs its own frame (independent replicas, weak scaling);
+the time is the maximum over ranks. ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_CFG = 2
+CROP_LENSLETS = 13      # CPU-baseline sample: 195x195 px crop of the frame
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lfd", choices=["lfd", "reference"])
+    p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
+    p.add_argument("--config", type=int, default=WORKLOAD_CFG)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--skip-fp32-ref", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ distributed --
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x: float, world: int, device=None) -> float:
+    """Maximum of a float over ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": smax or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ inputs --
+def make_inputs(cfg: int):
+    """PSF, ground truth and the seeded parameters of the workload."""
+    from paper_2208_11422_gb300 import synth
+    g = synth.CONFIGS[cfg]
+    psf = synth.make_psf(cfg)
+    vt = synth.ground_truth(cfg)
+    return g, psf, vt
+
+
+def algorithmic_flops_per_projection(g) -> float:
+    # 2 flops per multiply-add, H*W*Nz*P^2 multiply-adds
+    return 2.0 * g.H * g.W * g.nz * g.P * g.P
+
+
+# ------------------------------------------------------------- CPU baseline --
+def cpu_baseline_sample(cfg: int, psf=None):
+    """One oracle RL iteration on a 195x195 px crop of the workload (13x13
+    lenslets, same Nnum, depths and PSF), scaled to the full frame by the exact
+    ratio of multiply-adds. Returns (iterations/s, seconds, sample text, cores)."""
+    import oracle
+    from oracle import rl as orl
+    from paper_2208_11422_gb300 import synth
+    g = synth.CONFIGS[cfg]
+    Lc = min(CROP_LENSLETS, g.lenslets)
+    Hc = Wc = Lc * g.nnum
+    psf = (synth.make_psf(cfg) if psf is None else psf).astype(np.float64)
+    vt = synth.beads(100 + cfg, g.nz, Hc, Wc, max(1, g.beads * Lc * Lc // (g.lenslets ** 2)),
+                     g.bead_radius, g.amp_lo)
+    y = synth.poisson_data(oracle.forward(psf, g.nnum, vt), g.scale, g.background, 200 + cfg)
+    ht1 = orl.ht_one(psf, g.nnum, Hc, Wc)
+    v = np.ones((g.nz, Hc, Wc))
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    vn, _ = orl.rl_step(psf, g.nnum, y, v, ht1)
+    from oracle.metric import dct_entropy, mip_z, region_size
+    XS, YS = region_size(g.nnum, Hc, Wc)
+    dct_entropy(mip_z(vn), XS, YS)
+    dt = time.perf_counter() - t0
+    ratio = oracle.macs_per_projection(g.P, g.nz, g.H, g.W) / oracle.macs_per_projection(g.P, g.nz, Hc, Wc)
+    it_s = 1.0 / (dt * ratio)
+    sample = ("one FP64 RL iteration (forward, ratio, backward, update, metric) on a %dx%d px crop "
+              "(%dx%d lenslets, Nz %d, PSF %d px) took %.2f s; scaled to the full %dx%d frame by the "
+              "exact multiply-add ratio %.1f" % (Hc, Wc, Lc, Lc, g.nz, g.P, dt, g.W, g.H, ratio))
+    return it_s, dt, sample, cores
+
+
+# ---------------------------------------------------------------- GPU arm --
+def run_lfd(args, rank, world, local):
+    import torch
+    from paper_2208_11422_gb300 import build, lfd, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    lfd.load()
+    prec = args.precision or "fp32"
+    steps = args.steps if args.steps is not None else 3
+    warm = max(3, args.warmup)
+    g, psf, vt = make_inputs(args.config)
+    psf_d = torch.from_numpy(psf).to(dev)
+
+    # data: y = Poisson(scale * H v_true) + background, H v_true by the FP32 path
+    ctx32 = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, lfd.lfd_default_options(precision="fp32"))
+    vt_d = torch.from_numpy(vt.astype(np.float32)).to(dev)
+    hv = torch.empty((g.H, g.W), device=dev)
+    lfd.lfd_forward(ctx32, vt_d, hv)
+    torch.cuda.synchronize()
+    y = synth.poisson_data(hv.cpu().numpy(), g.scale, g.background, 200 + args.config)
+    del vt_d, hv
+    y_d = torch.from_numpy(y).to(dev)
+
+    if prec == "fp32":
+        ctx = ctx32
+    else:
+        ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, lfd.lfd_default_options(precision=prec))
+    v = torch.ones((g.nz, g.H, g.W), device=dev)
+
+    # warm-up (untimed)
+    lfd.lfd_rl_iterate(ctx, y_d, v, warm)
+    v.fill_(1.0)
+    torch.cuda.synchronize()
+
+    # device-resident timed region: one call of `steps` iterations
+    lfd.lfd_set_profiling(ctx, True)
+    launches0 = lfd.lfd_launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        done, pred, ent, flux = lfd.lfd_rl_iterate(ctx, y_d, v, steps, False, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+    launches = lfd.lfd_launch_count() - launches0
+    secs = e0.elapsed_time(e1) / 1e3
+    stage = lfd.lfd_stage_times(ctx)
+    lfd.lfd_set_profiling(ctx, False)
+    tmax = dist_max(secs, world, dev)
+    value = aggregate(steps, world, tmax)
+
+    # end to end through the C ABI with pinned host buffers, one iteration per call
+    e2e = None
+    if not args.no_e2e:
+        y_h = torch.from_numpy(y).pin_memory()
+        v_h = torch.ones((g.nz, g.H, g.W)).pin_memory()
+        lfd.lfd_rl_iterate(ctx, y_h, v_h, 1)   # warm the staging buffers
+        v_h.fill_(1.0)
+        dist_barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            lfd.lfd_rl_iterate(ctx, y_h, v_h, 1)
+        t_e2e = time.perf_counter() - t0
+        dist_barrier(world)
+        t_e2e = dist_max(t_e2e, world, dev)
+        e2e = {"value": aggregate(steps, world, t_e2e), "unit": "RL iterations/s",
+               "h2d_bytes_per_step": int(y_h.numel() * 4 + v_h.numel() * 4),
+               "d2h_bytes_per_step": int(v_h.numel() * 4)}
+
+    # the plain FP32 GPU path on the same GPU (reported beside the tensor-core path)
+    fp32_ref = None
+    if prec != "fp32" and not args.skip_fp32_ref:
+        v32 = torch.ones((g.nz, g.H, g.W), device=dev)
+        lfd.lfd_rl_iterate(ctx32, y_d, v32, 1)
+        v32.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lfd.lfd_rl_iterate(ctx32, y_d, v32, 2, False, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp32_ref = {"value": 2.0 / (a.elapsed_time(b) / 1e3), "unit": "RL iterations/s",
+                    "rel_l2_vs_this_path_after_%d_iterations" % 2: None}
+
+    peaks, peak_src = measured_peaks()
+    fl = algorithmic_flops_per_projection(g)
+    fwd_ms, bwd_ms = stage[0], stage[2]
+    dom_ms = max(fwd_ms, bwd_ms)
+    dom = "forward projection" if fwd_ms >= bwd_ms else "backprojection"
+    if prec == "fp32":
+        smax = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * smax * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max clock
+        roof = {"bound": "alu", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x %g MHz" % smax}
+    else:
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": "bf16_tflops_sustained (%s)" % peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["stage_ms"] = {"forward": stage[0], "ratio": stage[1], "backward": stage[2],
+                        "update": stage[3], "metric": stage[4]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it_s, dt, sample, cores = cpu_baseline_sample(args.config, psf)
+        cpu = {"value": it_s, "unit": "RL iterations/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    clocks = clk.summary()
+    out = {
+        "metric": "RL iterations/s, 2025x2025 px x 51 depths, PSF 345 px (Nnum 15)",
+        "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": tmax * 1e3 / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
+        "data": "synthetic (seeded beads + filaments, Poisson noise)",
+        "config": {"workload": synth.CONFIGS[args.config].name, "H": g.H, "W": g.W,
+                   "Nnum": g.nnum, "Nz": g.nz, "P": g.P, "precision": prec,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (volume %.2f GB)" % (g.nz * g.H * g.W * 4 / 1e9)},
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "roofline": roof, "cpu_baseline": cpu, "fp32_gpu": fp32_ref,
+        "entropy": ent, "predicted_iteration": pred,
+    }
+    lfd.lfd_destroy(ctx)
+    if ctx is not ctx32:
+        lfd.lfd_destroy(ctx32)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    if rank != 0:
+        return
+    steps = args.steps if args.steps is not None else 1
+    warm = args.warmup
+    vals = []
+    sample = cores = None
+    for _ in range(steps):
+        it_s, dt, sample, cores = cpu_baseline_sample(args.config)
+        vals.append(dt)
+    from paper_2208_11422_gb300 import synth
+    import oracle
+    g = synth.CONFIGS[args.config]
+    Hc = CROP_LENSLETS * g.nnum
+    ratio = oracle.macs_per_projection(g.P, g.nz, g.H, g.W) / oracle.macs_per_projection(g.P, g.nz, Hc, Hc)
+    value = 1.0 / (statistics.mean(vals) * ratio)
+    out = {
+        "impl": "reference",
+        "metric": "RL iterations/s, 2025x2025 px x 51 depths, PSF 345 px (Nnum 15)",
+        "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps, "warmup": warm,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": g.name, "H": g.H, "W": g.W, "Nnum": g.nnum, "Nz": g.nz, "P": g.P},
+        "cpu_baseline": {"value": value, "unit": "RL iterations/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "RL iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_lfd(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

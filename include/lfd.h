@@ -1,0 +1,180 @@
+/*
+ * lfd.h - C ABI of the GB300 light-field Richardson-Lucy deconvolution library
+ * (liblfd.so, CUDA for sm_103a).
+ *
+ * The library runs the data-parallel hot path of light-field microscopy
+ * deconvolution that AutoDeconJ (Su et al., arXiv 2208.11422) accelerates:
+ * Richardson-Lucy (RL) iterations on a light-field image with a depth- and
+ * phase-dependent PSF (Sections 1 and 2.1), with the DCT-entropy image-quality
+ * metric of Section 2.2 (Eqs. 1-12) evaluated on every iterate to predict the
+ * iteration count. Intermediates stay on the GPU; only results come back
+ * (Section 2.1, Fig. 1).
+ *
+ * Model. Volume v[z][i'][j'] (z < Nz, i' < H, j' < W), sensor image y[i][j],
+ * PSF K[z][aa][bb][mi][mj] (aa, bb < Nnum lenslet phase, mi, mj < P, P odd,
+ * centre c = (P-1)/2). The paper does not write the model out; it is the
+ * Prevedel et al. 2014 model the paper builds on:
+ *   forward   (Hv)[i][j]        = sum_{z,i',j'} v[z][i'][j'] K[z][i'%N][j'%N][i-i'+c][j-j'+c]
+ *   backward  (H^T r)[z][i'][j'] = sum_{i,j}    r[i][j]     K[z][i'%N][j'%N][i-i'+c][j-j'+c]
+ * (terms outside the PSF window or the sensor are zero). One RL iteration:
+ *   r = y / (Hv + eps);  v <- max(0, v * (H^T r) / (H^T 1))  (0 where H^T 1 = 0).
+ *
+ * Conventions
+ *   - All arrays are dense, row-major, FP32. Volumes are [Nz][H][W] (stack
+ *     order), images [H][W], the PSF [Nz][Nnum][Nnum][P][P].
+ *   - Pointers may be device or host memory; the library tells them apart with
+ *     cudaPointerGetAttributes. Host buffers are staged through device memory
+ *     owned by the context (pinned host memory makes those copies fast).
+ *   - The caller owns every buffer it passes; the context owns its internal
+ *     buffers and frees them in lfd_destroy.
+ *   - Calls are ordered on the CUDA stream passed in (NULL = legacy default
+ *     stream). lfd_forward / lfd_backward return after enqueueing when given
+ *     device pointers; the others synchronise the stream before returning.
+ *     Launch and argument errors are returned at once; asynchronous device
+ *     faults surface at the next call that synchronises.
+ *   - No function aborts the process. On error the status is returned and
+ *     lfd_last_error(ctx) gives a message.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef LFD_H
+#define LFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lfd_ctx lfd_ctx;
+
+typedef enum {
+    LFD_OK = 0,
+    LFD_EINVAL = 1,       /* invalid argument or shape                         */
+    LFD_ENOMEM = 2,       /* a device or host allocation failed                 */
+    LFD_ECUDA = 3,        /* a CUDA runtime/driver call failed                  */
+    LFD_ENOTREADY = 4,    /* reserved for asynchronous request handles          */
+    LFD_ETIMEDOUT = 5,    /* a bounded device wait gave up (kernel error flag)  */
+    LFD_EBUSY = 6,        /* reserved                                           */
+    LFD_EINTERNAL = 7,    /* internal consistency check failed                  */
+    LFD_EUNSUPPORTED = 8  /* option not available for this shape / device       */
+} lfd_status;
+
+/* Arithmetic of the two projections (the ratio, update and metric are FP32 with
+ * FP64 reductions in every mode). */
+typedef enum {
+    LFD_FP32 = 0,   /* FP32 inputs and FP32 FMA accumulation on the CUDA cores   */
+    LFD_TF32 = 1,   /* reserved                                                  */
+    LFD_BF16 = 2,   /* BF16 inputs on tcgen05 tensor cores, FP32 accumulation    */
+    LFD_BF16X3 = 3  /* split BF16: x = hi + lo, three products hi*hi + hi*lo +
+                       lo*hi per term, FP32 accumulation (tensor cores)          */
+} lfd_precision;
+
+typedef struct {
+    int precision;        /* lfd_precision                                          */
+    float eps;            /* ratio guard: r = y / (Hv + eps); default 1e-6          */
+    /* optics for the metric's region size (Eqs. 7, 9-11); defaults
+       d_ML = 150 um, Q = 40, NA = 0.95, lambda = 0.525 um                          */
+    double dML_um, Q, NA, lambda_um;
+    int XS, YS;           /* region width / height; > 0 overrides the optics        */
+    int l2_over_region;   /* 1: L2 norm of Eq. 12 over the region S (default);
+                             0: over the whole DCT (= 2-norm of the MIP)            */
+} lfd_options;
+
+/* Fills *opt with the defaults listed above. */
+void lfd_default_options(lfd_options* opt);
+
+/* Creates a context for one PSF and one sensor shape (Fig. 1: the PSF is moved
+ * to the GPU once and reused by every reconstruction).
+ *   psf     [Nz][Nnum][Nnum][P][P] FP32, host or device; copied, not kept.
+ *   P       PSF window width in pixels: odd, a multiple of Nnum.
+ *   Nnum    pixels per lenslet (odd, >= 1).  Nz >= 1 depths.
+ *   H, W    sensor height / width in pixels, each a positive multiple of Nnum.
+ *   opt     NULL for defaults.
+ * Work done here: the PSF is repacked into the polyphase layout the projection
+ * kernels read, H^T 1 is computed, and the metric's cosine tables are built.
+ * Errors: LFD_EINVAL (shape rules above, NULL out), LFD_ENOMEM, LFD_ECUDA,
+ * LFD_EUNSUPPORTED (precision needs tensor cores the device lacks).
+ * On error *out is NULL. */
+lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                      const lfd_options* opt, void* cuda_stream, lfd_ctx** out);
+
+/* Forward projection y_out = H v (model above).
+ *   v      [Nz][H][W], y_out [H][W]; host or device. */
+lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_stream);
+
+/* Backprojection v_out = H^T r (model above): the flipped-PSF sum of every
+ * phase, sub-sampled into each depth.
+ *   r      [H][W], v_out [Nz][H][W]; host or device. */
+lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_stream);
+
+/* Runs up to n RL iterations (model above) starting from the volume in v and
+ * writes the result back into v. After each iteration the DCT entropy of the
+ * z-maximum projection is computed (Section 2.2, Eqs. 1-12).
+ *   y                 [H][W] light-field image (host or device)
+ *   v                 [Nz][H][W] in: v^0 (e.g. all ones), out: result
+ *   n                 iterations to run (>= 1)
+ *   stop_at_predicted 0: run n iterations, v = v^n.
+ *                     1: stop once the entropy decreases (E_{k+1} < E_k) and
+ *                        return v = v^k, the iterate with the higher entropy
+ *                        (Section 2.2: stop when the entropy starts to fall).
+ *   iters_done        (may be NULL) iterations whose result is in v
+ *   predicted         (may be NULL) predicted iteration n*: first k with
+ *                     E_{k+1} < E_k, else the first argmax of E_1..E_ran
+ *   entropy_hist      (may be NULL) host array of n doubles, E_1..E_ran
+ *                     (entries past the last iteration run are set to NaN)
+ *   flux_hist         (may be NULL) host array of n doubles:
+ *                     sum(H^T1 * v^k), which equals sum(y * Hv/(Hv+eps))
+ * Synchronises the stream. */
+lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n,
+                          int stop_at_predicted, int* iters_done, int* predicted,
+                          double* entropy_hist, double* flux_hist, void* cuda_stream);
+
+/* DCT entropy (Eq. 12 over the region of Eq. 6) of the z-maximum projection of
+ * the volume v [Nz][H][W] (host or device); result in *entropy (host).
+ * Synchronises the stream. */
+lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda_stream);
+
+/* Frees the context and everything it owns. NULL is a no-op. */
+void lfd_destroy(lfd_ctx* ctx);
+
+/* Message of the last error on ctx ("" if none); static text if ctx is NULL. */
+const char* lfd_last_error(const lfd_ctx* ctx);
+
+/* Name of a status code. */
+const char* lfd_status_string(lfd_status s);
+
+/* Host-only helpers (no GPU needed). */
+
+/* Region size of Eqs. 7, 9, 10, 11: P_u = d_ML / (Q Nnum),
+ * d_psf = 1.22 lambda Nnum / NA, X_S = floor(P_u W / d_psf),
+ * Y_S = floor(P_u H / d_psf), each clamped to [min(2, size), size].
+ * Errors: LFD_EINVAL for non-positive sizes or optics, NULL outputs. */
+lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q,
+                           double NA, double lambda_um, int* XS, int* YS);
+
+/* Predicted iteration (1-based) from an entropy history E[0..n-1] = E_1..E_n:
+ * the first k with E_{k+1} < E_k, else the first argmax; 0 when n < 1. */
+int lfd_predict_stop(const double* E, int n);
+
+/* Shape of the context's internal problem, for inspection and tests.
+ * Each pointer may be NULL. taps = k + 2 where k = P / Nnum. */
+lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps,
+                            int* precision, int64_t* device_bytes);
+
+/* Number of kernels the library has launched in this process (all contexts). */
+uint64_t lfd_launch_count(void);
+
+/* Per-stage device time of lfd_rl_iterate iterations, in milliseconds, measured
+ * with CUDA events recorded on the call's stream around each stage:
+ * [0] forward projection, [1] split reduction + ratio, [2] backprojection,
+ * [3] update + MIP + flux, [4] metric. lfd_set_profiling(ctx, 1) turns the
+ * events on and resets the averages; lfd_stage_times returns the mean over
+ * every iteration run since then (zeros if none). */
+lfd_status lfd_set_profiling(lfd_ctx* ctx, int on);
+lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms5);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFD_H */

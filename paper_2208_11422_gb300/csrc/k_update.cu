@@ -1,0 +1,218 @@
+// Fused RL update (multiplicative step, clamp, z-MIP, FP64 flux) and the
+// DCT-entropy metric of Section 2.2.
+#include "lfd_internal.h"
+
+namespace lfd {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// block-wide sum in a fixed order (deterministic); all threads get the result
+__device__ double block_sum(double x, double* red) {
+    x = warp_sum(x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+// One block per lenslet (Iy, Ix); thread t < S walks the depths of phase t.
+//   v_new = v * x * inv   (x = H^T r, inv = 1 / H^T 1, 0 where H^T 1 = 0)
+//   v_new = max(0, v_new) with NaN -> 0
+// and, on the fly, the z-maximum of v_new for pixel (Iy*N + ty, Ix*N + tx)
+// and this lenslet's share of the flux sum(H^T1 * v_new) = sum(v * x) taken
+// where H^T 1 > 0, accumulated in FP64.
+__global__ void __launch_bounds__(256) k_update(
+    const float* __restrict__ vin, float* __restrict__ vout, __nv_bfloat16* __restrict__ hi,
+    __nv_bfloat16* __restrict__ lo, const float* __restrict__ parts, int nsplit,
+    const float* __restrict__ inv, Geo g, float* __restrict__ mip, double* __restrict__ flux_part) {
+    __shared__ double red[32];
+    const int l = blockIdx.x;
+    const int Iy = l / g.Lx, Ix = l % g.Lx;
+    const int64_t m = (int64_t)Iy * g.Lp + Ix;
+    const int64_t grow = (g.m_base + m) * g.Cpad;
+    const int64_t orow = m * g.Cpad;
+    const int64_t pstride = g.M_pad * g.Cpad;
+    double flux = 0.0;
+    for (int t = threadIdx.x; t < g.S; t += blockDim.x) {
+        float mx = 0.f;
+        for (int z = 0; z < g.Nz; ++z) {
+            const int c = z * g.S + t;
+            float x = parts[orow + c];
+            for (int q = 1; q < nsplit; ++q) x += parts[orow + c + q * pstride];
+            const float iv = inv[orow + c];
+            const float vo = vin[grow + c];
+            float vn = 0.f;
+            if (iv > 0.f) {
+                const float vx = vo * x;
+                vn = vx * iv;
+                flux += (double)vx;
+            }
+            vn = vn > 0.f ? vn : 0.f;  // clamp; a NaN compares false and becomes 0
+            vout[grow + c] = vn;
+            if (hi) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(vn);
+                hi[grow + c] = h;
+                if (lo) lo[grow + c] = __float2bfloat16_rn(vn - __bfloat162float(h));
+            }
+            mx = fmaxf(mx, vn);
+        }
+        const int ty = t / g.N, tx = t % g.N;
+        mip[((int64_t)Iy * g.N + ty) * g.W + (int64_t)Ix * g.N + tx] = mx;
+    }
+    const double f = block_sum(flux, red);
+    if (threadIdx.x == 0) flux_part[l] = f;
+}
+
+// z-maximum projection straight from a padded channels-last volume
+__global__ void k_mip(const float* __restrict__ vp, Geo g, float* __restrict__ mip) {
+    const int l = blockIdx.x;
+    const int Iy = l / g.Lx, Ix = l % g.Lx;
+    const int64_t grow = (g.m_base + (int64_t)Iy * g.Lp + Ix) * g.Cpad;
+    for (int t = threadIdx.x; t < g.S; t += blockDim.x) {
+        float mx = 0.f;
+        for (int z = 0; z < g.Nz; ++z) mx = fmaxf(mx, vp[grow + z * g.S + t]);
+        const int ty = t / g.N, tx = t % g.N;
+        mip[((int64_t)Iy * g.N + ty) * g.W + (int64_t)Ix * g.N + tx] = mx;
+    }
+}
+
+// z-maximum projection of a volume in stack order [Nz][H][W]
+__global__ void k_mip_stack(const float* __restrict__ v, int Nz, int64_t HW, float* __restrict__ mip) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < HW;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float mx = 0.f;
+        for (int z = 0; z < Nz; ++z) mx = fmaxf(mx, v[z * HW + e]);
+        mip[e] = mx;
+    }
+}
+
+// G[y][u] = sum_x f[y][x] * C_u(x; W) for u < XS (Eq. 1 along the rows, with
+// the basis of Eqs. 2-4 tabulated in cosW[u][x]); rowE2[y] = sum_x f[y][x]^2.
+__global__ void k_dct_rows(const float* __restrict__ f, const double* __restrict__ cosW, int W,
+                           int XS, double* __restrict__ G, double* __restrict__ rowE2) {
+    extern __shared__ float row[];
+    __shared__ double red[32];
+    const int y = blockIdx.x;
+    double e2 = 0.0;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const float a = f[(int64_t)y * W + x];
+        row[x] = a;
+        e2 += (double)a * (double)a;
+    }
+    const double tot = block_sum(e2, red);  // contains the barrier that publishes row[]
+    if (threadIdx.x == 0) rowE2[y] = tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int u = w; u < XS; u += nw) {
+        double s = 0.0;
+        const double* cb = cosW + (int64_t)u * W;
+        for (int x = lane; x < W; x += 32) s += (double)row[x] * cb[x];
+        s = warp_sum(s);
+        if (lane == 0) G[(int64_t)y * XS + u] = s;
+    }
+}
+
+// F(u, v) = sum_y C_v(y; H) * G[y][u] for (u, v) in the triangle
+// u*YS + v*XS < XS*YS (Eq. 6); one block per column u.
+__global__ void k_dct_cols(const double* __restrict__ G, const double* __restrict__ cosH, int H,
+                           int XS, int YS, double* __restrict__ coef) {
+    const int u = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int v = w; v < YS; v += nw) {
+        double s = 0.0;
+        const bool in = (int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS;
+        if (in) {
+            const double* cb = cosH + (int64_t)v * H;
+            for (int y = lane; y < H; y += 32) s += cb[y] * G[(int64_t)y * XS + u];
+            s = warp_sum(s);
+        }
+        if (lane == 0) coef[(int64_t)v * XS + u] = in ? s : 0.0;
+    }
+}
+
+// E = -(1/G_S) sum_S |p| log2 |p|, p = F / ||F||_2 (Eqs. 5, 6, 12), and the
+// flux total; single block, fixed reduction order.
+__global__ void k_entropy(const double* __restrict__ coef, const double* __restrict__ rowE2, int H,
+                          int XS, int YS, int l2_over_region, const double* __restrict__ flux_part,
+                          int nflux, double* __restrict__ out_entropy, double* __restrict__ out_flux) {
+    __shared__ double red[32];
+    const int n = XS * YS;
+    double a = 0.0;
+    if (l2_over_region) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) a += coef[i] * coef[i];
+    } else {
+        for (int i = threadIdx.x; i < H; i += blockDim.x) a += rowE2[i];
+    }
+    const double norm = sqrt(block_sum(a, red));
+    double e = 0.0;
+    if (norm > 0.0) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int v = i / XS, u = i % XS;
+            if ((int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS) {
+                const double p = fabs(coef[i]) / norm;
+                if (p > 0.0) e += p * log2(p);
+            }
+        }
+    }
+    const double ent = block_sum(e, red);
+    double fl = 0.0;
+    for (int i = threadIdx.x; i < nflux; i += blockDim.x) fl += flux_part[i];
+    const double flux = block_sum(fl, red);
+    if (threadIdx.x == 0) {
+        out_entropy[0] = norm > 0.0 ? -ent / (0.5 * (double)XS * (double)YS) : 0.0;
+        if (out_flux) out_flux[0] = flux;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_update(const float* vin, float* vout, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          const float* parts, int nsplit, const float* inv, const Geo& g,
+                          float* mip, double* flux_part, cudaStream_t st) {
+    const int threads = g.S >= 256 ? 256 : ((g.S + 31) / 32) * 32;
+    k_update<<<g.Ly * g.Lx, threads, 0, st>>>(vin, vout, hi, lo, parts, nsplit, inv, g, mip,
+                                              flux_part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mip(const float* vp32, const Geo& g, float* mip, cudaStream_t st) {
+    const int threads = g.S >= 256 ? 256 : ((g.S + 31) / 32) * 32;
+    k_mip<<<g.Ly * g.Lx, threads, 0, st>>>(vp32, g, mip);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mip_stack(const float* v, int Nz, int64_t HW, float* mip, cudaStream_t st) {
+    int64_t b = (HW + 255) / 256;
+    k_mip_stack<<<(unsigned)(b < 4864 ? b : 4864), 256, 0, st>>>(v, Nz, HW, mip);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH, int H, int W,
+                          int XS, int YS, int l2_over_region, double* G, double* rowE2,
+                          double* coef, const double* flux_part, int nflux, double* out_entropy,
+                          double* out_flux, cudaStream_t st) {
+    const size_t smem = (size_t)W * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_dct_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_dct_rows<<<H, 256, smem, st>>>(mip, cosW, W, XS, G, rowE2);
+    k_dct_cols<<<XS, 256, 0, st>>>(G, cosH, H, XS, YS, coef);
+    k_entropy<<<1, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
+                                 out_entropy, out_flux);
+    count_launch(3);
+    return cudaGetLastError();
+}
+
+}  // namespace lfd

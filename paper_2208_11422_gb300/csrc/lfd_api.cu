@@ -1,0 +1,611 @@
+// C ABI of liblfd (include/lfd.h): context set-up, projections, the RL loop
+// and the metric, all enqueued on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lfd_internal.h"
+#include "tc_gemm.h"
+
+using namespace lfd;
+
+#define LFD_CK(call)                                                                \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? LFD_ENOMEM : LFD_ECUDA;        \
+        }                                                                           \
+    } while (0)
+
+namespace lfd {
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why) {
+    auto fail = [&](const char* m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (N < 1 || (N % 2) == 0) return fail("Nnum must be odd and >= 1");
+    if (Nz < 1) return fail("Nz must be >= 1");
+    if (P < 1 || (P % 2) == 0) return fail("P must be odd and >= 1");
+    if (P % N != 0) return fail("P must be a multiple of Nnum");
+    if (H < N || W < N || H % N != 0 || W % N != 0)
+        return fail("H and W must be positive multiples of Nnum");
+    if ((int64_t)N * N * Nz > (1LL << 24)) return fail("Nnum^2 * Nz too large");
+    Geo r{};
+    r.N = N;
+    r.Nz = Nz;
+    r.P = P;
+    r.H = H;
+    r.W = W;
+    r.Ly = H / N;
+    r.Lx = W / N;
+    r.k = P / N;
+    r.h = (r.k + 1) / 2;
+    r.T = 2 * r.h + 1;
+    r.S = N * N;
+    r.Spad = (int)round_up(r.S, 16);
+    r.C = Nz * r.S;
+    r.Cpad = (int)round_up(r.C, 64);
+    r.Lp = r.Lx + r.h;
+    r.m_base = r.h + (int64_t)r.h * r.Lp;
+    r.M_out = (int64_t)r.Ly * r.Lp;
+    r.M_pad = round_up(r.M_out, 256);
+    r.rows = r.m_base + r.M_pad + (int64_t)r.h * r.Lp + r.h;
+    *g = r;
+    return true;
+}
+
+}  // namespace lfd
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+lfd_status dalloc(lfd_ctx* ctx, T** p, int64_t count, bool zero) {
+    const size_t bytes = (size_t)count * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        ctx->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? LFD_ENOMEM : LFD_ECUDA;
+    }
+    ctx->device_bytes += (int64_t)bytes;
+    if (zero) {
+        e = cudaMemset(*p, 0, bytes);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cudaMemset: ") + cudaGetErrorString(e);
+            return LFD_ECUDA;
+        }
+    }
+    return LFD_OK;
+}
+
+#define LFD_TRY(x)                       \
+    do {                                 \
+        lfd_status s_ = (x);             \
+        if (s_ != LFD_OK) return s_;     \
+    } while (0)
+
+bool uses_tc(const lfd_ctx* ctx) {
+    return ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3;
+}
+bool uses_lo(const lfd_ctx* ctx) { return ctx->opt.precision == LFD_BF16X3; }
+
+// forward projection of Vp32[buf] (and its BF16 copies) into ctx->Fwd
+lfd_status run_forward(lfd_ctx* ctx, int buf, cudaStream_t st) {
+    const Geo& g = ctx->g;
+    if (uses_tc(ctx)) {
+        cudaError_t e = tc_forward(ctx, buf, st);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("tc_forward: ") + cudaGetErrorString(e);
+            return LFD_ECUDA;
+        }
+        return LFD_OK;
+    }
+    LFD_CK(launch_simt_forward(ctx->Vp32[buf], ctx->W32, g, ctx->fwd_splits, ctx->Fwd, st));
+    return LFD_OK;
+}
+
+// backprojection of Rp32 (and its BF16 copies) into ctx->Bwd
+lfd_status run_backward(lfd_ctx* ctx, cudaStream_t st, bool force_fp32 = false) {
+    const Geo& g = ctx->g;
+    if (uses_tc(ctx) && !force_fp32) {
+        cudaError_t e = tc_backward(ctx, st);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("tc_backward: ") + cudaGetErrorString(e);
+            return LFD_ECUDA;
+        }
+        return LFD_OK;
+    }
+    LFD_CK(launch_simt_backward(ctx->Rp32, ctx->W32, g, ctx->bwd_splits, ctx->Bwd, st));
+    return LFD_OK;
+}
+
+int fwd_parts(const lfd_ctx* ctx) { return uses_tc(ctx) ? tc_forward_parts(ctx) : ctx->fwd_splits; }
+int bwd_parts(const lfd_ctx* ctx, bool force_fp32 = false) {
+    return (uses_tc(ctx) && !force_fp32) ? tc_backward_parts(ctx) : ctx->bwd_splits;
+}
+
+lfd_status ensure_stage(lfd_ctx* ctx, bool vol) {
+    const Geo& g = ctx->g;
+    if (vol && !ctx->stage_vol) return dalloc(ctx, &ctx->stage_vol, (int64_t)g.Nz * g.H * g.W, false);
+    if (!vol && !ctx->stage_img) return dalloc(ctx, &ctx->stage_img, (int64_t)g.H * g.W, false);
+    return LFD_OK;
+}
+
+void free_all(lfd_ctx* ctx) {
+    void* ptrs[] = {ctx->W32, ctx->Wb[0], ctx->Wb[1], ctx->Vp32[0], ctx->Vp32[1], ctx->Vpb[0],
+                    ctx->Vpb[1], ctx->Rp32, ctx->Rpb[0], ctx->Rpb[1], ctx->Fwd, ctx->Bwd,
+                    ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
+                    ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    for (auto& e : ctx->prof.ev)
+        if (e) cudaEventDestroy(e);
+    ctx->prof.ev.clear();
+    tc_destroy(ctx);
+}
+
+std::vector<double> dct_table(int n, int Z) {
+    // C_k(x; Z) = c(k, Z) cos((2x+1) pi k / (2Z)), c = sqrt(1/Z) for k = 0, sqrt(2/Z) otherwise
+    std::vector<double> t((size_t)n * Z);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        const double ck = k == 0 ? std::sqrt(1.0 / Z) : std::sqrt(2.0 / Z);
+        for (int x = 0; x < Z; ++x) t[(size_t)k * Z + x] = ck * std::cos((2.0 * x + 1.0) * pi * k / (2.0 * Z));
+    }
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lfd_default_options(lfd_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = LFD_FP32;
+    opt->eps = 1e-6f;
+    opt->dML_um = 150.0;
+    opt->Q = 40.0;
+    opt->NA = 0.95;
+    opt->lambda_um = 0.525;
+    opt->XS = 0;
+    opt->YS = 0;
+    opt->l2_over_region = 1;
+}
+
+lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q, double NA,
+                           double lambda_um, int* XS, int* YS) {
+    if (!XS || !YS || Nnum < 1 || H < 1 || W < 1 || !(dML_um > 0) || !(Q > 0) || !(NA > 0) ||
+        !(lambda_um > 0))
+        return LFD_EINVAL;
+    // Eq. 7: pixel size in object space; Eq. 11: resolution limit; Eqs. 9-10
+    const double P_u = dML_um / (Q * Nnum);
+    const double d_psf = 1.22 * lambda_um * Nnum / NA;
+    const double xs = P_u * W / d_psf;
+    const double ys = P_u * H / d_psf;
+    auto clamp = [](double val, int n) {
+        double f = std::floor(val);
+        const double lo = n < 2 ? n : 2;
+        if (!(f >= lo)) f = lo;  // also catches NaN
+        if (f > n) f = n;
+        return (int)f;
+    };
+    *XS = clamp(xs, W);
+    *YS = clamp(ys, H);
+    return LFD_OK;
+}
+
+int lfd_predict_stop(const double* E, int n) {
+    if (!E || n < 1) return 0;
+    for (int k = 1; k < n; ++k)
+        if (E[k] < E[k - 1]) return k;
+    int best = 0;
+    for (int k = 1; k < n; ++k)
+        if (E[k] > E[best]) best = k;
+    return best + 1;
+}
+
+const char* lfd_status_string(lfd_status s) {
+    switch (s) {
+        case LFD_OK: return "LFD_OK";
+        case LFD_EINVAL: return "LFD_EINVAL";
+        case LFD_ENOMEM: return "LFD_ENOMEM";
+        case LFD_ECUDA: return "LFD_ECUDA";
+        case LFD_ENOTREADY: return "LFD_ENOTREADY";
+        case LFD_ETIMEDOUT: return "LFD_ETIMEDOUT";
+        case LFD_EBUSY: return "LFD_EBUSY";
+        case LFD_EINTERNAL: return "LFD_EINTERNAL";
+        case LFD_EUNSUPPORTED: return "LFD_EUNSUPPORTED";
+    }
+    return "unknown";
+}
+
+const char* lfd_last_error(const lfd_ctx* ctx) {
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+uint64_t lfd_launch_count(void) { return g_launches.load(); }
+
+lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                      const lfd_options* opt_in, void* cuda_stream, lfd_ctx** out) {
+    if (!out) return LFD_EINVAL;
+    *out = nullptr;
+    if (!psf) return LFD_EINVAL;
+    Geo g;
+    std::string why;
+    if (!make_geo(P, Nnum, Nz, H, W, &g, &why)) return LFD_EINVAL;
+    lfd_options opt;
+    if (opt_in) opt = *opt_in; else lfd_default_options(&opt);
+    if (opt.precision < LFD_FP32 || opt.precision > LFD_BF16X3 || opt.precision == LFD_TF32)
+        return LFD_EINVAL;
+    if (!(opt.eps >= 0.f)) return LFD_EINVAL;
+    int XS = opt.XS, YS = opt.YS;
+    if (XS <= 0 || YS <= 0) {
+        if (lfd_region_size(Nnum, H, W, opt.dML_um, opt.Q, opt.NA, opt.lambda_um, &XS, &YS) != LFD_OK)
+            return LFD_EINVAL;
+    }
+    if (XS > W || YS > H) return LFD_EINVAL;
+
+    lfd_ctx* ctx = new (std::nothrow) lfd_ctx();
+    if (!ctx) return LFD_ENOMEM;
+    ctx->g = g;
+    ctx->opt = opt;
+    ctx->XS = XS;
+    ctx->YS = YS;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    auto bail = [&](lfd_status s) {
+        std::fprintf(stderr, "lfd_create: %s\n", ctx->err.c_str());
+        free_all(ctx);
+        delete ctx;
+        return s;
+    };
+#define CREATE_CK(call)                                                          \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return bail(e_ == cudaErrorMemoryAllocation ? LFD_ENOMEM : LFD_ECUDA); \
+        }                                                                        \
+    } while (0)
+#define CREATE_TRY(x)                     \
+    do {                                  \
+        lfd_status s_ = (x);              \
+        if (s_ != LFD_OK) return bail(s_); \
+    } while (0)
+
+    CREATE_CK(cudaGetDevice(&ctx->device));
+    CREATE_CK(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (uses_tc(ctx)) {
+        int major = 0, minor = 0;
+        CREATE_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device));
+        CREATE_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device));
+        if (major != 10) {
+            ctx->err = "tensor-core precisions need an sm_10x (Blackwell) device";
+            return bail(LFD_EUNSUPPORTED);
+        }
+    }
+
+    ctx->fwd_splits = simt_fwd_splits(g, ctx->sm_count);
+    ctx->bwd_splits = simt_bwd_splits(g, ctx->sm_count);
+    // Hv partials serve both the SIMT path and the tensor-core path
+    const int fparts = std::max(ctx->fwd_splits, uses_tc(ctx) ? tc_forward_parts_for(g, ctx->sm_count) : 1);
+    const int bparts = std::max(ctx->bwd_splits, uses_tc(ctx) ? tc_backward_parts_for(g, ctx->sm_count) : 1);
+
+    const int64_t wcount = g.taps() * g.Spad * (int64_t)g.Cpad;
+    CREATE_TRY(dalloc(ctx, &ctx->W32, wcount, false));
+    for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vp32[b], g.rows * g.Cpad, true));
+    CREATE_TRY(dalloc(ctx, &ctx->Rp32, g.rows * g.Spad, true));
+    CREATE_TRY(dalloc(ctx, &ctx->Fwd, (int64_t)fparts * g.M_pad * g.Spad, true));
+    CREATE_TRY(dalloc(ctx, &ctx->Bwd, (int64_t)bparts * g.M_pad * g.Cpad, true));
+    CREATE_TRY(dalloc(ctx, &ctx->invHt1, g.M_pad * g.Cpad, true));
+    CREATE_TRY(dalloc(ctx, &ctx->ypoly, g.M_pad * g.Spad, true));
+    if (uses_tc(ctx)) {
+        const int nb = uses_lo(ctx) ? 2 : 1;
+        for (int b = 0; b < nb; ++b) {
+            CREATE_TRY(dalloc(ctx, &ctx->Wb[b], wcount, false));
+            CREATE_TRY(dalloc(ctx, &ctx->Vpb[b], g.rows * g.Cpad, true));
+            CREATE_TRY(dalloc(ctx, &ctx->Rpb[b], g.rows * g.Spad, true));
+        }
+    }
+    CREATE_TRY(dalloc(ctx, &ctx->mip, (int64_t)g.H * g.W, true));
+    CREATE_TRY(dalloc(ctx, &ctx->cosW, (int64_t)XS * g.W, false));
+    CREATE_TRY(dalloc(ctx, &ctx->cosH, (int64_t)YS * g.H, false));
+    CREATE_TRY(dalloc(ctx, &ctx->G, (int64_t)g.H * XS, true));
+    CREATE_TRY(dalloc(ctx, &ctx->rowE2, (int64_t)g.H, true));
+    CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)XS * YS, true));
+    CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)g.Ly * g.Lx, true));
+    ctx->hist_cap = 64;
+    CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * ctx->hist_cap, true));
+    CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned, 4 * sizeof(double)));
+
+    // PSF to the device (a device pointer is read in place)
+    const int64_t psf_count = (int64_t)Nz * Nnum * Nnum * P * P;
+    const float* psf_dev = psf;
+    float* psf_tmp = nullptr;
+    if (!is_device_ptr(psf)) {
+        CREATE_CK(cudaMalloc((void**)&psf_tmp, (size_t)psf_count * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(psf_tmp, psf, (size_t)psf_count * sizeof(float),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFree(psf_tmp);
+            CREATE_CK(e);
+        }
+        psf_dev = psf_tmp;
+    }
+    cudaError_t e = launch_repack_psf(psf_dev, g, ctx->W32, ctx->Wb[0], ctx->Wb[1], st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (psf_tmp) cudaFree(psf_tmp);
+    CREATE_CK(e);
+
+    // H^T 1 (FP32 path) and its reciprocal
+    CREATE_TRY(ensure_stage(ctx, false));
+    CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
+    CREATE_CK(launch_poly_image(ctx->stage_img, g, ctx->Rp32, g.m_base, nullptr, nullptr, st));
+    CREATE_TRY(run_backward(ctx, st, /*force_fp32=*/true));
+    CREATE_CK(launch_inv_ht1(ctx->Bwd, ctx->bwd_splits, g, ctx->invHt1, st));
+
+    // metric tables (Eqs. 2-4), FP64 on the host
+    {
+        std::vector<double> tw = dct_table(XS, g.W), th = dct_table(YS, g.H);
+        CREATE_CK(cudaMemcpyAsync(ctx->cosW, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CREATE_CK(cudaMemcpyAsync(ctx->cosH, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CREATE_CK(cudaStreamSynchronize(st));
+    }
+    if (uses_tc(ctx)) {
+        cudaError_t te = tc_init(ctx);
+        if (te != cudaSuccess) {
+            if (ctx->err.empty()) ctx->err = std::string("tc_init: ") + cudaGetErrorString(te);
+            return bail(LFD_ECUDA);
+        }
+    }
+    *out = ctx;
+    return LFD_OK;
+#undef CREATE_CK
+#undef CREATE_TRY
+}
+
+void lfd_destroy(lfd_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps, int* precision,
+                            int64_t* device_bytes) {
+    if (!ctx) return LFD_EINVAL;
+    if (XS) *XS = ctx->XS;
+    if (YS) *YS = ctx->YS;
+    if (taps) *taps = ctx->g.T;
+    if (precision) *precision = ctx->opt.precision;
+    if (device_bytes) *device_bytes = ctx->device_bytes;
+    return LFD_OK;
+}
+
+lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!v || !y_out) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W;
+    const bool vdev = is_device_ptr(v), ydev = is_device_ptr(y_out);
+    const float* vd = v;
+    if (!vdev) {
+        LFD_TRY(ensure_stage(ctx, true));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
+        vd = ctx->stage_vol;
+    }
+    LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
+    LFD_TRY(run_forward(ctx, 0, st));
+    float* yd = y_out;
+    if (!ydev) {
+        LFD_TRY(ensure_stage(ctx, false));
+        yd = ctx->stage_img;
+    }
+    LFD_CK(launch_fwd_finish_image(ctx->Fwd, fwd_parts(ctx), g, yd, st));
+    if (!ydev) {
+        LFD_CK(cudaMemcpyAsync(y_out, yd, nimg * sizeof(float), cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaStreamSynchronize(st));
+    }
+    return LFD_OK;
+}
+
+lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!r || !v_out) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W;
+    const bool rdev = is_device_ptr(r), vdev = is_device_ptr(v_out);
+    const float* rd = r;
+    if (!rdev) {
+        LFD_TRY(ensure_stage(ctx, false));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_img, r, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
+        rd = ctx->stage_img;
+    }
+    LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
+    LFD_TRY(run_backward(ctx, st));
+    float* vd = v_out;
+    if (!vdev) {
+        LFD_TRY(ensure_stage(ctx, true));
+        vd = ctx->stage_vol;
+    }
+    LFD_CK(launch_sum_depoly_volume(ctx->Bwd, bwd_parts(ctx), g, vd, st));
+    if (!vdev) {
+        LFD_CK(cudaMemcpyAsync(v_out, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaStreamSynchronize(st));
+    }
+    return LFD_OK;
+}
+
+lfd_status lfd_set_profiling(lfd_ctx* ctx, int on) {
+    if (!ctx) return LFD_EINVAL;
+    ctx->prof.on = on != 0;
+    for (double& x : ctx->prof.sum_ms) x = 0.0;
+    ctx->prof.count = 0;
+    return LFD_OK;
+}
+
+lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms5) {
+    if (!ctx || !ms5) return LFD_EINVAL;
+    for (int i = 0; i < 5; ++i)
+        ms5[i] = ctx->prof.count ? (float)(ctx->prof.sum_ms[i] / ctx->prof.count) : 0.f;
+    return LFD_OK;
+}
+
+lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int stop_at_predicted,
+                          int* iters_done, int* predicted, double* entropy_hist, double* flux_hist,
+                          void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!y || !v || n < 1) {
+        ctx->err = "invalid argument (NULL pointer or n < 1)";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W;
+    if (n > ctx->hist_cap) {
+        cudaFree(ctx->hist);
+        ctx->hist = nullptr;
+        ctx->hist_cap = n;
+        LFD_TRY(dalloc(ctx, &ctx->hist, 2LL * n, true));
+    }
+    const bool ydev = is_device_ptr(y), vdev = is_device_ptr(v);
+    const float* yd = y;
+    float* vd = v;
+    if (!ydev) {
+        LFD_TRY(ensure_stage(ctx, false));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_img, y, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
+        yd = ctx->stage_img;
+    }
+    if (!vdev) {
+        LFD_TRY(ensure_stage(ctx, true));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
+        vd = ctx->stage_vol;
+    }
+    LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
+    int cur = 0;
+    LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
+
+    const bool prof = ctx->prof.on;
+    if (prof && ctx->prof.ev.size() < 6 * (size_t)n) {
+        const size_t old = ctx->prof.ev.size();
+        ctx->prof.ev.resize(6 * (size_t)n, nullptr);
+        for (size_t i = old; i < ctx->prof.ev.size(); ++i) LFD_CK(cudaEventCreate(&ctx->prof.ev[i]));
+    }
+    cudaEvent_t* ev = prof ? ctx->prof.ev.data() : nullptr;
+    std::vector<double> E;
+    int ran = 0;
+    bool stopped = false;
+    const int fp = fwd_parts(ctx), bp = bwd_parts(ctx);
+    __nv_bfloat16* rhi = uses_tc(ctx) ? ctx->Rpb[0] : nullptr;
+    __nv_bfloat16* rlo = uses_lo(ctx) ? ctx->Rpb[1] : nullptr;
+    __nv_bfloat16* vhi = uses_tc(ctx) ? ctx->Vpb[0] : nullptr;
+    __nv_bfloat16* vlo = uses_lo(ctx) ? ctx->Vpb[1] : nullptr;
+    for (int k = 0; k < n; ++k) {
+        const int nxt = cur ^ 1;
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 0], st));
+        LFD_TRY(run_forward(ctx, cur, st));
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 1], st));
+        LFD_CK(launch_fwd_finish_ratio(ctx->Fwd, fp, ctx->ypoly, ctx->opt.eps, g, ctx->Rp32, rhi, rlo, st));
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 2], st));
+        LFD_TRY(run_backward(ctx, st));
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 3], st));
+        LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
+                             ctx->mip, ctx->flux_part, st));
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 4], st));
+        LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
+                             ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, ctx->flux_part,
+                             g.Ly * g.Lx, ctx->hist + k, ctx->hist + ctx->hist_cap + k, st));
+        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 5], st));
+        ran = k + 1;
+        if (stop_at_predicted) {
+            LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist + k, sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+            LFD_CK(cudaStreamSynchronize(st));
+            E.push_back(ctx->host_pinned[0]);
+            if (k >= 1 && E[k] < E[k - 1]) {  // E_{k+1} < E_k: keep v^k, still in Vp32[cur]
+                stopped = true;
+                break;
+            }
+        }
+        cur = nxt;
+    }
+    const int result = cur;
+    const int done = stopped ? ran - 1 : ran;
+    LFD_CK(launch_depoly_volume(ctx->Vp32[result], g.m_base, g, vd, st));
+    if (!vdev) LFD_CK(cudaMemcpyAsync(v, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
+    std::vector<double> hbuf(2 * (size_t)ran);
+    LFD_CK(cudaMemcpyAsync(hbuf.data(), ctx->hist, ran * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LFD_CK(cudaMemcpyAsync(hbuf.data() + ran, ctx->hist + ctx->hist_cap, ran * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+    LFD_CK(cudaStreamSynchronize(st));
+    if (prof) {
+        for (int k = 0; k < ran; ++k) {
+            for (int i = 0; i < 5; ++i) {
+                float ms = 0.f;
+                LFD_CK(cudaEventElapsedTime(&ms, ev[6 * k + i], ev[6 * k + i + 1]));
+                ctx->prof.sum_ms[i] += ms;
+            }
+        }
+        ctx->prof.count += ran;
+    }
+    if (entropy_hist)
+        for (int k = 0; k < n; ++k) entropy_hist[k] = k < ran ? hbuf[k] : NAN;
+    if (flux_hist)
+        for (int k = 0; k < n; ++k) flux_hist[k] = k < ran ? hbuf[ran + k] : NAN;
+    if (iters_done) *iters_done = done;
+    if (predicted) *predicted = lfd_predict_stop(hbuf.data(), ran);
+    return LFD_OK;
+}
+
+lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!v || !entropy) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t nvol = (int64_t)g.Nz * g.H * g.W;
+    const float* vd = v;
+    if (!is_device_ptr(v)) {
+        LFD_TRY(ensure_stage(ctx, true));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
+        vd = ctx->stage_vol;
+    }
+    LFD_CK(launch_mip_stack(vd, g.Nz, (int64_t)g.H * g.W, ctx->mip, st));
+    LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
+                         ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, nullptr, 0,
+                         ctx->hist, nullptr, st));
+    LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LFD_CK(cudaStreamSynchronize(st));
+    *entropy = ctx->host_pinned[0];
+    return LFD_OK;
+}
+
+}  // extern "C"

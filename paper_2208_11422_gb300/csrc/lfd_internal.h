@@ -1,0 +1,154 @@
+// Internal declarations of liblfd: problem geometry, the context, kernel
+// launchers. Not part of the public ABI (include/lfd.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "lfd.h"
+
+namespace lfd {
+
+// ---------------------------------------------------------------- geometry --
+// Polyphase form of the light-field projection (the PSF repack of the
+// forward model in include/lfd.h). Pixel i = Nnum*I + s (lenslet I, phase s),
+// voxel i' = Nnum*I' + t. With D = I - I' the PSF index is
+// m = Nnum*D + s - t + c, so
+//   Hv[I][s]      = sum_D sum_{(z,t)} V[I-D][(z,t)] * Wp[D][s][(z,t)]
+//   HtR[I'][(z,t)] = sum_D sum_s     R[I'+D][s]     * Wp[D][s][(z,t)]
+// with Wp[D][s][(z,t)] = K[z][t][m_y][m_x] (0 outside the window). Every pair
+// (s, t) has exactly k = P/Nnum valid D per axis; the union over pairs is
+// D in [-h, h], h = (k+1)/2, i.e. T = k+2 taps per axis.
+//
+// Lenslet-grid buffers are flattened with a zero halo so that a tap shift is a
+// constant row offset: lenslet (Iy, Ix) lives at row
+//   g = m_base + Iy*Lp + Ix,  Lp = Lx + h,  m_base = h + h*Lp,
+// columns Ix in [Lx, Lp) and the h rows above / below the grid stay zero, so a
+// shift by D = (Dy, Dx) is the row offset Dy*Lp + Dx and every out-of-grid
+// neighbour reads a zero. Output position m (0 <= m < M_out = Ly*Lp) maps to
+// (Iy, Ix) = (m / Lp, m % Lp); positions with Ix >= Lx are padding.
+struct Geo {
+    int N, Nz, P, H, W;     // Nnum, depths, PSF width, sensor size
+    int Ly, Lx, k, h, T;    // lenslet grid, PSF width in lenslets, halo, taps/axis
+    int S, Spad;            // phases per lenslet N*N, padded to a multiple of 16
+    int C, Cpad;            // channels Nz*S, padded to a multiple of 64
+    int Lp;                 // padded row length of the lenslet grid
+    int64_t m_base;         // row of lenslet (0,0) in a padded buffer
+    int64_t M_out;          // output positions Ly*Lp
+    int64_t M_pad;          // M_out rounded up to a multiple of 256
+    int64_t rows;           // rows allocated for padded buffers
+    __host__ __device__ int64_t taps() const { return (int64_t)T * T; }
+};
+
+bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why);
+
+// ------------------------------------------------------------ device buffers --
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// CUDA events bracketing the five stages of every RL iteration while
+// profiling is on; read back (and averaged) at the end of lfd_rl_iterate.
+struct StageTimes {
+    std::vector<cudaEvent_t> ev;  // 6 per iteration slot
+    bool on = false;
+    double sum_ms[5] = {0, 0, 0, 0, 0};
+    int64_t count = 0;
+};
+
+}  // namespace lfd
+
+struct lfd_ctx {
+    lfd::Geo g;
+    lfd_options opt;
+    int XS = 0, YS = 0;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+
+    // packed PSF: [T*T][Spad][Cpad]
+    float* W32 = nullptr;
+    __nv_bfloat16* Wb[2] = {nullptr, nullptr};   // hi, lo
+    // padded channels-last volume [rows][Cpad] (double-buffered iterate)
+    float* Vp32[2] = {nullptr, nullptr};
+    __nv_bfloat16* Vpb[2] = {nullptr, nullptr};  // hi, lo of the forward input
+    // padded polyphase image [rows][Spad]
+    float* Rp32 = nullptr;
+    __nv_bfloat16* Rpb[2] = {nullptr, nullptr};
+    // projection outputs indexed by output position m
+    float* Fwd = nullptr;        // [fwd_splits][M_pad][Spad]
+    float* Bwd = nullptr;        // [bwd_splits][M_pad][Cpad]
+    int fwd_splits = 1, bwd_splits = 1;
+    float* invHt1 = nullptr;     // [M_pad][Cpad]
+    float* ypoly = nullptr;      // [M_pad][Spad]
+    // metric
+    float* mip = nullptr;        // [H][W]
+    double* cosW = nullptr;      // [XS][W]
+    double* cosH = nullptr;      // [YS][H]
+    double* G = nullptr;         // [H][XS]
+    double* rowE2 = nullptr;     // [H] sum of mip^2 per row
+    double* coef = nullptr;      // [YS][XS]
+    double* flux_part = nullptr; // [Ly*Lx]
+    double* hist = nullptr;      // [2][hist_cap]: entropy, flux
+    int hist_cap = 0;
+    double* host_pinned = nullptr;  // [4]
+    // staging for host pointers
+    float* stage_vol = nullptr;  // [Nz][H][W]
+    float* stage_img = nullptr;  // [H][W]
+    int64_t device_bytes = 0;
+    lfd::StageTimes prof;
+    // tensor-core path state (tcgen05), created on first use
+    void* tc = nullptr;
+};
+
+namespace lfd {
+
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// --------------------------------------------------------- kernel launchers --
+// All launchers enqueue on `st` and return the launch error (cudaGetLastError).
+cudaError_t launch_fill(float* p, int64_t n, float val, cudaStream_t st);
+cudaError_t launch_mip_stack(const float* v, int Nz, int64_t HW, float* mip, cudaStream_t st);
+cudaError_t launch_repack_psf(const float* psf, const Geo& g, float* W32,
+                              __nv_bfloat16* whi, __nv_bfloat16* wlo, cudaStream_t st);
+cudaError_t launch_poly_volume(const float* v, const Geo& g, float* vp32,
+                               __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+cudaError_t launch_depoly_volume(const float* vp32, int64_t row0, const Geo& g,
+                                 float* v, cudaStream_t st);
+cudaError_t launch_sum_depoly_volume(const float* parts, int nsplit, const Geo& g,
+                                     float* v, cudaStream_t st);
+cudaError_t launch_poly_image(const float* y, const Geo& g, float* dst, int64_t row0,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+cudaError_t launch_fwd_finish_image(const float* parts, int nsplit, const Geo& g,
+                                    float* y_out, cudaStream_t st);
+cudaError_t launch_fwd_finish_ratio(const float* parts, int nsplit, const float* ypoly,
+                                    float eps, const Geo& g, float* rp32,
+                                    __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+cudaError_t launch_inv_ht1(const float* parts, int nsplit, const Geo& g, float* inv,
+                           cudaStream_t st);
+cudaError_t launch_update(const float* vin, float* vout, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          const float* parts, int nsplit, const float* inv, const Geo& g,
+                          float* mip, double* flux_part, cudaStream_t st);
+cudaError_t launch_mip(const float* vp32, const Geo& g, float* mip, cudaStream_t st);
+cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH,
+                          int H, int W, int XS, int YS, int l2_over_region,
+                          double* G, double* rowE2, double* coef,
+                          const double* flux_part, int nflux, double* out_entropy,
+                          double* out_flux, cudaStream_t st);
+
+// FP32 SIMT implicit-GEMM projections (CUDA cores)
+int simt_fwd_splits(const Geo& g, int sm_count);
+int simt_bwd_splits(const Geo& g, int sm_count);
+cudaError_t launch_simt_forward(const float* vp32, const float* W32, const Geo& g,
+                                int nsplit, float* out, cudaStream_t st);
+cudaError_t launch_simt_backward(const float* rp32, const float* W32, const Geo& g,
+                                 int nsplit, float* out, cudaStream_t st);
+
+}  // namespace lfd

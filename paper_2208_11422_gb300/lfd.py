@@ -1,0 +1,222 @@
+"""ctypes binding of liblfd (include/lfd.h), one Python function per C entry point.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Array arguments may be torch tensors (CUDA or CPU, contiguous
+float32), numpy float32 arrays, or raw integer addresses; streams may be a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer or None (default stream).
+``load()`` raises ``LfdError`` when the library is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblfd.so")
+
+LFD_OK, LFD_EINVAL, LFD_ENOMEM, LFD_ECUDA, LFD_ENOTREADY, LFD_ETIMEDOUT, LFD_EBUSY, \
+    LFD_EINTERNAL, LFD_EUNSUPPORTED = range(9)
+LFD_FP32, LFD_TF32, LFD_BF16, LFD_BF16X3 = range(4)
+PRECISIONS = {"fp32": LFD_FP32, "bf16": LFD_BF16, "bf16x3": LFD_BF16X3}
+
+
+class LfdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class lfd_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("eps", ctypes.c_float),
+        ("dML_um", ctypes.c_double),
+        ("Q", ctypes.c_double),
+        ("NA", ctypes.c_double),
+        ("lambda_um", ctypes.c_double),
+        ("XS", ctypes.c_int),
+        ("YS", ctypes.c_int),
+        ("l2_over_region", ctypes.c_int),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "lfd_default_options": (None, [ctypes.POINTER(lfd_options)]),
+    "lfd_create": (_I, [_VP, _I, _I, _I, _I, _I, ctypes.POINTER(lfd_options), _VP,
+                        ctypes.POINTER(_VP)]),
+    "lfd_forward": (_I, [_VP, _VP, _VP, _VP]),
+    "lfd_backward": (_I, [_VP, _VP, _VP, _VP]),
+    "lfd_rl_iterate": (_I, [_VP, _VP, _VP, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
+    "lfd_quality": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
+    "lfd_destroy": (None, [_VP]),
+    "lfd_last_error": (ctypes.c_char_p, [_VP]),
+    "lfd_status_string": (ctypes.c_char_p, [_I]),
+    "lfd_region_size": (_I, [_I, _I, _I, _D, _D, _D, _D, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lfd_predict_stop": (_I, [ctypes.POINTER(_D), _I]),
+    "lfd_get_geometry": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)]),
+    "lfd_launch_count": (ctypes.c_uint64, []),
+    "lfd_set_profiling": (_I, [_VP, _I]),
+    "lfd_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+}
+
+
+def load(path: str | None = None):
+    """Load liblfd.so (built by ``paper_2208_11422_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise LfdError(LFD_EINTERNAL, "liblfd.so not built: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+# ----------------------------------------------------------- marshalling --
+def _ptr(x):
+    """Address of a contiguous float32 tensor / array, or an int address."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("tensor must be contiguous float32")
+        return x.data_ptr()
+    if hasattr(x, "__array_interface__"):
+        import numpy as np
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous float32")
+        return x.__array_interface__["data"][0]
+    raise TypeError("unsupported array argument %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return getattr(s, "cuda_stream", s)
+
+
+def _check(status: int, ctx=None):
+    if status != LFD_OK:
+        lib = load()
+        msg = lib.lfd_last_error(ctx).decode() if ctx else ""
+        raise LfdError(status, "%s: %s" % (lib.lfd_status_string(status).decode(), msg))
+
+
+# ------------------------------------------------------------- entry points --
+def lfd_default_options(**overrides) -> lfd_options:
+    o = lfd_options()
+    load().lfd_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def lfd_create(psf, P: int, Nnum: int, Nz: int, H: int, W: int, opt: lfd_options | None = None,
+               stream=None):
+    out = _VP()
+    st = load().lfd_create(_ptr(psf), P, Nnum, Nz, H, W,
+                           ctypes.byref(opt) if opt is not None else None, _stream(stream),
+                           ctypes.byref(out))
+    if st != LFD_OK:
+        raise LfdError(st, "lfd_create failed: %s" % load().lfd_status_string(st).decode())
+    return out.value
+
+
+def lfd_forward(ctx, v, y_out, stream=None):
+    _check(load().lfd_forward(ctx, _ptr(v), _ptr(y_out), _stream(stream)), ctx)
+
+
+def lfd_backward(ctx, r, v_out, stream=None):
+    _check(load().lfd_backward(ctx, _ptr(r), _ptr(v_out), _stream(stream)), ctx)
+
+
+def lfd_rl_iterate(ctx, y, v, n: int, stop_at_predicted: bool = False, stream=None):
+    """Returns (iters_done, predicted, entropy list, flux list)."""
+    done, pred = _I(0), _I(0)
+    ent = (_D * n)()
+    flux = (_D * n)()
+    _check(load().lfd_rl_iterate(ctx, _ptr(y), _ptr(v), n, int(bool(stop_at_predicted)),
+                                 ctypes.byref(done), ctypes.byref(pred), ent, flux,
+                                 _stream(stream)), ctx)
+    return done.value, pred.value, list(ent), list(flux)
+
+
+def lfd_quality(ctx, v, stream=None) -> float:
+    e = _D(0)
+    _check(load().lfd_quality(ctx, _ptr(v), ctypes.byref(e), _stream(stream)), ctx)
+    return e.value
+
+
+def lfd_destroy(ctx):
+    if ctx:
+        load().lfd_destroy(ctx)
+
+
+def lfd_last_error(ctx) -> str:
+    return load().lfd_last_error(ctx).decode()
+
+
+def lfd_status_string(s: int) -> str:
+    return load().lfd_status_string(s).decode()
+
+
+def lfd_region_size(Nnum, H, W, dML_um=150.0, Q=40.0, NA=0.95, lambda_um=0.525):
+    xs, ys = _I(0), _I(0)
+    _check(load().lfd_region_size(Nnum, H, W, dML_um, Q, NA, lambda_um, ctypes.byref(xs),
+                                  ctypes.byref(ys)))
+    return xs.value, ys.value
+
+
+def lfd_predict_stop(E) -> int:
+    arr = (_D * len(E))(*E)
+    return load().lfd_predict_stop(arr, len(E))
+
+
+def lfd_get_geometry(ctx) -> dict:
+    xs, ys, taps, prec = _I(0), _I(0), _I(0), _I(0)
+    nbytes = ctypes.c_int64(0)
+    _check(load().lfd_get_geometry(ctx, ctypes.byref(xs), ctypes.byref(ys), ctypes.byref(taps),
+                                   ctypes.byref(prec), ctypes.byref(nbytes)), ctx)
+    return {"XS": xs.value, "YS": ys.value, "taps": taps.value, "precision": prec.value,
+            "device_bytes": nbytes.value}
+
+
+def lfd_launch_count() -> int:
+    return int(load().lfd_launch_count())
+
+
+def lfd_set_profiling(ctx, on: bool = True):
+    _check(load().lfd_set_profiling(ctx, int(bool(on))), ctx)
+
+
+def lfd_stage_times(ctx):
+    arr = (ctypes.c_float * 5)()
+    _check(load().lfd_stage_times(ctx, arr), ctx)
+    return list(arr)

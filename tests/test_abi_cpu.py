@@ -1,0 +1,109 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+that include/lfd.h declares, validates shapes before touching CUDA, and its
+host-only helpers agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import metric
+from paper_2208_11422_gb300 import lfd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_11422_gb300 import build
+    build.build()
+    return lfd.load()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(lfd_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "lfd_create" in names and "lfd_rl_iterate" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding covers the same set
+    assert set(names) <= set(lfd.exported_names())
+
+
+@pytest.mark.parametrize("args", [
+    (25, 4, 5, 75, 75),    # even Nnum
+    (24, 5, 5, 75, 75),    # even P
+    (27, 5, 5, 75, 75),    # P not a multiple of Nnum
+    (25, 5, 0, 75, 75),    # no depths
+    (25, 5, 5, 74, 75),    # H not a multiple of Nnum
+    (25, 5, 5, 75, 0),     # empty sensor
+    (25, 5, 5, -5, 75),
+])
+def test_create_rejects_bad_shapes_before_any_cuda_call(lib, args):
+    P, N, Nz, H, W = args
+    psf = np.zeros(16, np.float32)
+    out = ctypes.c_void_p(123)
+    st = lib.lfd_create(psf.ctypes.data, P, N, Nz, H, W, None, None, ctypes.byref(out))
+    assert st == lfd.LFD_EINVAL
+    assert out.value is None
+
+
+def test_create_rejects_null_psf_and_bad_options(lib):
+    out = ctypes.c_void_p()
+    assert lib.lfd_create(None, 25, 5, 5, 75, 75, None, None, ctypes.byref(out)) == lfd.LFD_EINVAL
+    psf = np.zeros(16, np.float32)
+    o = lfd.lfd_default_options()
+    o.precision = 9
+    assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
+                          ctypes.byref(out)) == lfd.LFD_EINVAL
+    o = lfd.lfd_default_options(XS=100, YS=4)   # region wider than the image
+    assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
+                          ctypes.byref(out)) == lfd.LFD_EINVAL
+    assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, None, None, None) == lfd.LFD_EINVAL
+
+
+def test_null_context_calls(lib):
+    assert lib.lfd_forward(None, None, None, None) == lfd.LFD_EINVAL
+    assert lib.lfd_backward(None, None, None, None) == lfd.LFD_EINVAL
+    assert lib.lfd_rl_iterate(None, None, None, 1, 0, None, None, None, None, None) == lfd.LFD_EINVAL
+    lib.lfd_destroy(None)
+    assert lfd.lfd_status_string(lfd.LFD_EINVAL) == "LFD_EINVAL"
+
+
+def test_defaults():
+    o = lfd.lfd_default_options()
+    assert o.precision == lfd.LFD_FP32 and abs(o.eps - 1e-6) < 1e-12
+    assert (o.dML_um, o.Q, o.NA, o.lambda_um) == (150.0, 40.0, 0.95, 0.525)
+    assert o.l2_over_region == 1
+
+
+@pytest.mark.parametrize("N,H,W", [(5, 75, 75), (15, 615, 615), (15, 2025, 2025),
+                                   (15, 615, 2025), (11, 363, 1331), (13, 13, 13), (1, 7, 3),
+                                   (3, 900, 30)])
+def test_region_size_matches_oracle(N, H, W):
+    assert lfd.lfd_region_size(N, H, W) == metric.region_size(N, H, W)
+
+
+def test_region_size_rejects_bad_optics(lib):
+    xs, ys = ctypes.c_int(), ctypes.c_int()
+    assert lib.lfd_region_size(5, 75, 75, 0.0, 40.0, 0.95, 0.5, ctypes.byref(xs), ctypes.byref(ys)) \
+        == lfd.LFD_EINVAL
+
+
+def test_predict_stop_matches_oracle():
+    rng = np.random.default_rng(0)
+    for trial in range(200):
+        n = int(rng.integers(1, 12))
+        E = rng.integers(0, 4, n).astype(float).tolist()   # many ties on purpose
+        assert lfd.lfd_predict_stop(E) == metric.predicted_iteration(E), E
+    assert lfd.lfd_predict_stop([]) == 0
