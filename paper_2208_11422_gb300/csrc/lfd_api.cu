@@ -301,6 +301,10 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
             ctx->err = "tensor-core precisions need an sm_10x (Blackwell) device";
             return bail(LFD_EUNSUPPORTED);
         }
+        if (!tc_supported(g)) {
+            ctx->err = "tensor-core precisions support Nnum <= 15";
+            return bail(LFD_EUNSUPPORTED);
+        }
     }
 
     ctx->fwd_splits = simt_fwd_splits(g, ctx->sm_count);
@@ -564,6 +568,13 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
     LFD_CK(cudaMemcpyAsync(hbuf.data() + ran, ctx->hist + ctx->hist_cap, ran * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
     LFD_CK(cudaStreamSynchronize(st));
+    if (uses_tc(ctx)) {
+        const int te = tc_error(ctx);
+        if (te != 0) {
+            ctx->err = "tensor-core kernel gave up waiting (code " + std::to_string(te) + ")";
+            return LFD_ETIMEDOUT;
+        }
+    }
     if (prof) {
         for (int k = 0; k < ran; ++k) {
             for (int i = 0; i < 5; ++i) {

@@ -1,16 +1,569 @@
-// Tensor-core projections (placeholder until the tcgen05 kernels land).
+// Light-field projections as implicit GEMMs on the 5th-generation tensor cores
+// (tcgen05, sm_103a): TMA-staged BF16 tiles in shared memory, FP32
+// accumulators in tensor memory (TMEM).
+//
+//   forward   Hv[m][s]      = sum_D sum_c  Vp[m_base + m - off(D)][c] * Wp[D][s][c]
+//   backward  HtR[m][(z,t)] = sum_D sum_s  Rp[m_base + m + off(D)][s] * Wp[D][s][(z,t)]
+//
+// (polyphase form and padded row layout: see lfd_internal.h). A block owns a
+// 256-row output tile (two M=128 MMAs, accumulators at TMEM columns 0 and 256)
+// and up to 256 output columns. The K loop walks (tap, 64-element block); for
+// every step one TMA box of the shifted A rows (256 x 128 B) and one box of
+// the tap's weights land in a 3-stage shared-memory ring. The weights are the
+// B operand in K-major form for the forward (Wp[D] is [s][c], c contiguous)
+// and in MN-major form for the backward (same array, contraction over s). In
+// split-BF16 mode each step runs three passes: hi*hi, hi*lo, lo*hi.
+//
+// Warp roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues
+// the MMAs (one thread), warps 2-5 drain the accumulators to global memory.
+// Blocks are persistent over work units (row tile, column tile, K split); a K
+// split writes its own partial output, summed later in a fixed order.
+//
+// Every wait on an mbarrier is bounded (4 s of %globaltimer). On a timeout the
+// block raises a shared abort flag, records an error code in global memory,
+// waits (bounded) for its own TMA copies and MMAs still in flight, frees TMEM
+// and returns; the host reports LFD_ETIMEDOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
 #include "tc_gemm.h"
 
 namespace lfd {
-int tc_forward_parts_for(const Geo&, int) { return 1; }
-int tc_backward_parts_for(const Geo&, int) { return 1; }
-int tc_forward_parts(const lfd_ctx*) { return 1; }
-int tc_backward_parts(const lfd_ctx*) { return 1; }
-cudaError_t tc_init(lfd_ctx* ctx) {
-    ctx->err = "tensor-core projections are not built yet";
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int kStages = 3;
+constexpr int kBM = 256;
+constexpr int kBK = 64;                       // bf16 elements per k-block = 128 B
+constexpr int kABytes = kBM * kBK * 2;        // 32 KB
+constexpr int kBBytesMax = 256 * kBK * 2;     // 32 KB
+constexpr int kStageBytes = kABytes + kBBytesMax;
+constexpr int kThreads = 192;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;
+
+struct TcArgs {
+    int64_t m_base;
+    int Lp, T, h;
+    int n_mtiles, n_ntiles, nsplit, n_units;
+    int kb_per_tap, kb_total;
+    int bn;             // accumulator columns (MMA N)
+    int n_valid;        // row length of the destination (Spad or Cpad)
+    int passes;         // 1 BF16, 3 split BF16
+    uint32_t tx_bytes;  // bytes landing per stage
+    float* out;
+    int64_t slot_stride;
+    int* err;
+};
+
+// ---------------------------------------------------------------- PTX bits --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-cudaError_t tc_forward(lfd_ctx*, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_backward(lfd_ctx*, cudaStream_t) { return cudaErrorNotSupported; }
-void tc_destroy(lfd_ctx*) {}
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false when the block is aborting or the limit passed
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
+                          int code) {
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtime() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+// wait used while tearing down: limit only, ignores the abort flag
+__device__ void mbar_wait_drain(uint64_t* b, uint32_t parity) {
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(b, parity))
+        if (gtime() - t0 > kTimeoutNs) return;
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                       uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                       uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 format):
+// start >> 4 in bits 0-13, leading byte offset >> 4 in 16-29, stride byte
+// offset >> 4 in 32-45, descriptor version 1 at bit 46, swizzle mode 2
+// (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), A K-major (bit 15 = 0), B K- or MN-major
+// (bit 16), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Unit {
+    int split, ntile, mtile, kb_lo, kb_hi;
+};
+__device__ __forceinline__ Unit decode(const TcArgs& a, int u) {
+    Unit r;
+    const int per_split = a.n_mtiles * a.n_ntiles;
+    r.split = u / per_split;
+    const int rem = u % per_split;
+    r.ntile = rem / a.n_mtiles;
+    r.mtile = rem % a.n_mtiles;
+    r.kb_lo = (int)((int64_t)r.split * a.kb_total / a.nsplit);
+    r.kb_hi = (int)((int64_t)(r.split + 1) * a.kb_total / a.nsplit);
+    return r;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+          const TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t* smem = smem_raw + (sbase - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* acc_full = empty + kStages;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* mma_done = acc_empty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 128);
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        *consumed_ctr = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------- TMA producer --
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+                const Unit w = decode(a, u);
+                const int64_t m0 = (int64_t)w.mtile * kBM;
+                const int n0 = w.ntile * a.bn;
+                for (int kb = w.kb_lo; kb < w.kb_hi && ok; ++kb) {
+                    const int tap = kb / a.kb_per_tap, cb = kb % a.kb_per_tap;
+                    const int Dy = tap / a.T - a.h, Dx = tap % a.T - a.h;
+                    const int64_t off = (int64_t)Dy * a.Lp + Dx;
+                    const int row = (int)(a.m_base + m0 + (FWD ? -off : off));
+                    for (int p = 0; p < a.passes; ++p) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 1)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&full[stage], a.tx_bytes);
+                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
+                        const CUtensorMap* ma = (p == 2) ? &mA1 : &mA0;
+                        const CUtensorMap* mb = (p == 1) ? &mB1 : &mB0;
+                        tma_2d(sA, ma, cb * kBK, row, &full[stage]);
+                        if (FWD) {
+                            tma_3d(sB, mb, cb * kBK, 0, tap, &full[stage]);
+                        } else {
+                            for (int j = 0; j < a.bn / 64; ++j)
+                                tma_3d(sB + j * 8192, mb, n0 + j * 64, cb * kBK, tap, &full[stage]);
+                        }
+                        ++issued;
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {  // drain our own copies still in flight
+                for (int i = *consumed_ctr; i < issued; ++i)
+                    mbar_wait_drain(&full[i % kStages], (uint32_t)((i / kStages) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer --
+            constexpr bool kBMn = !FWD;
+            const uint32_t idesc = idesc_bf16(128, a.bn, kBMn);
+            int stage = 0, consumed = 0, ui = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < a.n_units && ok; u += gridDim.x, ++ui) {
+                const Unit w = decode(a, u);
+                if (ui > 0 && !mbar_wait(acc_empty, (uint32_t)((ui - 1) & 1), abort_flag, a.err, 2)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                bool first = true;
+                for (int kb = w.kb_lo; kb < w.kb_hi && ok; ++kb) {
+                    for (int p = 0; p < a.passes; ++p) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 3)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
+#pragma unroll
+                        for (int ks = 0; ks < kBK / 16; ++ks) {
+                            const uint64_t bd = FWD ? sdesc(sB + ks * 32, 16, 1024)
+                                                    : sdesc(sB + ks * 2048, 8192, 1024);
+#pragma unroll
+                            for (int half = 0; half < 2; ++half) {
+                                const uint64_t ad = sdesc(sA + half * 16384 + ks * 32, 16, 1024);
+                                umma_bf16(tmem + half * 256, ad, bd, idesc,
+                                          (first && ks == 0) ? 0u : 1u);
+                            }
+                        }
+                        first = false;
+                        umma_commit(&empty[stage]);
+                        *consumed_ctr = ++consumed;
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+                if (ok) umma_commit(acc_full);
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            umma_commit(mma_done);
+            mbar_wait_drain(mma_done, 0);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int lg = warp & 3;  // TMEM lane quarter this warp may access
+        const int row = lg * 32 + lane;
+        int ui = 0;
+        for (int u = blockIdx.x; u < a.n_units; u += gridDim.x, ++ui) {
+            const Unit w = decode(a, u);
+            if (!mbar_wait(acc_full, (uint32_t)(ui & 1), abort_flag, a.err, 4)) break;
+            tc_fence_after();
+            float* outp = a.out + (int64_t)w.split * a.slot_stride;
+            for (int half = 0; half < 2; ++half) {
+                const int64_t m = (int64_t)w.mtile * kBM + half * 128 + row;
+                for (int c0 = 0; c0 < a.bn; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + half * 256 + c0, r);
+                    const int n = w.ntile * a.bn + c0;
+                    if (n < a.n_valid) {
+                        float4* dst = reinterpret_cast<float4*>(outp + m * a.n_valid + n);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                                 __uint_as_float(r[4 * q + 2]),
+                                                 __uint_as_float(r[4 * q + 3]));
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ------------------------------------------------------------------- host --
+struct TcState {
+    CUtensorMap fa[2], fb[2];   // forward: A = Vpb hi/lo, B = Wb hi/lo (K-major)
+    CUtensorMap ba[2], bb[2];   // backward: A = Rpb hi/lo, B = Wb hi/lo (MN-major)
+    TcArgs fwd, bwd;
+    int fwd_grid = 0, bwd_grid = 0;
+    int* err = nullptr;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, int rank, const cuuint64_t* dims,
+              const cuuint64_t* strides, const cuuint32_t* box) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// smallest split count whose wave efficiency is within 3% of the best
+int pick_split(int64_t base_units, int kb_total, int sm_count, int max_split) {
+    double best = 0.0;
+    std::vector<double> eff(max_split + 1, 0.0);
+    for (int s = 1; s <= max_split; ++s) {
+        if (kb_total / s < 2 && s > 1) break;
+        const int64_t units = base_units * s;
+        const int64_t grid = std::min<int64_t>(units, sm_count);
+        const int64_t waves = (units + grid - 1) / grid;
+        eff[s] = (double)units / (double)(waves * sm_count);
+        best = std::max(best, eff[s]);
+    }
+    for (int s = 1; s <= max_split; ++s)
+        if (eff[s] >= 0.97 * best) return s;
+    return 1;
+}
+
+int fwd_split_for(const Geo& g, int sm) {
+    const int kb_total = (int)(g.taps() * (g.Cpad / kBK));
+    return pick_split(g.M_pad / kBM, kb_total, sm, 64);
+}
+int bwd_ntiles(const Geo& g) { return (g.Cpad + 255) / 256; }
+int bwd_bn(const Geo& g) { return g.Cpad >= 256 ? 256 : g.Cpad; }
+int bwd_split_for(const Geo& g, int sm) {
+    const int kb_total = (int)(g.taps() * ((g.Spad + kBK - 1) / kBK));
+    return pick_split((g.M_pad / kBM) * bwd_ntiles(g), kb_total, sm, 16);
+}
+
+}  // namespace
+
+bool tc_supported(const Geo& g) { return g.Spad <= 256; }
+
+int tc_forward_parts_for(const Geo& g, int sm_count) { return fwd_split_for(g, sm_count); }
+int tc_backward_parts_for(const Geo& g, int sm_count) { return bwd_split_for(g, sm_count); }
+int tc_forward_parts(const lfd_ctx* ctx) {
+    return ctx->tc ? static_cast<const TcState*>(ctx->tc)->fwd.nsplit : 1;
+}
+int tc_backward_parts(const lfd_ctx* ctx) {
+    return ctx->tc ? static_cast<const TcState*>(ctx->tc)->bwd.nsplit : 1;
+}
+
+cudaError_t tc_init(lfd_ctx* ctx) {
+    const Geo& g = ctx->g;
+    if (!tc_supported(g)) {
+        ctx->err = "tensor-core projections need Nnum^2 padded to <= 256 (Nnum <= 15)";
+        return cudaErrorNotSupported;
+    }
+    TcState* s = new (std::nothrow) TcState();
+    if (!s) return cudaErrorMemoryAllocation;
+    std::memset(s, 0, sizeof(*s));
+    ctx->tc = s;
+    cudaError_t e = cudaMalloc(&s->err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(s->err, 0, sizeof(int));
+    if (e != cudaSuccess) return e;
+
+    const bool split = ctx->opt.precision == LFD_BF16X3;
+    const int lo = split ? 1 : 0;
+    // forward A: Vpb [rows][Cpad]; B: Wb [taps][Spad][Cpad]
+    for (int b = 0; b < 2; ++b) {
+        const int idx = b == 0 ? 0 : lo;
+        {
+            const cuuint64_t dims[2] = {(cuuint64_t)g.Cpad, (cuuint64_t)g.rows};
+            const cuuint64_t str[1] = {(cuuint64_t)g.Cpad * 2};
+            const cuuint32_t box[2] = {64, 256};
+            if (!make_map(&s->fa[b], ctx->Vpb[idx], 2, dims, str, box)) goto fail;
+        }
+        {
+            const cuuint64_t dims[3] = {(cuuint64_t)g.Cpad, (cuuint64_t)g.Spad, (cuuint64_t)g.taps()};
+            const cuuint64_t str[2] = {(cuuint64_t)g.Cpad * 2, (cuuint64_t)g.Cpad * 2 * g.Spad};
+            const cuuint32_t boxf[3] = {64, (cuuint32_t)g.Spad, 1};
+            const cuuint32_t boxb[3] = {64, 64, 1};
+            if (!make_map(&s->fb[b], ctx->Wb[idx], 3, dims, str, boxf)) goto fail;
+            if (!make_map(&s->bb[b], ctx->Wb[idx], 3, dims, str, boxb)) goto fail;
+        }
+        {
+            const cuuint64_t dims[2] = {(cuuint64_t)g.Spad, (cuuint64_t)g.rows};
+            const cuuint64_t str[1] = {(cuuint64_t)g.Spad * 2};
+            const cuuint32_t box[2] = {64, 256};
+            if (!make_map(&s->ba[b], ctx->Rpb[idx], 2, dims, str, box)) goto fail;
+        }
+    }
+    {
+        TcArgs& f = s->fwd;
+        f.m_base = g.m_base;
+        f.Lp = g.Lp;
+        f.T = g.T;
+        f.h = g.h;
+        f.n_mtiles = (int)(g.M_pad / kBM);
+        f.n_ntiles = 1;
+        f.nsplit = fwd_split_for(g, ctx->sm_count);
+        f.n_units = f.n_mtiles * f.nsplit;
+        f.kb_per_tap = g.Cpad / kBK;
+        f.kb_total = (int)(g.taps() * f.kb_per_tap);
+        f.bn = g.Spad;
+        f.n_valid = g.Spad;
+        f.passes = split ? 3 : 1;
+        f.tx_bytes = (uint32_t)(kABytes + kBK * 2 * g.Spad);
+        f.out = ctx->Fwd;
+        f.slot_stride = g.M_pad * g.Spad;
+        f.err = s->err;
+        s->fwd_grid = std::min(f.n_units, ctx->sm_count);
+
+        TcArgs& b = s->bwd;
+        b = f;
+        b.n_ntiles = bwd_ntiles(g);
+        b.nsplit = bwd_split_for(g, ctx->sm_count);
+        b.n_units = b.n_mtiles * b.n_ntiles * b.nsplit;
+        b.kb_per_tap = (g.Spad + kBK - 1) / kBK;
+        b.kb_total = (int)(g.taps() * b.kb_per_tap);
+        b.bn = bwd_bn(g);
+        b.n_valid = g.Cpad;
+        b.tx_bytes = (uint32_t)(kABytes + (b.bn / 64) * 8192);
+        b.out = ctx->Bwd;
+        b.slot_stride = g.M_pad * g.Cpad;
+        s->bwd_grid = std::min(b.n_units, ctx->sm_count);
+    }
+    e = cudaFuncSetAttribute(k_tc_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    return e;
+fail:
+    ctx->err = "cuTensorMapEncodeTiled failed (or the driver entry point is missing)";
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_forward(lfd_ctx* ctx, int /*buf*/, cudaStream_t st) {
+    TcState* s = static_cast<TcState*>(ctx->tc);
+    if (!s) return cudaErrorNotReady;
+    k_tc_conv<true><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fb[0],
+                                                               s->fb[1], s->fwd);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tc_backward(lfd_ctx* ctx, cudaStream_t st) {
+    TcState* s = static_cast<TcState*>(ctx->tc);
+    if (!s) return cudaErrorNotReady;
+    k_tc_conv<false><<<s->bwd_grid, kThreads, kSmemBytes, st>>>(s->ba[0], s->ba[1], s->bb[0],
+                                                                s->bb[1], s->bwd);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int tc_error(lfd_ctx* ctx) {
+    TcState* s = static_cast<TcState*>(ctx->tc);
+    if (!s || !s->err) return 0;
+    int h = 0;
+    if (cudaMemcpy(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (h) cudaMemset(s->err, 0, sizeof(int));
+    return h;
+}
+
+void tc_destroy(lfd_ctx* ctx) {
+    TcState* s = static_cast<TcState*>(ctx->tc);
+    if (!s) return;
+    if (s->err) cudaFree(s->err);
+    delete s;
+    ctx->tc = nullptr;
+}
+
 }  // namespace lfd

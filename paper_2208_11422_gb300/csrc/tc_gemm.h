@@ -17,5 +17,10 @@ cudaError_t tc_forward(lfd_ctx* ctx, int buf, cudaStream_t st);
 // H^T r partials of the BF16 copies of Rp32 into ctx->Bwd
 cudaError_t tc_backward(lfd_ctx* ctx, cudaStream_t st);
 void tc_destroy(lfd_ctx* ctx);
+// shape check: the forward tile holds all Nnum^2 phases (<= 256 columns)
+bool tc_supported(const Geo& g);
+// error word of the tensor-core kernels (0 = none; 1-4 = which wait timed
+// out); reading it synchronises with the device and clears it
+int tc_error(lfd_ctx* ctx);
 
 }  // namespace lfd
