@@ -45,6 +45,13 @@ constexpr int kStageBytes = kABytes + kBBytesMax;
 constexpr int kThreads = 192;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
+// The tensor cores add each MMA's result into the FP32 accumulator with a
+// rounding that loses about half an ulp per step in one direction, so the
+// relative error of a long chain grows linearly with its length (measured:
+// ~3e-8 per MMA step). Chains are therefore cut after kChainSteps MMA steps:
+// the accumulator is drained and added into the FP32 output in registers
+// (round to nearest), and the next chunk starts from zero.
+constexpr int kChainSteps = 1536;
 
 struct TcArgs {
     int64_t m_base;
@@ -54,6 +61,9 @@ struct TcArgs {
     int bn;             // accumulator columns (MMA N)
     int n_valid;        // row length of the destination (Spad or Cpad)
     int passes;         // 1 BF16, 3 split BF16
+    int taps;           // T*T
+    int tap_inner;      // k-block order: 1 = (block, tap) tap fastest; 0 = (tap, block)
+    int chunk_kb;       // k-blocks per accumulation chunk (see below)
     uint32_t tx_bytes;  // bytes landing per stage
     float* out;
     int64_t slot_stride;
@@ -172,6 +182,7 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
             smem_u32(bar))
         : "memory");
 }
+// 32 lanes x 16 columns of 32-bit accumulator, one row per thread (no wait)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -180,7 +191,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_v4(float* p, const uint32_t* r) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+// element-wise FP32 add into global memory, performed at L2 (no return value)
+__device__ __forceinline__ void red_add_v4(float* p, const uint32_t* r) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(__uint_as_float(r[0])),
+                 "f"(__uint_as_float(r[1])), "f"(__uint_as_float(r[2])), "f"(__uint_as_float(r[3]))
+                 : "memory");
 }
 
 struct Unit {
@@ -252,7 +276,8 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 const int64_t m0 = (int64_t)w.mtile * kBM;
                 const int n0 = w.ntile * a.bn;
                 for (int kb = w.kb_lo; kb < w.kb_hi && ok; ++kb) {
-                    const int tap = kb / a.kb_per_tap, cb = kb % a.kb_per_tap;
+                    const int tap = a.tap_inner ? kb % a.taps : kb / a.kb_per_tap;
+                    const int cb = a.tap_inner ? kb / a.taps : kb % a.kb_per_tap;
                     const int Dy = tap / a.T - a.h, Dx = tap % a.T - a.h;
                     const int64_t off = (int64_t)Dy * a.Lp + Dx;
                     const int row = (int)(a.m_base + m0 + (FWD ? -off : off));
@@ -290,46 +315,50 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             // ---------------------------------------------------- MMA issuer --
             constexpr bool kBMn = !FWD;
             const uint32_t idesc = idesc_bf16(128, a.bn, kBMn);
-            int stage = 0, consumed = 0, ui = 0;
+            int stage = 0, consumed = 0, ci = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < a.n_units && ok; u += gridDim.x, ++ui) {
+            for (int u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
                 const Unit w = decode(a, u);
-                if (ui > 0 && !mbar_wait(acc_empty, (uint32_t)((ui - 1) & 1), abort_flag, a.err, 2)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                bool first = true;
-                for (int kb = w.kb_lo; kb < w.kb_hi && ok; ++kb) {
-                    for (int p = 0; p < a.passes; ++p) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 3)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
+                for (int c0 = w.kb_lo; c0 < w.kb_hi && ok; c0 += a.chunk_kb, ++ci) {
+                    const int c1 = min(w.kb_hi, c0 + a.chunk_kb);
+                    if (ci > 0 &&
+                        !mbar_wait(acc_empty, (uint32_t)((ci - 1) & 1), abort_flag, a.err, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    bool first = true;
+                    for (int kb = c0; kb < c1 && ok; ++kb) {
+                        for (int p = 0; p < a.passes; ++p) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 3)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
 #pragma unroll
-                        for (int ks = 0; ks < kBK / 16; ++ks) {
-                            const uint64_t bd = FWD ? sdesc(sB + ks * 32, 16, 1024)
-                                                    : sdesc(sB + ks * 2048, 8192, 1024);
+                            for (int ks = 0; ks < kBK / 16; ++ks) {
+                                const uint64_t bd = FWD ? sdesc(sB + ks * 32, 16, 1024)
+                                                        : sdesc(sB + ks * 2048, 8192, 1024);
 #pragma unroll
-                            for (int half = 0; half < 2; ++half) {
-                                const uint64_t ad = sdesc(sA + half * 16384 + ks * 32, 16, 1024);
-                                umma_bf16(tmem + half * 256, ad, bd, idesc,
-                                          (first && ks == 0) ? 0u : 1u);
+                                for (int half = 0; half < 2; ++half) {
+                                    const uint64_t ad = sdesc(sA + half * 16384 + ks * 32, 16, 1024);
+                                    umma_bf16(tmem + half * 256, ad, bd, idesc,
+                                              (first && ks == 0) ? 0u : 1u);
+                                }
+                            }
+                            first = false;
+                            umma_commit(&empty[stage]);
+                            *consumed_ctr = ++consumed;
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
                             }
                         }
-                        first = false;
-                        umma_commit(&empty[stage]);
-                        *consumed_ctr = ++consumed;
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
                     }
+                    if (ok) umma_commit(acc_full);
                 }
-                if (ok) umma_commit(acc_full);
             }
             // all MMAs issued by this thread complete before TMEM is freed
             umma_commit(mma_done);
@@ -339,30 +368,49 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         // ------------------------------------------------------- epilogue --
         const int lg = warp & 3;  // TMEM lane quarter this warp may access
         const int row = lg * 32 + lane;
-        int ui = 0;
-        for (int u = blockIdx.x; u < a.n_units; u += gridDim.x, ++ui) {
+        int ci = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
             const Unit w = decode(a, u);
-            if (!mbar_wait(acc_full, (uint32_t)(ui & 1), abort_flag, a.err, 4)) break;
-            tc_fence_after();
             float* outp = a.out + (int64_t)w.split * a.slot_stride;
-            for (int half = 0; half < 2; ++half) {
-                const int64_t m = (int64_t)w.mtile * kBM + half * 128 + row;
-                for (int c0 = 0; c0 < a.bn; c0 += 16) {
-                    uint32_t r[16];
-                    tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + half * 256 + c0, r);
-                    const int n = w.ntile * a.bn + c0;
-                    if (n < a.n_valid) {
-                        float4* dst = reinterpret_cast<float4*>(outp + m * a.n_valid + n);
+            for (int c0 = w.kb_lo; c0 < w.kb_hi; c0 += a.chunk_kb, ++ci) {
+                if (!mbar_wait(acc_full, (uint32_t)(ci & 1), abort_flag, a.err, 4)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                // the first chunk of a unit stores, later chunks add; each
+                // thread owns its row, so its adds reach a location in order
+                const bool first_chunk = c0 == w.kb_lo;
+                for (int half = 0; half < 2; ++half) {
+                    const int64_t m = (int64_t)w.mtile * kBM + half * 128 + row;
+                    float* orow = outp + m * a.n_valid + w.ntile * a.bn;
+                    const int ncols = min(a.bn, a.n_valid - w.ntile * a.bn);
+                    const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + half * 256;
+                    for (int cc = 0; cc < a.bn; cc += 32) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16(tbase + cc, r0);
+                        if (cc + 16 < a.bn) tmem_ld16(tbase + cc + 16, r1);
+                        tmem_wait_ld();
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                                 __uint_as_float(r[4 * q + 2]),
-                                                 __uint_as_float(r[4 * q + 3]));
+                            if (cc + 4 * q < ncols) {
+                                if (first_chunk) st_v4(orow + cc + 4 * q, r0 + 4 * q);
+                                else red_add_v4(orow + cc + 4 * q, r0 + 4 * q);
+                            }
+                        if (cc + 16 < a.bn) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (cc + 16 + 4 * q < ncols) {
+                                    if (first_chunk) st_v4(orow + cc + 16 + 4 * q, r1 + 4 * q);
+                                    else red_add_v4(orow + cc + 16 + 4 * q, r1 + 4 * q);
+                                }
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(acc_empty);
             }
-            tc_fence_before();
-            mbar_arrive(acc_empty);
         }
     }
 
@@ -502,6 +550,9 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         f.bn = g.Spad;
         f.n_valid = g.Spad;
         f.passes = split ? 3 : 1;
+        f.taps = (int)g.taps();
+        f.tap_inner = 1;
+        f.chunk_kb = kChainSteps / (4 * f.passes);
         f.tx_bytes = (uint32_t)(kABytes + kBK * 2 * g.Spad);
         f.out = ctx->Fwd;
         f.slot_stride = g.M_pad * g.Spad;
@@ -514,6 +565,7 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         b.nsplit = bwd_split_for(g, ctx->sm_count);
         b.n_units = b.n_mtiles * b.n_ntiles * b.nsplit;
         b.kb_per_tap = (g.Spad + kBK - 1) / kBK;
+        b.tap_inner = 0;
         b.kb_total = (int)(g.taps() * b.kb_per_tap);
         b.bn = bwd_bn(g);
         b.n_valid = g.Cpad;
