@@ -57,6 +57,7 @@ _SIGS = {
     "lfd_rl_iterate": (_I, [_VP, _VP, _VP, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
     "lfd_quality": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
+    "lfd_quality_mip_static": (_I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
     "lfd_destroy": (None, [_VP]),
     "lfd_last_error": (ctypes.c_char_p, [_VP]),
     "lfd_status_string": (ctypes.c_char_p, [_I]),
@@ -172,6 +173,17 @@ def lfd_quality(ctx, v, stream=None) -> float:
     e = _D(0)
     _check(load().lfd_quality(ctx, _ptr(v), ctypes.byref(e), _stream(stream)), ctx)
     return e.value
+
+
+def lfd_quality_mip_static(mip, H: int, W: int, XS: int, YS: int, l2_over_region: int,
+                           entropy_out, stream=None):
+    """Allocation-free DCT entropy of a device image ``mip`` [H][W]; the result is
+    written to ``entropy_out`` (a float64 CUDA tensor of one element, or an address)."""
+    out = entropy_out if isinstance(entropy_out, int) else entropy_out.data_ptr()
+    st = load().lfd_quality_mip_static(_ptr(mip), H, W, XS, YS, int(l2_over_region), out,
+                                       _stream(stream))
+    if st != LFD_OK:
+        raise LfdError(st, "lfd_quality_mip_static: %s" % lfd_status_string(st))
 
 
 def lfd_destroy(ctx):
