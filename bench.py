@@ -38,7 +38,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lfd", choices=["lfd", "reference"])
     p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
+    p.add_argument("--variant", default="fft", choices=["fft", "direct"])
     p.add_argument("--config", type=int, default=WORKLOAD_CFG)
+    p.add_argument("--depths", type=int, default=None,
+                   help="override the number of depths (small cases for profiler captures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-fp32-ref", action="store_true")
@@ -155,12 +158,19 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ inputs --
-def make_inputs(cfg: int):
-    """PSF, ground truth and the seeded parameters of the workload."""
+def make_inputs(cfg: int, depths=None):
+    """PSF, ground truth and the seeded parameters of the workload (optionally
+    with fewer depths, for small profiler cases)."""
+    import dataclasses
     from paper_2208_11422_gb300 import synth
     g = synth.CONFIGS[cfg]
-    psf = synth.make_psf(cfg)
-    vt = synth.ground_truth(cfg)
+    if depths:
+        g = dataclasses.replace(g, nz=depths, z_c=depths // 2,
+                                beads=max(1, g.beads * depths // g.nz),
+                                filaments=g.filaments * depths // g.nz,
+                                name=g.name + "_%dz" % depths)
+    psf = synth.make_psf(g)
+    vt = synth.ground_truth(g, seed=100 + cfg)
     return g, psf, vt
 
 
@@ -202,6 +212,57 @@ def cpu_baseline_sample(cfg: int, psf=None):
 
 
 # ---------------------------------------------------------------- GPU arm --
+PATH_NAMES = {("fft", "fp32"): "fft_fp32", ("direct", "bf16x3"): "direct_bf16x3",
+              ("direct", "bf16"): "direct_bf16", ("direct", "fp32"): "direct_fp32"}
+
+
+def fft_plan_numbers(g):
+    """The FFT tiling the library picks (same rule as fft_plan_for)."""
+    N, k = g.nnum, g.psf_lenslets
+    h = (k + 1) // 2
+    S, C = N * N, g.nz * N * N
+    L = g.lenslets
+    best = None
+    for F in (32, 64):
+        B = F - 2 * h
+        if B < 4:
+            continue
+        nt = math.ceil(L / B) ** 2
+        if nt > 16 or S > 256:
+            continue
+        bins = F * (F // 2 + 1)
+        Cf = (C + 3) // 4 * 4
+        spectra = bins * S * Cf * 8.0
+        if spectra > 96e9:
+            continue
+        flops = bins * S * nt * C * 8.0
+        t = max(spectra / 6.0e12, flops / 6.0e13)
+        if best is None or t < best[0]:
+            best = (t, F, bins, nt, Cf, S, C)
+    return best
+
+
+def time_path(lfd, torch, dev, psf_d, g, y_d, variant, precision, iters, warm, stream):
+    """RL iterations/s of one path; returns (it/s, stage times, final volume)."""
+    ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W,
+                         lfd.lfd_default_options(precision=precision, variant=variant))
+    try:
+        v = torch.ones((g.nz, g.H, g.W), device=dev)
+        if warm:
+            lfd.lfd_rl_iterate(ctx, y_d, v, warm)
+            v.fill_(1.0)
+        torch.cuda.synchronize()
+        lfd.lfd_set_profiling(ctx, True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lfd.lfd_rl_iterate(ctx, y_d, v, iters, False, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return iters / (a.elapsed_time(b) / 1e3), lfd.lfd_stage_times(ctx), v
+    finally:
+        lfd.lfd_destroy(ctx)
+
+
 def run_lfd(args, rank, world, local):
     import torch
     from paper_2208_11422_gb300 import build, lfd, synth
@@ -210,26 +271,25 @@ def run_lfd(args, rank, world, local):
     dev = torch.device("cuda", local)
     build.build()
     lfd.load()
-    prec = args.precision or "bf16x3"
+    variant = args.variant
+    prec = args.precision or ("fp32" if variant == "fft" else "bf16x3")
     steps = args.steps if args.steps is not None else 5
     warm = max(3, args.warmup)
-    g, psf, vt = make_inputs(args.config)
+    g, psf, vt = make_inputs(args.config, args.depths)
     psf_d = torch.from_numpy(psf).to(dev)
+    stream = torch.cuda.current_stream()
 
-    # data: y = Poisson(scale * H v_true) + background, H v_true by the FP32 path
-    ctx32 = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, lfd.lfd_default_options(precision="fp32"))
+    ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W,
+                         lfd.lfd_default_options(precision=prec, variant=variant))
+    # data: y = Poisson(scale * H v_true) + background; H v_true by this path's
+    # forward projection (an input for timing, never an expected value)
     vt_d = torch.from_numpy(vt.astype(np.float32)).to(dev)
     hv = torch.empty((g.H, g.W), device=dev)
-    lfd.lfd_forward(ctx32, vt_d, hv)
+    lfd.lfd_forward(ctx, vt_d, hv)
     torch.cuda.synchronize()
     y = synth.poisson_data(hv.cpu().numpy(), g.scale, g.background, 200 + args.config)
     del vt_d, hv
     y_d = torch.from_numpy(y).to(dev)
-
-    if prec == "fp32":
-        ctx = ctx32
-    else:
-        ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, lfd.lfd_default_options(precision=prec))
     v = torch.ones((g.nz, g.H, g.W), device=dev)
 
     # warm-up (untimed)
@@ -240,7 +300,6 @@ def run_lfd(args, rank, world, local):
     # device-resident timed region: one call of `steps` iterations
     lfd.lfd_set_profiling(ctx, True)
     launches0 = lfd.lfd_launch_count()
-    stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         dist_barrier(world)
@@ -256,6 +315,7 @@ def run_lfd(args, rank, world, local):
     lfd.lfd_set_profiling(ctx, False)
     tmax = dist_max(secs, world, dev)
     value = aggregate(steps, world, tmax)
+    v_head = v.clone()
 
     # end to end through the C ABI with pinned host buffers, one iteration per call
     e2e = None
@@ -274,60 +334,76 @@ def run_lfd(args, rank, world, local):
         e2e = {"value": aggregate(steps, world, t_e2e), "unit": "RL iterations/s",
                "h2d_bytes_per_step": int(y_h.numel() * 4 + v_h.numel() * 4),
                "d2h_bytes_per_step": int(v_h.numel() * 4)}
+        del y_h, v_h
+    lfd.lfd_destroy(ctx)
+    del v
 
-    # the plain FP32 GPU path on the same GPU (reported beside the tensor-core path)
-    fp32_ref = None
-    if prec != "fp32" and not args.skip_fp32_ref:
-        v32 = torch.ones((g.nz, g.H, g.W), device=dev)
-        lfd.lfd_rl_iterate(ctx32, y_d, v32, 1)
-        v32.fill_(1.0)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lfd.lfd_rl_iterate(ctx32, y_d, v32, 2, False, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fp32_ref = {"value": 2.0 / (a.elapsed_time(b) / 1e3), "unit": "RL iterations/s"}
-        del v32
-
-    # plain BF16 tensor-core path (reported beside the split-BF16 headline)
-    bf16_side = None
-    if prec == "bf16x3" and not args.skip_fp32_ref:
-        ctxb = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, lfd.lfd_default_options(precision="bf16"))
-        vb = torch.ones((g.nz, g.H, g.W), device=dev)
-        lfd.lfd_rl_iterate(ctxb, y_d, vb, 2)
-        vb.fill_(1.0)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lfd.lfd_rl_iterate(ctxb, y_d, vb, steps, False, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        bf16_side = {"value": steps / (a.elapsed_time(b) / 1e3), "unit": "RL iterations/s"}
-        lfd.lfd_destroy(ctxb)
-        del vb
+    # the other formulations and precisions on the same GPU and data, with the
+    # relative L2 distance of their v^steps from this path's
+    paths = {}
+    if not args.skip_fp32_ref:
+        for var, pr in (("fft", "fp32"), ("direct", "bf16x3"), ("direct", "bf16"), ("direct", "fp32")):
+            if (var, pr) == (variant, prec):
+                continue
+            n_it = 1 if (var, pr) == ("direct", "fp32") else steps
+            it_s, st_ms, vo = time_path(lfd, torch, dev, psf_d, g, y_d, var, pr, n_it,
+                                        0 if n_it == 1 else 2, stream)
+            rel = None
+            if n_it == steps:
+                rel = float(torch.linalg.vector_norm(vo - v_head) / torch.linalg.vector_norm(v_head))
+            paths[PATH_NAMES[(var, pr)]] = {
+                "value": it_s, "unit": "RL iterations/s", "iterations": n_it,
+                "forward_ms": st_ms[0], "backward_ms": st_ms[2],
+                "rel_l2_vs_headline_after_%d_iterations" % steps: rel}
+            del vo
+            torch.cuda.empty_cache()
 
     peaks, peak_src = measured_peaks()
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max clock
     fl = algorithmic_flops_per_projection(g)
-    fwd_ms, bwd_ms = stage[0], stage[2]
-    dom_ms = max(fwd_ms, bwd_ms)
-    dom = "forward projection" if fwd_ms >= bwd_ms else "backprojection"
-    if prec == "fp32":
-        smax = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * smax * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max clock
+    stage_names = ["forward", "ratio", "backward", "update", "metric", "forward_contraction",
+                   "backward_contraction", "fft_transforms"]
+    stage_ms = dict(zip(stage_names, stage))
+    if variant == "fft":
+        plan = fft_plan_numbers(g)
+        _, F, bins, nt, Cf, S, C = plan
+        cflops = 8.0 * bins * S * nt * C
+        cbytes = 8.0 * bins * S * Cf
+        dom_ms = max(stage[5], stage[6])
+        dom = "forward contraction" if stage[5] >= stage[6] else "backward contraction"
+        alu = cflops / (dom_ms / 1e3) / 1e12
+        hbm = cbytes / (dom_ms / 1e3) / 1e9
+        alu_frac, hbm_frac = alu / fp32_peak, hbm / peaks["hbm_gbs"]
+        if alu_frac >= hbm_frac:
+            roof = {"bound": "alu", "kernel": dom, "achieved": alu, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": alu_frac,
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %g MHz" % smax}
+        else:
+            roof = {"bound": "hbm", "kernel": dom, "achieved": hbm, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": hbm_frac, "peak_source": "hbm_gbs (%s)" % peak_src}
+        roof["other"] = {"hbm_GBps": hbm, "hbm_frac": hbm_frac, "alu_TFLOPs": alu, "alu_frac": alu_frac}
+        roof["algorithmic_per_launch"] = {"flops": cflops, "spectra_bytes": cbytes,
+                                          "F": F, "bins": bins, "tiles": nt}
+    elif prec == "fp32":
+        dom_ms = max(stage[0], stage[2])
+        dom = "forward projection" if stage[0] >= stage[2] else "backprojection"
         roof = {"bound": "alu", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x %g MHz" % smax}
+                "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x %g MHz" % smax}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     else:
+        dom_ms = max(stage[0], stage[2])
+        dom = "forward projection" if stage[0] >= stage[2] else "backprojection"
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "peak_source": "bf16_tflops_sustained (%s)" % peak_src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["stage_ms"] = {"forward": stage[0], "ratio": stage[1], "backward": stage[2],
-                        "update": stage[3], "metric": stage[4]}
+    roof["stage_ms"] = stage_ms
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.depths:
         it_s, dt, sample, cores = cpu_baseline_sample(args.config, psf)
         cpu = {"value": it_s, "unit": "RL iterations/s", "cores": cores, "kind": "oracle",
                "sample": sample}
@@ -340,17 +416,14 @@ def run_lfd(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
         "data": "synthetic (seeded beads + filaments, Poisson noise)",
-        "config": {"workload": synth.CONFIGS[args.config].name, "H": g.H, "W": g.W,
-                   "Nnum": g.nnum, "Nz": g.nz, "P": g.P, "precision": prec,
+        "config": {"workload": g.name, "H": g.H, "W": g.W,
+                   "Nnum": g.nnum, "Nz": g.nz, "P": g.P, "precision": prec, "variant": variant,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (volume %.2f GB)" % (g.nz * g.H * g.W * 4 / 1e9)},
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "roofline": roof, "cpu_baseline": cpu, "fp32_gpu": fp32_ref, "bf16_gpu": bf16_side,
+        "roofline": roof, "cpu_baseline": cpu, "paths": paths,
         "entropy": ent, "predicted_iteration": pred,
     }
-    lfd.lfd_destroy(ctx)
-    if ctx is not ctx32:
-        lfd.lfd_destroy(ctx32)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -78,7 +78,17 @@ typedef struct {
     int XS, YS;           /* region width / height; > 0 overrides the optics        */
     int l2_over_region;   /* 1: L2 norm of Eq. 12 over the region S (default);
                              0: over the whole DCT (= 2-norm of the MIP)            */
+    int variant;          /* projection formulation, lfd_variant                     */
 } lfd_options;
+
+/* How the two projections are computed (same results up to rounding). */
+typedef enum {
+    LFD_DIRECT = 0,  /* polyphase implicit GEMM: tcgen05 (BF16 precisions) or CUDA
+                        cores (FP32)                                                */
+    LFD_FFT = 1      /* overlap-save FFT on the lenslet grid with cached PSF spectra,
+                        FP32 transforms and FP32 complex contractions; precision
+                        must be LFD_FP32                                            */
+} lfd_variant;
 
 /* Fills *opt with the defaults listed above. */
 void lfd_default_options(lfd_options* opt);
@@ -193,12 +203,14 @@ uint64_t lfd_launch_count(void);
 
 /* Per-stage device time of lfd_rl_iterate iterations, in milliseconds, measured
  * with CUDA events recorded on the call's stream around each stage:
- * [0] forward projection, [1] split reduction + ratio, [2] backprojection,
- * [3] update + MIP + flux, [4] metric. lfd_set_profiling(ctx, 1) turns the
- * events on and resets the averages; lfd_stage_times returns the mean over
- * every iteration run since then (zeros if none). */
-lfd_status lfd_set_profiling(lfd_ctx* ctx, int on);
-lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms5);
+ * [0] forward projection (FFT variant: ratio included), [1] ratio (direct
+ * variant), [2] backprojection, [3] update + MIP + flux, [4] metric,
+ * [5] forward contraction kernel alone, [6] backward contraction kernel alone,
+ * [7] the FFT variant's transforms (0 for the direct variant).
+ * lfd_set_profiling(ctx, 1) turns the events on and resets the averages;
+ * lfd_stage_times writes the mean over every iteration run since then (zeros
+ * if none) into ms[0..n-1] (entries past 7 are 0). */
+lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n);
 
 #ifdef __cplusplus
 }

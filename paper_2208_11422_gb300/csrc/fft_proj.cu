@@ -1,0 +1,596 @@
+// FFT variant of the light-field projections (FP32 throughout).
+//
+// In polyphase form both projections are multi-channel 2-D convolutions on the
+// lenslet grid with kernels of T x T taps (lfd_internal.h):
+//   forward   Hv[s]   = sum_c  Wp[.][s][c]  (*)  V[c]      (convolution)
+//   backward  HtR[c]  = sum_s  Wp[.][s][c]  (x)  R[s]      (correlation)
+// Overlap-save on tiles: an F x F patch (F = 32 or 64) holds B = F - 2h valid
+// outputs per axis, so the grid is covered by tiles_y x tiles_x patches. Every
+// (s, c) kernel is transformed once (at context creation) into its F x (F/2+1)
+// half spectrum Wf[bin][s][c]. Per projection:
+//   1. R2C transform of every input channel's patch of every tile,
+//   2. per frequency bin a complex contraction over channels
+//        forward  Yh[bin][tile][s] = sum_c Wf[bin][s][c]       Xh[bin][tile][c]
+//        backward Xh[bin][tile][c] = sum_s conj(Wf[bin][s][c]) Yh[bin][tile][s]
+//   3. C2R transform of every output channel's patch; the valid window is
+//      [2h, F) for the convolution and [0, B) for the correlation.
+// The ratio r = y / (Hv + eps) is fused into the forward's C2R store.
+//
+// Transforms are radix-2 in shared memory, one warp per 1-D transform; the
+// contractions run on the CUDA cores in FP32, streaming the spectra once per
+// projection with every tile's accumulators in registers.
+#include <cmath>
+#include <vector>
+
+#include "fft_proj.h"
+
+namespace lfd {
+namespace {
+
+constexpr int kCPB = 4;  // channels per transform block
+
+__constant__ float2 c_tw[32];  // exp(-2 pi i k / 64), k < 32
+
+template <int F>
+struct FftSize {
+    static constexpr int LOG = F == 64 ? 6 : 5;
+    static constexpr int H2 = F / 2 + 1;
+    static constexpr int BINS = F * H2;
+};
+
+__device__ __forceinline__ int bitrev(int i, int log) { return (int)(__brev((unsigned)i) >> (32 - log)); }
+
+// in-place radix-2 FFT of F points in shared memory by one warp; input must
+// already be in bit-reversed order. INV uses conjugate twiddles (no scaling).
+template <int F, bool INV>
+__device__ __forceinline__ void warp_fft(float2* a) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int st = 1; st <= FftSize<F>::LOG; ++st) {
+        const int half = 1 << (st - 1);
+        const int len = half << 1;
+#pragma unroll
+        for (int b = lane; b < F / 2; b += 32) {
+            const int j = b & (half - 1);
+            const int i0 = (b >> (st - 1)) * len + j, i1 = i0 + half;
+            float2 w = c_tw[j * (64 / len)];
+            if (INV) w.y = -w.y;
+            const float2 u = a[i0], v = a[i1];
+            const float2 t = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            a[i0] = make_float2(u.x + t.x, u.y + t.y);
+            a[i1] = make_float2(u.x - t.x, u.y - t.y);
+        }
+        __syncwarp();
+    }
+}
+
+// channel-major images [nch][Ly][Lx]; patch of tile (ty, tx) starts at
+// lenslet (ty*B - h, tx*B - h), zero outside the grid
+struct ImgSrc {
+    const float* img;
+    int Ly, Lx, h, B, tiles_x;
+    __device__ float operator()(int c, int tile, int r, int x) const {
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        const int Iy = ty * B - h + r, Ix = tx * B - h + x;
+        return (Iy >= 0 && Iy < Ly && Ix >= 0 && Ix < Lx) ? img[((int64_t)c * Ly + Iy) * Lx + Ix] : 0.f;
+    }
+};
+
+// packed PSF Wp[T*T][Spad][Cpad] read as one T x T kernel per (s, c); the
+// "tile" index is s here, and tap (qy, qx) = (Dy + h, Dx + h)
+struct TapSrc {
+    const float* W;
+    int T, Spad, Cpad;
+    __device__ float operator()(int c, int s, int r, int x) const {
+        return (r < T && x < T) ? W[(((int64_t)(r * T + x)) * Spad + s) * Cpad + c] : 0.f;
+    }
+};
+
+// R2C 2-D transform of kCPB channels' patches of one tile.
+// out[(bin * ntile + tile) * ldc + c], bin = fy * (F/2+1) + fx.
+template <int F, class Src>
+__global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, int ntile,
+                                                 float2* __restrict__ out) {
+    constexpr int H2 = FftSize<F>::H2, LOG = FftSize<F>::LOG;
+    extern __shared__ float2 sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* spec = sm;                               // [kCPB][F][H2]
+    float2* scr = sm + kCPB * F * H2 + warp * F;     // per-warp [F]
+    const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    for (int job = warp; job < kCPB * F; job += 8) {  // rows
+        const int ch = job / F, r = job % F, c = c0 + ch;
+        for (int x = lane; x < F; x += 32)
+            scr[bitrev(x, LOG)] = make_float2(c < nch ? src(c, tile, r, x) : 0.f, 0.f);
+        __syncwarp();
+        warp_fft<F, false>(scr);
+        for (int k = lane; k < H2; k += 32) spec[(ch * F + r) * H2 + k] = scr[k];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int job = warp; job < kCPB * H2; job += 8) {  // columns
+        const int ch = job / H2, k = job % H2;
+        for (int r = lane; r < F; r += 32) scr[bitrev(r, LOG)] = spec[(ch * F + r) * H2 + k];
+        __syncwarp();
+        warp_fft<F, false>(scr);
+        for (int r = lane; r < F; r += 32) spec[(ch * F + r) * H2 + k] = scr[r];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
+        const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
+        if (c < ldc)
+            out[((int64_t)bin * ntile + tile) * ldc + c] =
+                c < nch ? spec[ch * F * H2 + bin] : make_float2(0.f, 0.f);
+    }
+}
+
+// forward output: Hv of polyphase channel s for lenslet (Iy, Ix); optionally
+// stored as an image [H][W] and / or turned into r = y / (Hv + eps)
+struct HvDst {
+    float* img;        // [H][W] or null
+    float* rcm;        // [S][Ly][Lx] ratio or null
+    const float* ycm;  // [S][Ly][Lx]
+    float eps;
+    int N, W, Ly, Lx, B, tiles_x;
+    __device__ void operator()(int s, int tile, int i, int j, float hv) const {
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        const int Iy = ty * B + i, Ix = tx * B + j;
+        if (Iy >= Ly || Ix >= Lx) return;
+        if (img) img[((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N] = hv;
+        if (rcm) {
+            const int64_t o = ((int64_t)s * Ly + Iy) * Lx + Ix;
+            const float den = hv + eps;
+            rcm[o] = den > 0.f ? ycm[o] / den : 0.f;
+        }
+    }
+};
+
+// backward output: H^T r of channel c = (z, t) for lenslet (Iy, Ix), into a
+// channel-major volume or a stack-order volume [Nz][H][W]
+struct VolDst {
+    float* cm;     // [C][Ly][Lx] or null
+    float* stack;  // [Nz][H][W] or null
+    int N, S, H, W, Ly, Lx, B, tiles_x;
+    __device__ void operator()(int c, int tile, int i, int j, float x) const {
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        const int Iy = ty * B + i, Ix = tx * B + j;
+        if (Iy >= Ly || Ix >= Lx) return;
+        if (cm) cm[((int64_t)c * Ly + Iy) * Lx + Ix] = x;
+        if (stack) {
+            const int z = c / S, t = c % S;
+            stack[((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
+        }
+    }
+};
+
+// C2R 2-D transform of kCPB channels of one tile; the rows / columns
+// [off, off + B) of the real result, times `scale`, go to dst.
+template <int F, class Dst>
+__global__ void __launch_bounds__(256) k_fft_c2r(const float2* __restrict__ in, int nch, int ldc,
+                                                 int ntile, int off, int B, float scale, Dst dst) {
+    constexpr int H2 = FftSize<F>::H2, LOG = FftSize<F>::LOG;
+    extern __shared__ float2 sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* spec = sm;
+    float2* scr = sm + kCPB * F * H2 + warp * F;
+    const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
+        const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
+        spec[ch * F * H2 + bin] =
+            c < nch ? in[((int64_t)bin * ntile + tile) * ldc + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int job = warp; job < kCPB * H2; job += 8) {  // columns: fy -> y
+        const int ch = job / H2, k = job % H2;
+        for (int r = lane; r < F; r += 32) scr[bitrev(r, LOG)] = spec[(ch * F + r) * H2 + k];
+        __syncwarp();
+        warp_fft<F, true>(scr);
+        for (int r = lane; r < F; r += 32) spec[(ch * F + r) * H2 + k] = scr[r];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int job = warp; job < kCPB * B; job += 8) {  // rows y in [off, off+B): fx -> x
+        const int ch = job / B, i = job % B, y = off + i, c = c0 + ch;
+        const float2* row = spec + (ch * F + y) * H2;
+        for (int x = lane; x < F; x += 32) {
+            float2 v;
+            if (x < H2) {
+                v = row[x];
+            } else {  // a real row has a conjugate-symmetric spectrum
+                v = row[F - x];
+                v.y = -v.y;
+            }
+            scr[bitrev(x, LOG)] = v;
+        }
+        __syncwarp();
+        warp_fft<F, true>(scr);
+        if (c < nch)
+            for (int j = lane; j < B; j += 32) dst(c, tile, i, j, scr[off + j].x * scale);
+        __syncwarp();
+    }
+}
+
+// forward contraction: Yh[bin][t][s] = sum_c Wf[bin][s][c] Xh[bin][t][c].
+// One block per bin, one thread per phase s holding all tiles (<= 16) in
+// registers. Each thread streams its own row of Wf straight from global memory
+// (32-byte loads, prefetched one step ahead); the tiles' spectra for the
+// current 64 channels are broadcast from shared memory.
+constexpr int kFC = 64;  // channels per shared-memory chunk
+template <int NT>
+__global__ void __launch_bounds__(256) k_contract_fwd(const float2* __restrict__ Wf,
+                                                      const float2* __restrict__ Xh,
+                                                      float2* __restrict__ Yh, int S, int Sf,
+                                                      int C, int Cf, int ntile) {
+    __shared__ __align__(16) float2 Xs[kFC][NT];
+    const int bin = blockIdx.x;
+    const int s = threadIdx.x;
+    const bool active = s < S;
+    const float2* wrow = Wf + ((int64_t)bin * S + (active ? s : 0)) * Cf;
+    const float2* Xb = Xh + (int64_t)bin * ntile * Cf;
+    float ar[NT], ai[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ar[t] = ai[t] = 0.f;
+    for (int k0 = 0; k0 < C; k0 += kFC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kFC * NT; e += blockDim.x) {
+            const int t = e / kFC, k = e % kFC, c = k0 + k;
+            Xs[k][t] = (t < ntile && c < C) ? Xb[(int64_t)t * Cf + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (!active) continue;
+        const int kn = min(kFC, C - k0);
+        float4 w01 = make_float4(0.f, 0.f, 0.f, 0.f), w23 = w01;
+        if (kn >= 4) {
+            w01 = *reinterpret_cast<const float4*>(wrow + k0);
+            w23 = *reinterpret_cast<const float4*>(wrow + k0 + 2);
+        }
+        for (int k = 0; k < kn; k += 4) {
+            float4 n01 = make_float4(0.f, 0.f, 0.f, 0.f), n23 = n01;
+            if (k + 8 <= kn) {  // prefetch the next 4 channels
+                n01 = *reinterpret_cast<const float4*>(wrow + k0 + k + 4);
+                n23 = *reinterpret_cast<const float4*>(wrow + k0 + k + 6);
+            }
+            float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
+                           make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+            if (k + 4 > kn) {  // ragged end of C (C % 4 != 0)
+                for (int q = 0; q < 4; ++q)
+                    w[q] = k + q < kn ? wrow[k0 + k + q] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const float2 x = Xs[k + q][t];
+                    ar[t] = fmaf(w[q].x, x.x, fmaf(-w[q].y, x.y, ar[t]));
+                    ai[t] = fmaf(w[q].x, x.y, fmaf(w[q].y, x.x, ai[t]));
+                }
+            }
+            w01 = n01;
+            w23 = n23;
+        }
+    }
+    if (!active) return;
+    float2* Yb = Yh + (int64_t)bin * ntile * Sf;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+        if (t < ntile) Yb[(int64_t)t * Sf + s] = make_float2(ar[t], ai[t]);
+}
+
+// backward contraction: Xh[bin][t][c] = sum_s conj(Wf[bin][s][c]) Yh[bin][t][s].
+// One block per (bin, 512 channels), two channels per thread, all tiles in
+// registers; Wf rows are read coalesced, Yh[bin] sits in shared memory.
+template <int NT>
+__global__ void __launch_bounds__(256) k_contract_adj(const float2* __restrict__ Wf,
+                                                      const float2* __restrict__ Yh,
+                                                      float2* __restrict__ Xh, int S, int Sf,
+                                                      int C, int Cf, int ntile) {
+    extern __shared__ float2 Ys[];  // [S][NT]
+    const int bin = blockIdx.x;
+    const int c = blockIdx.y * 512 + 2 * threadIdx.x;
+    const float2* Wb = Wf + (int64_t)bin * S * Cf;
+    const float2* Yb = Yh + (int64_t)bin * ntile * Sf;
+    for (int e = threadIdx.x; e < S * NT; e += blockDim.x) {
+        const int sidx = e / NT, t = e % NT;
+        Ys[e] = t < ntile ? Yb[(int64_t)t * Sf + sidx] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (c >= Cf) return;
+    float ar0[NT], ai0[NT], ar1[NT], ai1[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ar0[t] = ai0[t] = ar1[t] = ai1[t] = 0.f;
+    float4 w = *reinterpret_cast<const float4*>(Wb + c);
+    for (int sidx = 0; sidx < S; ++sidx) {
+        float4 wn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sidx + 1 < S) wn = *reinterpret_cast<const float4*>(Wb + (int64_t)(sidx + 1) * Cf + c);
+        const float2* yrow = Ys + sidx * NT;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {  // conj(w) * y
+            const float2 y = yrow[t];
+            ar0[t] = fmaf(w.x, y.x, fmaf(w.y, y.y, ar0[t]));
+            ai0[t] = fmaf(w.x, y.y, fmaf(-w.y, y.x, ai0[t]));
+            ar1[t] = fmaf(w.z, y.x, fmaf(w.w, y.y, ar1[t]));
+            ai1[t] = fmaf(w.z, y.y, fmaf(-w.w, y.x, ai1[t]));
+        }
+        w = wn;
+    }
+    float2* Xb = Xh + (int64_t)bin * ntile * Cf;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+        if (t < ntile)
+            *reinterpret_cast<float4*>(Xb + (int64_t)t * Cf + c) = make_float4(ar0[t], ai0[t], ar1[t], ai1[t]);
+}
+
+template <int NT>
+cudaError_t run_contract_fwd(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Xh,
+                             float2* Yh, cudaStream_t st) {
+    k_contract_fwd<NT><<<p.bins, 256, 0, st>>>(Wf, Xh, Yh, g.S, p.Sf, g.C, p.Cf, p.ntile);
+    count_launch();
+    return cudaGetLastError();
+}
+template <int NT>
+cudaError_t run_contract_adj(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Yh,
+                             float2* Xh, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * (size_t)g.S * NT;
+    cudaError_t e = cudaFuncSetAttribute(k_contract_adj<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)p.bins, (unsigned)((p.Cf + 511) / 512));
+    k_contract_adj<NT><<<grid, 256, smem, st>>>(Wf, Yh, Xh, g.S, p.Sf, g.C, p.Cf, p.ntile);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ layout and update kernels --
+// v[z][Iy*N+ty][Ix*N+tx] -> vcm[z*S + ty*N + tx][Iy][Ix]
+__global__ void k_poly_volume_cm(const float* __restrict__ v, Geo g, float* __restrict__ vcm) {
+    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.C * L2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / L2);
+        const int64_t l = e % L2;
+        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+        const int z = c / g.S, t = c % g.S;
+        vcm[e] = v[((int64_t)z * g.H + (int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N];
+    }
+}
+__global__ void k_depoly_volume_cm(const float* __restrict__ vcm, Geo g, float* __restrict__ v) {
+    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.C * L2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / L2);
+        const int64_t l = e % L2;
+        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+        const int z = c / g.S, t = c % g.S;
+        v[((int64_t)z * g.H + (int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N] = vcm[e];
+    }
+}
+// y[Iy*N+sy][Ix*N+sx] -> ycm[sy*N + sx][Iy][Ix]
+__global__ void k_poly_image_cm(const float* __restrict__ y, Geo g, float* __restrict__ ycm) {
+    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.S * L2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / L2);
+        const int64_t l = e % L2;
+        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+        ycm[e] = y[((int64_t)Iy * g.N + s / g.N) * g.W + (int64_t)Ix * g.N + s % g.N];
+    }
+}
+__global__ void k_fill_cm(float* __restrict__ p, int64_t n, float val) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = val;
+}
+__global__ void k_inv_cm(const float* __restrict__ x, int64_t n, float* __restrict__ inv) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        inv[e] = x[e] > 0.f ? 1.0f / x[e] : 0.f;
+}
+
+// RL update on channel-major volumes; thread per (phase t, lenslet), walking
+// the depths: v_new = max(0, v * x * inv) (NaN -> 0, 0 where H^T 1 = 0), the
+// z-maximum of v_new for its pixel, and the FP64 flux sum(v * x) where H^T 1 > 0.
+__global__ void __launch_bounds__(256) k_update_cm(const float* __restrict__ vin, float* __restrict__ vout,
+                                                   const float* __restrict__ x, const float* __restrict__ inv,
+                                                   Geo g, float* __restrict__ mip,
+                                                   double* __restrict__ flux_part) {
+    __shared__ double red[8];
+    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.S * L2;
+    double flux = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / L2);
+        const int64_t l = e % L2;
+        float mx = 0.f;
+#pragma unroll 4
+        for (int z = 0; z < g.Nz; ++z) {
+            const int64_t o = (int64_t)(z * g.S + t) * L2 + l;
+            const float iv = inv[o], vo = vin[o];
+            float vn = 0.f;
+            if (iv > 0.f) {
+                const float vx = vo * x[o];
+                vn = vx * iv;
+                flux += (double)vx;
+            }
+            vn = vn > 0.f ? vn : 0.f;
+            vout[o] = vn;
+            mx = fmaxf(mx, vn);
+        }
+        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+        mip[((int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N] = mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = flux;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double f = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) f += red[i];
+        flux_part[blockIdx.x] = f;
+    }
+}
+
+inline int grid_for(int64_t n, int cap = 152 * 16) {
+    int64_t b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+template <int F>
+size_t fft_smem() {
+    return sizeof(float2) * ((size_t)kCPB * F * FftSize<F>::H2 + 8 * F);
+}
+
+bool g_tw_ready[64] = {};
+
+cudaError_t upload_twiddles() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && g_tw_ready[dev]) return cudaSuccess;
+    float2 tw[32];
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < 32; ++k)
+        tw[k] = make_float2((float)std::cos(2.0 * pi * k / 64.0), (float)-std::sin(2.0 * pi * k / 64.0));
+    e = cudaMemcpyToSymbol(c_tw, tw, sizeof(tw));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_tw_ready[dev] = true;
+    return e;
+}
+
+template <int F, class Src>
+cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, float2* out, cudaStream_t st) {
+    const size_t smem = fft_smem<F>();
+    cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)ntile, (unsigned)((ldc + kCPB - 1) / kCPB));
+    k_fft_r2c<F, Src><<<grid, 256, smem, st>>>(src, nch, ldc, ntile, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int F, class Dst>
+cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
+                    cudaStream_t st) {
+    const size_t smem = fft_smem<F>();
+    cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)ntile, (unsigned)((nch + kCPB - 1) / kCPB));
+    k_fft_c2r<F, Dst><<<grid, 256, smem, st>>>(in, nch, ldc, ntile, off, B, 1.0f / (F * F), dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan --
+bool fft_plan_for(const Geo& g, FftPlan* p) {
+    FftPlan best{};
+    double best_t = 1e300;
+    for (int F : {32, 64}) {
+        const int B = F - 2 * g.h;
+        if (B < 4) continue;
+        FftPlan q{};
+        q.F = F;
+        q.B = B;
+        q.h = g.h;
+        q.tiles_y = (g.Ly + B - 1) / B;
+        q.tiles_x = (g.Lx + B - 1) / B;
+        q.ntile = q.tiles_y * q.tiles_x;
+        if (q.ntile > 16) continue;
+        if (g.S > 256) continue;  // one thread per phase in the forward contraction
+        q.bins = F * (F / 2 + 1);
+        q.Cf = (g.C + 3) & ~3;
+        q.Sf = (g.S + 3) & ~3;
+        const double spectra = (double)q.bins * g.S * q.Cf * 8.0;
+        if (spectra > 96e9) continue;  // keep the cached spectra well inside HBM
+        const double flops = (double)q.bins * g.S * q.ntile * g.C * 8.0;
+        const double t = std::max(spectra / 6.0e12, flops / 6.0e13);
+        if (t < best_t) {
+            best_t = t;
+            best = q;
+        }
+    }
+    if (best.F == 0) return false;
+    *p = best;
+    return true;
+}
+
+// -------------------------------------------------------------- launchers --
+cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* Wf, cudaStream_t st) {
+    cudaError_t e = upload_twiddles();
+    if (e != cudaSuccess) return e;
+    TapSrc src{W32, g.T, g.Spad, g.Cpad};
+    // "tiles" = phases s, channels = c: output Wf[bin][s][c] with row length Cf
+    if (p.F == 64) return run_r2c<64>(src, g.C, p.Cf, g.S, Wf, st);
+    return run_r2c<32>(src, g.C, p.Cf, g.S, Wf, st);
+}
+
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
+                        float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
+                        float eps, cudaStream_t st, cudaEvent_t* ev) {
+    ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
+    cudaError_t e = p.F == 64 ? run_r2c<64>(src, g.C, p.Cf, p.ntile, Xh, st)
+                              : run_r2c<32>(src, g.C, p.Cf, p.ntile, Xh, st);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    if (p.ntile <= 1) e = run_contract_fwd<1>(p, g, Wf, Xh, Yh, st);
+    else if (p.ntile <= 4) e = run_contract_fwd<4>(p, g, Wf, Xh, Yh, st);
+    else if (p.ntile <= 9) e = run_contract_fwd<9>(p, g, Wf, Xh, Yh, st);
+    else e = run_contract_fwd<16>(p, g, Wf, Xh, Yh, st);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    HvDst dst{img_out, rcm, ycm, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
+    return p.F == 64 ? run_c2r<64>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st);
+}
+
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const float2* Wf, const float* rcm,
+                         float2* Xh, float2* Yh, float* xcm, float* stack_out, cudaStream_t st,
+                         cudaEvent_t* ev) {
+    ImgSrc src{rcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
+    cudaError_t e = p.F == 64 ? run_r2c<64>(src, g.S, p.Sf, p.ntile, Yh, st)
+                              : run_r2c<32>(src, g.S, p.Sf, p.ntile, Yh, st);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    if (p.ntile <= 1) e = run_contract_adj<1>(p, g, Wf, Yh, Xh, st);
+    else if (p.ntile <= 4) e = run_contract_adj<4>(p, g, Wf, Yh, Xh, st);
+    else if (p.ntile <= 9) e = run_contract_adj<9>(p, g, Wf, Yh, Xh, st);
+    else e = run_contract_adj<16>(p, g, Wf, Yh, Xh, st);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
+    return p.F == 64 ? run_c2r<64>(Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st)
+                     : run_c2r<32>(Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st);
+}
+
+cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st) {
+    k_poly_volume_cm<<<grid_for((int64_t)g.C * g.Ly * g.Lx), 256, 0, st>>>(v, g, vcm);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cudaStream_t st) {
+    k_depoly_volume_cm<<<grid_for((int64_t)g.C * g.Ly * g.Lx), 256, 0, st>>>(vcm, g, v);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_poly_image_cm(const float* y, const Geo& g, float* ycm, cudaStream_t st) {
+    k_poly_image_cm<<<grid_for((int64_t)g.S * g.Ly * g.Lx), 256, 0, st>>>(y, g, ycm);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_cm(float* p, int64_t n, float val, cudaStream_t st) {
+    k_fill_cm<<<grid_for(n), 256, 0, st>>>(p, n, val);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st) {
+    k_inv_cm<<<grid_for(n), 256, 0, st>>>(x, n, inv);
+    count_launch();
+    return cudaGetLastError();
+}
+int update_cm_blocks(const Geo& g) { return grid_for((int64_t)g.S * g.Ly * g.Lx, 4096); }
+cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
+                             const Geo& g, float* mip, double* flux_part, cudaStream_t st) {
+    k_update_cm<<<update_cm_blocks(g), 256, 0, st>>>(vin, vout, x, inv, g, mip, flux_part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lfd

@@ -1,0 +1,43 @@
+// FFT (overlap-save) variant of the projections: interface used by lfd_api.cu.
+#pragma once
+#include "lfd_internal.h"
+
+namespace lfd {
+
+struct FftPlan {
+    int F = 0;          // transform size per axis (32 or 64)
+    int B = 0;          // valid outputs per tile and axis, F - 2h
+    int h = 0;          // tap halo
+    int tiles_y = 0, tiles_x = 0, ntile = 0;
+    int bins = 0;       // F * (F/2 + 1)
+    int Cf = 0, Sf = 0; // channel / phase counts padded to 4 (row lengths of the spectra)
+};
+
+// picks F by a bandwidth / FP32 cost model; false if no plan fits (> 16 tiles,
+// spectra too large, or more than 225 phases)
+bool fft_plan_for(const Geo& g, FftPlan* p);
+
+// Wf[bin][s][Cf] = half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad])
+cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* Wf, cudaStream_t st);
+// ev (may be null): two events recorded after the transform and after the
+// contraction, for per-kernel timing.
+// forward projection of the channel-major volume vcm [C][Ly][Lx]; writes the
+// image Hv to img_out [H][W] and / or r = y / (Hv + eps) to rcm [S][Ly][Lx]
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
+                        float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
+                        float eps, cudaStream_t st, cudaEvent_t* ev);
+// backprojection of rcm [S][Ly][Lx] into xcm [C][Ly][Lx] and / or a stack-order volume
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const float2* Wf, const float* rcm,
+                         float2* Xh, float2* Yh, float* xcm, float* stack_out, cudaStream_t st,
+                         cudaEvent_t* ev);
+
+cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st);
+cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cudaStream_t st);
+cudaError_t launch_poly_image_cm(const float* y, const Geo& g, float* ycm, cudaStream_t st);
+cudaError_t launch_fill_cm(float* p, int64_t n, float val, cudaStream_t st);
+cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st);
+int update_cm_blocks(const Geo& g);
+cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
+                             const Geo& g, float* mip, double* flux_part, cudaStream_t st);
+
+}  // namespace lfd

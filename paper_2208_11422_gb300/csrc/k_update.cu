@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) k_update(
     double flux = 0.0;
     for (int t = threadIdx.x; t < g.S; t += blockDim.x) {
         float mx = 0.f;
+#pragma unroll 4
         for (int z = 0; z < g.Nz; ++z) {
             const int c = z * g.S + t;
             float x = parts[orow + c];

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lfd_internal.h"
+#include "fft_proj.h"
 #include "tc_gemm.h"
 
 using namespace lfd;
@@ -151,7 +152,9 @@ void free_all(lfd_ctx* ctx) {
     void* ptrs[] = {ctx->W32, ctx->Wb[0], ctx->Wb[1], ctx->Vp32[0], ctx->Vp32[1], ctx->Vpb[0],
                     ctx->Vpb[1], ctx->Rp32, ctx->Rpb[0], ctx->Rpb[1], ctx->Fwd, ctx->Bwd,
                     ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
-                    ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img};
+                    ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
+                    ctx->Wf, ctx->Xh, ctx->Yh, ctx->Vcm[0], ctx->Vcm[1], ctx->Rcm, ctx->Xcm,
+                    ctx->invcm, ctx->ycm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -159,6 +162,8 @@ void free_all(lfd_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     ctx->prof.ev.clear();
     tc_destroy(ctx);
+    delete static_cast<FftPlan*>(ctx->fft);
+    ctx->fft = nullptr;
 }
 
 std::vector<double> dct_table(int n, int Z) {
@@ -188,6 +193,7 @@ void lfd_default_options(lfd_options* opt) {
     opt->XS = 0;
     opt->YS = 0;
     opt->l2_over_region = 1;
+    opt->variant = LFD_DIRECT;
 }
 
 lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q, double NA,
@@ -257,6 +263,8 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (opt.precision < LFD_FP32 || opt.precision > LFD_BF16X3 || opt.precision == LFD_TF32)
         return LFD_EINVAL;
     if (!(opt.eps >= 0.f)) return LFD_EINVAL;
+    if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
+    if (opt.variant == LFD_FFT && opt.precision != LFD_FP32) return LFD_EINVAL;
     int XS = opt.XS, YS = opt.YS;
     if (XS <= 0 || YS <= 0) {
         if (lfd_region_size(Nnum, H, W, opt.dML_um, opt.Q, opt.NA, opt.lambda_um, &XS, &YS) != LFD_OK)
@@ -307,27 +315,51 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         }
     }
 
+    const bool fft = ctx->opt.variant == LFD_FFT;
+    FftPlan fplan{};
+    if (fft) {
+        if (!fft_plan_for(g, &fplan)) {
+            ctx->err = "no FFT tiling fits this geometry (at most 16 tiles of 64 x 64, Nnum <= 15)";
+            return bail(LFD_EUNSUPPORTED);
+        }
+        FftPlan* hp = new (std::nothrow) FftPlan(fplan);
+        if (!hp) return bail(LFD_ENOMEM);
+        ctx->fft = hp;
+    }
     ctx->fwd_splits = simt_fwd_splits(g, ctx->sm_count);
     ctx->bwd_splits = simt_bwd_splits(g, ctx->sm_count);
-    // Hv partials serve both the SIMT path and the tensor-core path
-    const int fparts = std::max(ctx->fwd_splits, uses_tc(ctx) ? tc_forward_parts_for(g, ctx->sm_count) : 1);
-    const int bparts = std::max(ctx->bwd_splits, uses_tc(ctx) ? tc_backward_parts_for(g, ctx->sm_count) : 1);
-
     const int64_t wcount = g.taps() * g.Spad * (int64_t)g.Cpad;
     CREATE_TRY(dalloc(ctx, &ctx->W32, wcount, false));
-    for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vp32[b], g.rows * g.Cpad, true));
-    CREATE_TRY(dalloc(ctx, &ctx->Rp32, g.rows * g.Spad, true));
-    CREATE_TRY(dalloc(ctx, &ctx->Fwd, (int64_t)fparts * g.M_pad * g.Spad, true));
-    CREATE_TRY(dalloc(ctx, &ctx->Bwd, (int64_t)bparts * g.M_pad * g.Cpad, true));
-    CREATE_TRY(dalloc(ctx, &ctx->invHt1, g.M_pad * g.Cpad, true));
-    CREATE_TRY(dalloc(ctx, &ctx->ypoly, g.M_pad * g.Spad, true));
-    if (uses_tc(ctx)) {
-        const int nb = uses_lo(ctx) ? 2 : 1;
-        for (int b = 0; b < nb; ++b) {
-            CREATE_TRY(dalloc(ctx, &ctx->Wb[b], wcount, false));
-            CREATE_TRY(dalloc(ctx, &ctx->Vpb[b], g.rows * g.Cpad, true));
-            CREATE_TRY(dalloc(ctx, &ctx->Rpb[b], g.rows * g.Spad, true));
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    if (fft) {
+        CREATE_TRY(dalloc(ctx, &ctx->Wf, (int64_t)fplan.bins * g.S * fplan.Cf, false));
+        CREATE_TRY(dalloc(ctx, &ctx->Xh, (int64_t)fplan.bins * fplan.ntile * fplan.Cf, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Yh, (int64_t)fplan.bins * fplan.ntile * fplan.Sf, true));
+        for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vcm[b], (int64_t)g.C * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Rcm, (int64_t)g.S * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Xcm, (int64_t)g.C * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->invcm, (int64_t)g.C * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->ycm, (int64_t)g.S * L2, true));
+        ctx->nflux = update_cm_blocks(g);
+    } else {
+        // Hv partials serve both the SIMT path and the tensor-core path
+        const int fparts = std::max(ctx->fwd_splits, uses_tc(ctx) ? tc_forward_parts_for(g, ctx->sm_count) : 1);
+        const int bparts = std::max(ctx->bwd_splits, uses_tc(ctx) ? tc_backward_parts_for(g, ctx->sm_count) : 1);
+        for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vp32[b], g.rows * g.Cpad, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Rp32, g.rows * g.Spad, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Fwd, (int64_t)fparts * g.M_pad * g.Spad, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Bwd, (int64_t)bparts * g.M_pad * g.Cpad, true));
+        CREATE_TRY(dalloc(ctx, &ctx->invHt1, g.M_pad * g.Cpad, true));
+        CREATE_TRY(dalloc(ctx, &ctx->ypoly, g.M_pad * g.Spad, true));
+        if (uses_tc(ctx)) {
+            const int nb = uses_lo(ctx) ? 2 : 1;
+            for (int b = 0; b < nb; ++b) {
+                CREATE_TRY(dalloc(ctx, &ctx->Wb[b], wcount, false));
+                CREATE_TRY(dalloc(ctx, &ctx->Vpb[b], g.rows * g.Cpad, true));
+                CREATE_TRY(dalloc(ctx, &ctx->Rpb[b], g.rows * g.Spad, true));
+            }
         }
+        ctx->nflux = g.Ly * g.Lx;
     }
     CREATE_TRY(dalloc(ctx, &ctx->mip, (int64_t)g.H * g.W, true));
     CREATE_TRY(dalloc(ctx, &ctx->cosW, (int64_t)XS * g.W, false));
@@ -335,7 +367,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     CREATE_TRY(dalloc(ctx, &ctx->G, (int64_t)g.H * XS, true));
     CREATE_TRY(dalloc(ctx, &ctx->rowE2, (int64_t)g.H, true));
     CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)XS * YS, true));
-    CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)g.Ly * g.Lx, true));
+    CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)std::max<int64_t>(ctx->nflux, L2), true));
     ctx->hist_cap = 64;
     CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * ctx->hist_cap, true));
     CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned, 4 * sizeof(double)));
@@ -359,12 +391,24 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (psf_tmp) cudaFree(psf_tmp);
     CREATE_CK(e);
 
-    // H^T 1 (FP32 path) and its reciprocal
-    CREATE_TRY(ensure_stage(ctx, false));
-    CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
-    CREATE_CK(launch_poly_image(ctx->stage_img, g, ctx->Rp32, g.m_base, nullptr, nullptr, st));
-    CREATE_TRY(run_backward(ctx, st, /*force_fp32=*/true));
-    CREATE_CK(launch_inv_ht1(ctx->Bwd, ctx->bwd_splits, g, ctx->invHt1, st));
+    if (fft) {
+        // PSF spectra, then H^T 1 by the FFT backprojection of ones
+        CREATE_CK(fft_init(fplan, g, ctx->W32, ctx->Wf, st));
+        CREATE_CK(launch_fill_cm(ctx->Rcm, (int64_t)g.S * L2, 1.0f, st));
+        CREATE_CK(fft_backward(fplan, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st, nullptr));
+        CREATE_CK(launch_inv_cm(ctx->Xcm, (int64_t)g.C * L2, ctx->invcm, st));
+        CREATE_CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->W32);  // the FFT variant reads only the spectra
+        ctx->device_bytes -= wcount * (int64_t)sizeof(float);
+        ctx->W32 = nullptr;
+    } else {
+        // H^T 1 (FP32 path) and its reciprocal
+        CREATE_TRY(ensure_stage(ctx, false));
+        CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
+        CREATE_CK(launch_poly_image(ctx->stage_img, g, ctx->Rp32, g.m_base, nullptr, nullptr, st));
+        CREATE_TRY(run_backward(ctx, st, /*force_fp32=*/true));
+        CREATE_CK(launch_inv_ht1(ctx->Bwd, ctx->bwd_splits, g, ctx->invHt1, st));
+    }
 
     // metric tables (Eqs. 2-4), FP64 on the host
     {
@@ -420,14 +464,21 @@ lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_st
         LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
         vd = ctx->stage_vol;
     }
-    LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
-    LFD_TRY(run_forward(ctx, 0, st));
     float* yd = y_out;
     if (!ydev) {
         LFD_TRY(ensure_stage(ctx, false));
         yd = ctx->stage_img;
     }
-    LFD_CK(launch_fwd_finish_image(ctx->Fwd, fwd_parts(ctx), g, yd, st));
+    if (ctx->fft) {
+        const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
+        LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
+        LFD_CK(fft_forward(fp, g, ctx->Wf, ctx->Vcm[0], ctx->Xh, ctx->Yh, yd, nullptr, nullptr, 0.f, st,
+                           nullptr));
+    } else {
+        LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
+        LFD_TRY(run_forward(ctx, 0, st));
+        LFD_CK(launch_fwd_finish_image(ctx->Fwd, fwd_parts(ctx), g, yd, st));
+    }
     if (!ydev) {
         LFD_CK(cudaMemcpyAsync(y_out, yd, nimg * sizeof(float), cudaMemcpyDeviceToHost, st));
         LFD_CK(cudaStreamSynchronize(st));
@@ -451,14 +502,20 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
         LFD_CK(cudaMemcpyAsync(ctx->stage_img, r, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
         rd = ctx->stage_img;
     }
-    LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
-    LFD_TRY(run_backward(ctx, st));
     float* vd = v_out;
     if (!vdev) {
         LFD_TRY(ensure_stage(ctx, true));
         vd = ctx->stage_vol;
     }
-    LFD_CK(launch_sum_depoly_volume(ctx->Bwd, bwd_parts(ctx), g, vd, st));
+    if (ctx->fft) {
+        const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
+        LFD_CK(launch_poly_image_cm(rd, g, ctx->Rcm, st));
+        LFD_CK(fft_backward(fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, nullptr, vd, st, nullptr));
+    } else {
+        LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
+        LFD_TRY(run_backward(ctx, st));
+        LFD_CK(launch_sum_depoly_volume(ctx->Bwd, bwd_parts(ctx), g, vd, st));
+    }
     if (!vdev) {
         LFD_CK(cudaMemcpyAsync(v_out, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
         LFD_CK(cudaStreamSynchronize(st));
@@ -474,10 +531,11 @@ lfd_status lfd_set_profiling(lfd_ctx* ctx, int on) {
     return LFD_OK;
 }
 
-lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms5) {
-    if (!ctx || !ms5) return LFD_EINVAL;
-    for (int i = 0; i < 5; ++i)
-        ms5[i] = ctx->prof.count ? (float)(ctx->prof.sum_ms[i] / ctx->prof.count) : 0.f;
+lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n) {
+    if (!ctx || !ms || n < 0) return LFD_EINVAL;
+    for (int i = 0; i < n && i < 8; ++i)
+        ms[i] = ctx->prof.count ? (float)(ctx->prof.sum_ms[i] / ctx->prof.count) : 0.f;
+    for (int i = 8; i < n; ++i) ms[i] = 0.f;
     return LFD_OK;
 }
 
@@ -511,41 +569,66 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
         vd = ctx->stage_vol;
     }
-    LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
+    const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
     int cur = 0;
-    LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
+    if (fp) {
+        LFD_CK(launch_poly_image_cm(yd, g, ctx->ycm, st));
+        LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[cur], st));
+    } else {
+        LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
+        LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
+    }
 
     const bool prof = ctx->prof.on;
-    if (prof && ctx->prof.ev.size() < 6 * (size_t)n) {
+    constexpr int kEv = 9;  // events per iteration (see lfd_stage_times)
+    if (prof && ctx->prof.ev.size() < kEv * (size_t)n) {
         const size_t old = ctx->prof.ev.size();
-        ctx->prof.ev.resize(6 * (size_t)n, nullptr);
+        ctx->prof.ev.resize(kEv * (size_t)n, nullptr);
         for (size_t i = old; i < ctx->prof.ev.size(); ++i) LFD_CK(cudaEventCreate(&ctx->prof.ev[i]));
     }
     cudaEvent_t* ev = prof ? ctx->prof.ev.data() : nullptr;
     std::vector<double> E;
     int ran = 0;
     bool stopped = false;
-    const int fp = fwd_parts(ctx), bp = bwd_parts(ctx);
+    const int fpart = fp ? 1 : fwd_parts(ctx), bp = fp ? 1 : bwd_parts(ctx);
     __nv_bfloat16* rhi = uses_tc(ctx) ? ctx->Rpb[0] : nullptr;
     __nv_bfloat16* rlo = uses_lo(ctx) ? ctx->Rpb[1] : nullptr;
     __nv_bfloat16* vhi = uses_tc(ctx) ? ctx->Vpb[0] : nullptr;
     __nv_bfloat16* vlo = uses_lo(ctx) ? ctx->Vpb[1] : nullptr;
     for (int k = 0; k < n; ++k) {
         const int nxt = cur ^ 1;
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 0], st));
-        LFD_TRY(run_forward(ctx, cur, st));
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 1], st));
-        LFD_CK(launch_fwd_finish_ratio(ctx->Fwd, fp, ctx->ypoly, ctx->opt.eps, g, ctx->Rp32, rhi, rlo, st));
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 2], st));
-        LFD_TRY(run_backward(ctx, st));
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 3], st));
-        LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
-                             ctx->mip, ctx->flux_part, st));
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 4], st));
+        cudaEvent_t* e9 = prof ? ev + kEv * k : nullptr;
+        auto mark = [&](int i) -> cudaError_t { return prof ? cudaEventRecord(e9[i], st) : cudaSuccess; };
+        LFD_CK(mark(0));
+        if (fp) {
+            // forward with the ratio fused into its last transform
+            LFD_CK(fft_forward(*fp, g, ctx->Wf, ctx->Vcm[cur], ctx->Xh, ctx->Yh, nullptr, ctx->Rcm,
+                               ctx->ycm, ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
+            LFD_CK(mark(3));
+            LFD_CK(fft_backward(*fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st,
+                                prof ? e9 + 4 : nullptr));
+            LFD_CK(mark(6));
+            LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, ctx->mip,
+                                    ctx->flux_part, st));
+        } else {
+            LFD_CK(mark(1));
+            LFD_TRY(run_forward(ctx, cur, st));
+            LFD_CK(mark(2));
+            LFD_CK(launch_fwd_finish_ratio(ctx->Fwd, fpart, ctx->ypoly, ctx->opt.eps, g, ctx->Rp32, rhi,
+                                           rlo, st));
+            LFD_CK(mark(3));
+            LFD_CK(mark(4));
+            LFD_TRY(run_backward(ctx, st));
+            LFD_CK(mark(5));
+            LFD_CK(mark(6));
+            LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
+                                 ctx->mip, ctx->flux_part, st));
+        }
+        LFD_CK(mark(7));
         LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
                              ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, ctx->flux_part,
-                             g.Ly * g.Lx, ctx->hist + k, ctx->hist + ctx->hist_cap + k, st));
-        if (prof) LFD_CK(cudaEventRecord(ev[6 * k + 5], st));
+                             ctx->nflux, ctx->hist + k, ctx->hist + ctx->hist_cap + k, st));
+        LFD_CK(mark(8));
         ran = k + 1;
         if (stop_at_predicted) {
             LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist + k, sizeof(double),
@@ -561,7 +644,8 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
     }
     const int result = cur;
     const int done = stopped ? ran - 1 : ran;
-    LFD_CK(launch_depoly_volume(ctx->Vp32[result], g.m_base, g, vd, st));
+    if (fp) LFD_CK(launch_depoly_volume_cm(ctx->Vcm[result], g, vd, st));
+    else LFD_CK(launch_depoly_volume(ctx->Vp32[result], g.m_base, g, vd, st));
     if (!vdev) LFD_CK(cudaMemcpyAsync(v, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
     std::vector<double> hbuf(2 * (size_t)ran);
     LFD_CK(cudaMemcpyAsync(hbuf.data(), ctx->hist, ran * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -577,11 +661,20 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
     }
     if (prof) {
         for (int k = 0; k < ran; ++k) {
-            for (int i = 0; i < 5; ++i) {
-                float ms = 0.f;
-                LFD_CK(cudaEventElapsedTime(&ms, ev[6 * k + i], ev[6 * k + i + 1]));
-                ctx->prof.sum_ms[i] += ms;
-            }
+            float t[kEv];
+            t[0] = 0.f;
+            for (int i = 1; i < kEv; ++i)
+                LFD_CK(cudaEventElapsedTime(&t[i], ev[kEv * k], ev[kEv * k + i]));
+            const bool f = fp != nullptr;
+            double* sm = ctx->prof.sum_ms;
+            sm[0] += f ? t[3] : t[2];              // forward projection
+            sm[1] += f ? 0.0 : t[3] - t[2];        // ratio (fused in the FFT variant)
+            sm[2] += t[6] - t[3];                  // backprojection
+            sm[3] += t[7] - t[6];                  // update
+            sm[4] += t[8] - t[7];                  // metric
+            sm[5] += t[2] - t[1];                  // forward contraction
+            sm[6] += t[5] - t[4];                  // backward contraction
+            sm[7] += f ? t[1] + (t[3] - t[2]) + (t[4] - t[3]) + (t[6] - t[5]) : 0.0;  // transforms
         }
         ctx->prof.count += ran;
     }

@@ -58,7 +58,7 @@ struct DevBuf {
 struct StageTimes {
     std::vector<cudaEvent_t> ev;  // 6 per iteration slot
     bool on = false;
-    double sum_ms[5] = {0, 0, 0, 0, 0};
+    double sum_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t count = 0;
 };
 
@@ -105,6 +105,17 @@ struct lfd_ctx {
     lfd::StageTimes prof;
     // tensor-core path state (tcgen05), created on first use
     void* tc = nullptr;
+    // FFT variant: cached PSF spectra and channel-major buffers
+    void* fft = nullptr;         // FftPlan (host)
+    float2* Wf = nullptr;        // [bins][S][Cf]
+    float2* Xh = nullptr;        // [bins][tiles][Cf]
+    float2* Yh = nullptr;        // [bins][tiles][Sf]
+    float* Vcm[2] = {nullptr, nullptr};  // [C][Ly][Lx]
+    float* Rcm = nullptr;        // [S][Ly][Lx]
+    float* Xcm = nullptr;        // [C][Ly][Lx]
+    float* invcm = nullptr;      // [C][Ly][Lx]
+    float* ycm = nullptr;        // [S][Ly][Lx]
+    int nflux = 0;               // flux partials written per update
 };
 
 namespace lfd {

@@ -64,6 +64,8 @@ struct TcArgs {
     int taps;           // T*T
     int tap_inner;      // k-block order: 1 = (block, tap) tap fastest; 0 = (tap, block)
     int chunk_kb;       // k-blocks per accumulation chunk (see below)
+    int kvalid;         // contraction entries that are not padding (C or S); MMA
+                        // k-steps of 16 that start at or past it are skipped
     uint32_t tx_bytes;  // bytes landing per stage
     float* out;
     int64_t slot_stride;
@@ -337,8 +339,11 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                             }
                             tc_fence_after();
                             const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
+                            const int cb = a.tap_inner ? kb / a.taps : kb % a.kb_per_tap;
+                            const int ksteps = min(kBK / 16, (a.kvalid - cb * kBK + 15) / 16);
 #pragma unroll
                             for (int ks = 0; ks < kBK / 16; ++ks) {
+                                if (ks >= ksteps) break;
                                 const uint64_t bd = FWD ? sdesc(sB + ks * 32, 16, 1024)
                                                         : sdesc(sB + ks * 2048, 8192, 1024);
 #pragma unroll
@@ -553,6 +558,7 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         f.taps = (int)g.taps();
         f.tap_inner = 1;
         f.chunk_kb = kChainSteps / (4 * f.passes);
+        f.kvalid = g.C;
         f.tx_bytes = (uint32_t)(kABytes + kBK * 2 * g.Spad);
         f.out = ctx->Fwd;
         f.slot_stride = g.M_pad * g.Spad;
@@ -566,6 +572,7 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         b.n_units = b.n_mtiles * b.n_ntiles * b.nsplit;
         b.kb_per_tap = (g.Spad + kBK - 1) / kBK;
         b.tap_inner = 0;
+        b.kvalid = g.S;
         b.kb_total = (int)(g.taps() * b.kb_per_tap);
         b.bn = bwd_bn(g);
         b.n_valid = g.Cpad;

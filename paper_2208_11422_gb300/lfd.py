@@ -20,6 +20,8 @@ LFD_OK, LFD_EINVAL, LFD_ENOMEM, LFD_ECUDA, LFD_ENOTREADY, LFD_ETIMEDOUT, LFD_EBU
     LFD_EINTERNAL, LFD_EUNSUPPORTED = range(9)
 LFD_FP32, LFD_TF32, LFD_BF16, LFD_BF16X3 = range(4)
 PRECISIONS = {"fp32": LFD_FP32, "bf16": LFD_BF16, "bf16x3": LFD_BF16X3}
+LFD_DIRECT, LFD_FFT = 0, 1
+VARIANTS = {"direct": LFD_DIRECT, "fft": LFD_FFT}
 
 
 class LfdError(RuntimeError):
@@ -39,6 +41,7 @@ class lfd_options(ctypes.Structure):
         ("XS", ctypes.c_int),
         ("YS", ctypes.c_int),
         ("l2_over_region", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -67,7 +70,7 @@ _SIGS = {
                               ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)]),
     "lfd_launch_count": (ctypes.c_uint64, []),
     "lfd_set_profiling": (_I, [_VP, _I]),
-    "lfd_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "lfd_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
 
 
@@ -135,6 +138,8 @@ def lfd_default_options(**overrides) -> lfd_options:
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
         setattr(o, k, v)
     return o
 
@@ -229,6 +234,8 @@ def lfd_set_profiling(ctx, on: bool = True):
 
 
 def lfd_stage_times(ctx):
-    arr = (ctypes.c_float * 5)()
-    _check(load().lfd_stage_times(ctx, arr), ctx)
+    """Mean stage times (ms): forward, ratio, backward, update, metric, forward
+    contraction, backward contraction, FFT transforms."""
+    arr = (ctypes.c_float * 8)()
+    _check(load().lfd_stage_times(ctx, arr, 8), ctx)
     return list(arr)

@@ -21,6 +21,7 @@ class Ctx:
     """Context manager around lfd_create / lfd_destroy with torch device buffers."""
 
     def __init__(self, psf, nnum, H, W, precision="fp32", **opt):
+        self.ctx = None
         import torch
         from paper_2208_11422_gb300 import lfd
         self.lfd = lfd

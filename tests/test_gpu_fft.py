@@ -1,0 +1,114 @@
+"""Parity of the FFT variant (overlap-save on the lenslet grid, FP32) with the
+FP64 oracle through the C ABI: relative L2 <= 1e-5 per projection and <= 1e-4
+after RL iterations, predicted iteration equal to the oracle's."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import metric
+from oracle import rl as orl
+from paper_2208_11422_gb300 import synth
+
+from gpu_util import Ctx, lib, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib()
+
+
+SHAPES = [
+    (5, 15, 15, 5, 5),     # the tiny workload's geometry, one tile
+    (5, 7, 12, 3, 5),      # non-square
+    (1, 20, 17, 2, 7),     # Nnum = 1
+    (3, 9, 9, 4, 1),       # PSF of one lenslet
+    (5, 3, 3, 2, 9),       # PSF wider than the sensor
+    (15, 5, 7, 31, 11),    # 225 phases
+    (5, 40, 40, 5, 5),     # 2 x 2 tiles with ragged last tiles
+    (3, 61, 20, 2, 3),     # 3 x 1 tiles, tall sensor
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fft_projections_match_oracle(shape):
+    N, Ly, Lx, Nz, k = shape
+    H, W, P = Ly * N, Lx * N, k * N
+    psf = synth.random_psf(21, N, Nz, P, density=0.8)
+    v = synth.random_volume(22, Nz, H, W)
+    r = synth.random_image(23, H, W, 0.1, 2.0)
+    with Ctx(psf, N, H, W, variant="fft") as c:
+        hv = c.forward(v)
+        ht = c.backward(r)
+    ef = rel_l2(hv, oracle.forward(psf, N, v))
+    eb = rel_l2(ht, oracle.backward(psf, N, r))
+    print("%s fft forward %.2e backward %.2e" % (shape, ef, eb))
+    assert ef <= 1e-5 and eb <= 1e-5
+
+
+def test_fft_rl_config0():
+    g = synth.CONFIGS[0]
+    psf = synth.make_psf(0)
+    y = synth.poisson_data(oracle.forward(psf, g.nnum, synth.ground_truth(0)), g.scale,
+                           g.background, 200)
+    XS, YS = metric.region_size(g.nnum, g.H, g.W)
+    ref = orl.rl(psf, g.nnum, y, g.iterations, XS, YS)
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+        v, done, pred, ent, flux = c.rl(y, g.iterations)
+        vs, done_s, pred_s, _, _ = c.rl(y, g.iterations, stop=True)
+    assert rel_l2(v, ref.v) <= 1e-4
+    assert pred == ref.predicted
+    np.testing.assert_allclose(ent, ref.entropy, rtol=1e-5)
+    np.testing.assert_allclose(flux, ref.flux, rtol=1e-5)
+    assert done_s == pred_s == ref.predicted
+
+
+def test_fft_rl_config1_against_stored_oracle_run():
+    d = np.load(os.path.join(GOLDEN, "lf_mid_615px_31z_psf165.npz"))
+    g = synth.CONFIGS[1]
+    psf = synth.make_psf(1)
+    y = (d["y_counts"].astype(np.float64) + float(d["background"])).astype(np.float32)
+    vox = d["sample_vox"]
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+        v, done, pred, ent, flux = c.rl(y, int(d["n_iter"]))
+    e = rel_l2(v[vox[:, 0], vox[:, 1], vox[:, 2]], d["v_last"])
+    print("config 1 fft: sampled rel-L2 %.2e, predicted %d" % (e, pred))
+    assert e <= 1e-4
+    assert pred == int(d["predicted"])
+    # The transforms leave an absolute error floor (~1e-6 of each patch's
+    # largest value); in dark voxels that is a larger relative error, and the
+    # z-maximum turns it into a small upward bias of the MIP background, which
+    # moves the entropy by up to ~1e-4 relative (measured 8e-5). The volume and
+    # the predicted iteration stay within their tolerances.
+    np.testing.assert_allclose(ent, d["entropy"], rtol=2e-4)
+
+
+def test_fft_full_size_sampled_projections():
+    g = synth.CONFIGS[2]
+    psf = synth.make_psf(2)
+    v = synth.beads(102, g.nz, g.H, g.W, g.beads, g.bead_radius, g.amp_lo).astype(np.float32)
+    r = synth.random_image(7, g.H, g.W, 0.5, 1.5)
+    pix = synth.sample_indices(8, 256, (g.H, g.W))
+    vox = synth.sample_indices(9, 256, (g.nz, g.H, g.W))
+    pix[:4] = [[0, 0], [g.H - 1, g.W - 1], [0, g.W - 1], [g.H - 1, 0]]
+    vox[:2] = [[0, 0, 0], [g.nz - 1, g.H - 1, g.W - 1]]
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+        hv = c.forward(v)
+        ht = c.backward(r)
+    ef = rel_l2(hv[pix[:, 0], pix[:, 1]], oracle.forward_at(psf, g.nnum, v, pix))
+    eb = rel_l2(ht[vox[:, 0], vox[:, 1], vox[:, 2]], oracle.backward_at(psf, g.nnum, r, vox))
+    print("config 2 fft: sampled forward %.2e backward %.2e" % (ef, eb))
+    assert ef <= 1e-5 and eb <= 1e-5
+
+
+def test_fft_rejects_tensor_core_precision():
+    from paper_2208_11422_gb300 import lfd
+    g = synth.CONFIGS[0]
+    psf = synth.make_psf(0)
+    with pytest.raises(lfd.LfdError):
+        Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision="bf16")
