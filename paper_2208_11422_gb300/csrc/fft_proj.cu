@@ -130,6 +130,7 @@ struct HvDst {
     float* img;        // [H][W] or null
     float* rcm;        // [S][Ly][Lx] ratio or null
     const float* ycm;  // [S][Ly][Lx]
+    float* rimg;       // [H][W] ratio in image layout or null
     float eps;
     int N, W, Ly, Lx, B, tiles_x;
     __device__ void operator()(int s, int tile, int i, int j, float hv) const {
@@ -140,7 +141,9 @@ struct HvDst {
         if (rcm) {
             const int64_t o = ((int64_t)s * Ly + Iy) * Lx + Ix;
             const float den = hv + eps;
-            rcm[o] = den > 0.f ? ycm[o] / den : 0.f;
+            const float r = den > 0.f ? ycm[o] / den : 0.f;
+            rcm[o] = r;
+            if (rimg) rimg[((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N] = r;
         }
     }
 };
@@ -339,6 +342,42 @@ cudaError_t run_contract_adj(const FftPlan& p, const Geo& g, const float2* Wf, c
     return cudaGetLastError();
 }
 
+// Exact backprojection at listed voxels, by direct summation over each voxel's
+// PSF window clipped to the sensor (one warp per voxel, FP32 products, one
+// partial sum per PSF row):
+//   X[c][Iy][Ix] = sum_{i,j} r[i][j] K[z][ty][tx][i - i' + c0][j - j' + c0]
+// with c = (z, t = ty*N + tx), i' = Iy*N + ty, j' = Ix*N + tx. The FFT variant
+// uses it for voxels whose sensitivity H^T 1 is so small that the transforms'
+// absolute error floor would dominate their update.
+__global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, const float* __restrict__ rimg,
+                            const float* __restrict__ psf, Geo g, float* __restrict__ xcm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const int c0 = (g.P - 1) / 2;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < n;
+         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t idx = list[q];
+        const int c = (int)(idx / L2);
+        const int64_t l = idx % L2;
+        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+        const int z = c / g.S, t = c % g.S, ty = t / g.N, tx = t % g.N;
+        const int ip = Iy * g.N + ty, jp = Ix * g.N + tx;
+        const float* K = psf + (((int64_t)z * g.N + ty) * g.N + tx) * g.P * g.P;
+        const int mi0 = max(0, c0 - ip), mi1 = min(g.P, g.H + c0 - ip);
+        const int mj0 = max(0, c0 - jp), mj1 = min(g.P, g.W + c0 - jp);
+        float acc = 0.f;
+        for (int mi = mi0; mi < mi1; ++mi) {
+            const float* rr = rimg + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
+            const float* kk = K + (int64_t)mi * g.P;
+            float row = 0.f;
+            for (int mj = mj0 + lane; mj < mj1; mj += 32) row = fmaf(rr[mj], kk[mj], row);
+            acc += row;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) xcm[idx] = acc;
+    }
+}
+
 // ------------------------------------------------ layout and update kernels --
 // v[z][Iy*N+ty][Ix*N+tx] -> vcm[z*S + ty*N + tx][Iy][Ix]
 __global__ void k_poly_volume_cm(const float* __restrict__ v, Geo g, float* __restrict__ vcm) {
@@ -524,7 +563,7 @@ cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* W
 
 cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
                         float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
-                        float eps, cudaStream_t st, cudaEvent_t* ev) {
+                        float* rimg, float eps, cudaStream_t st, cudaEvent_t* ev) {
     ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
     cudaError_t e = p.F == 64 ? run_r2c<64>(src, g.C, p.Cf, p.ntile, Xh, st)
                               : run_r2c<32>(src, g.C, p.Cf, p.ntile, Xh, st);
@@ -536,7 +575,7 @@ cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const 
     else e = run_contract_fwd<16>(p, g, Wf, Xh, Yh, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    HvDst dst{img_out, rcm, ycm, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
+    HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
     return p.F == 64 ? run_c2r<64>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st)
                      : run_c2r<32>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st);
 }
@@ -585,6 +624,16 @@ cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st
     count_launch();
     return cudaGetLastError();
 }
+cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, const float* psf,
+                             const Geo& g, float* xcm, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n * 32 + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_exact_bwd<<<(unsigned)blocks, 256, 0, st>>>(list, n, rimg, psf, g, xcm);
+    count_launch();
+    return cudaGetLastError();
+}
+
 int update_cm_blocks(const Geo& g) { return grid_for((int64_t)g.S * g.Ly * g.Lx, 4096); }
 cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
                              const Geo& g, float* mip, double* flux_part, cudaStream_t st) {

@@ -23,9 +23,10 @@ cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* W
 // contraction, for per-kernel timing.
 // forward projection of the channel-major volume vcm [C][Ly][Lx]; writes the
 // image Hv to img_out [H][W] and / or r = y / (Hv + eps) to rcm [S][Ly][Lx]
+// (and to rimg [H][W] in image layout when rimg is not null)
 cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
                         float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
-                        float eps, cudaStream_t st, cudaEvent_t* ev);
+                        float* rimg, float eps, cudaStream_t st, cudaEvent_t* ev);
 // backprojection of rcm [S][Ly][Lx] into xcm [C][Ly][Lx] and / or a stack-order volume
 cudaError_t fft_backward(const FftPlan& p, const Geo& g, const float2* Wf, const float* rcm,
                          float2* Xh, float2* Yh, float* xcm, float* stack_out, cudaStream_t st,
@@ -36,6 +37,11 @@ cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cu
 cudaError_t launch_poly_image_cm(const float* y, const Geo& g, float* ycm, cudaStream_t st);
 cudaError_t launch_fill_cm(float* p, int64_t n, float val, cudaStream_t st);
 cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st);
+// exact backprojection of rimg [H][W] at the voxels list[0..n) (linear
+// channel-major indices c*Ly*Lx + Iy*Lx + Ix), written into xcm; psf is the
+// original [Nz][Nnum][Nnum][P][P] array
+cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, const float* psf,
+                             const Geo& g, float* xcm, cudaStream_t st);
 int update_cm_blocks(const Geo& g);
 cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
                              const Geo& g, float* mip, double* flux_part, cudaStream_t st);

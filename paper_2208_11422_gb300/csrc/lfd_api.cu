@@ -65,6 +65,10 @@ bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why) {
 
 namespace {
 
+// FFT variant: voxels with H^T 1 below this fraction of the largest are
+// backprojected by direct summation (see lfd_create)
+constexpr float kLowSensitivity = 1e-3f;
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -154,7 +158,7 @@ void free_all(lfd_ctx* ctx) {
                     ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
                     ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
                     ctx->Wf, ctx->Xh, ctx->Yh, ctx->Vcm[0], ctx->Vcm[1], ctx->Rcm, ctx->Xcm,
-                    ctx->invcm, ctx->ycm};
+                    ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg, ctx->low_list};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -340,6 +344,8 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         CREATE_TRY(dalloc(ctx, &ctx->Xcm, (int64_t)g.C * L2, true));
         CREATE_TRY(dalloc(ctx, &ctx->invcm, (int64_t)g.C * L2, true));
         CREATE_TRY(dalloc(ctx, &ctx->ycm, (int64_t)g.S * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->rimg, (int64_t)g.H * g.W, true));
+        CREATE_TRY(dalloc(ctx, &ctx->psf_dev, (int64_t)Nz * Nnum * Nnum * P * P, false));
         ctx->nflux = update_cm_blocks(g);
     } else {
         // Hv partials serve both the SIMT path and the tensor-core path
@@ -387,6 +393,9 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         psf_dev = psf_tmp;
     }
     cudaError_t e = launch_repack_psf(psf_dev, g, ctx->W32, ctx->Wb[0], ctx->Wb[1], st);
+    if (e == cudaSuccess && ctx->psf_dev)
+        e = cudaMemcpyAsync(ctx->psf_dev, psf_dev, (size_t)psf_count * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (psf_tmp) cudaFree(psf_tmp);
     CREATE_CK(e);
@@ -396,6 +405,32 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         CREATE_CK(fft_init(fplan, g, ctx->W32, ctx->Wf, st));
         CREATE_CK(launch_fill_cm(ctx->Rcm, (int64_t)g.S * L2, 1.0f, st));
         CREATE_CK(fft_backward(fplan, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st, nullptr));
+        // Voxels whose sensitivity H^T 1 is below kLowSensitivity of the largest
+        // are dominated by the transforms' absolute error floor (~1e-7 of a
+        // tile's largest value); list them once and backproject them exactly,
+        // here for H^T 1 and in every iteration for H^T r.
+        {
+            const int64_t nvox = (int64_t)g.C * L2;
+            std::vector<float> h(nvox);
+            CREATE_CK(cudaMemcpyAsync(h.data(), ctx->Xcm, nvox * sizeof(float), cudaMemcpyDeviceToHost, st));
+            CREATE_CK(cudaStreamSynchronize(st));
+            float mx = 0.f;
+            for (float x : h) mx = x > mx ? x : mx;
+            const float thr = kLowSensitivity * mx;
+            std::vector<int64_t> low;
+            for (int64_t i = 0; i < nvox; ++i)
+                if (!(h[i] >= thr)) low.push_back(i);
+            ctx->n_low = (int64_t)low.size();
+            if (ctx->n_low > 0) {
+                CREATE_TRY(dalloc(ctx, &ctx->low_list, ctx->n_low, false));
+                CREATE_CK(cudaMemcpyAsync(ctx->low_list, low.data(), ctx->n_low * sizeof(int64_t),
+                                          cudaMemcpyHostToDevice, st));
+                CREATE_TRY(ensure_stage(ctx, false));
+                CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
+                CREATE_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, ctx->stage_img, ctx->psf_dev, g,
+                                           ctx->Xcm, st));
+            }
+        }
         CREATE_CK(launch_inv_cm(ctx->Xcm, (int64_t)g.C * L2, ctx->invcm, st));
         CREATE_CK(cudaStreamSynchronize(st));
         cudaFree(ctx->W32);  // the FFT variant reads only the spectra
@@ -472,8 +507,8 @@ lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_st
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
-        LFD_CK(fft_forward(fp, g, ctx->Wf, ctx->Vcm[0], ctx->Xh, ctx->Yh, yd, nullptr, nullptr, 0.f, st,
-                           nullptr));
+        LFD_CK(fft_forward(fp, g, ctx->Wf, ctx->Vcm[0], ctx->Xh, ctx->Yh, yd, nullptr, nullptr, nullptr,
+                           0.f, st, nullptr));
     } else {
         LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
         LFD_TRY(run_forward(ctx, 0, st));
@@ -510,7 +545,9 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_image_cm(rd, g, ctx->Rcm, st));
-        LFD_CK(fft_backward(fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, nullptr, vd, st, nullptr));
+        LFD_CK(fft_backward(fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st, nullptr));
+        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, rd, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(launch_depoly_volume_cm(ctx->Xcm, g, vd, st));
     } else {
         LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
         LFD_TRY(run_backward(ctx, st));
@@ -603,10 +640,11 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         if (fp) {
             // forward with the ratio fused into its last transform
             LFD_CK(fft_forward(*fp, g, ctx->Wf, ctx->Vcm[cur], ctx->Xh, ctx->Yh, nullptr, ctx->Rcm,
-                               ctx->ycm, ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
+                               ctx->ycm, ctx->rimg, ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
             LFD_CK(mark(3));
             LFD_CK(fft_backward(*fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st,
                                 prof ? e9 + 4 : nullptr));
+            LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
             LFD_CK(mark(6));
             LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, ctx->mip,
                                     ctx->flux_part, st));

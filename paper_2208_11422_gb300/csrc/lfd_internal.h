@@ -116,6 +116,10 @@ struct lfd_ctx {
     float* invcm = nullptr;      // [C][Ly][Lx]
     float* ycm = nullptr;        // [S][Ly][Lx]
     int nflux = 0;               // flux partials written per update
+    float* psf_dev = nullptr;    // original PSF [Nz][N][N][P][P] (FFT variant)
+    float* rimg = nullptr;       // ratio image [H][W] (FFT variant)
+    int64_t* low_list = nullptr; // voxels backprojected exactly (FFT variant)
+    int64_t n_low = 0;
 };
 
 namespace lfd {
