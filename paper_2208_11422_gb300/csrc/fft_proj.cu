@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "fft_proj.h"
+#include "tc_cgemm.h"
 
 namespace lfd {
 namespace {
@@ -86,11 +87,32 @@ struct TapSrc {
     }
 };
 
-// R2C 2-D transform of kCPB channels' patches of one tile.
-// out[(bin * ntile + tile) * ldc + c], bin = fy * (F/2+1) + fx.
-template <int F, class Src>
-__global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, int ntile,
-                                                 float2* __restrict__ out) {
+// spectrum outputs of the R2C transform: complex64, or BF16 planes
+// (real hi, real lo, imag hi, imag lo; x = hi + lo) for the tensor cores
+struct OutC64 {
+    float2* p;
+    int ntile, ld;
+    __device__ void operator()(int bin, int tile, int c, float2 v) const {
+        p[((int64_t)bin * ntile + tile) * ld + c] = v;
+    }
+};
+struct OutPlanes {
+    __nv_bfloat16* p[4];
+    int ntile, ld;
+    __device__ void operator()(int bin, int tile, int c, float2 v) const {
+        const int64_t o = ((int64_t)bin * ntile + tile) * ld + c;
+        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+        p[0][o] = rh;
+        p[1][o] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+        p[2][o] = ih;
+        p[3][o] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+    }
+};
+
+// R2C 2-D transform of kCPB channels' patches of one tile; bin = fy*(F/2+1)+fx,
+// out(bin, tile, c, value) for every c < ldc (zeros for c >= nch).
+template <int F, class Src, class Out>
+__global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, Out out) {
     constexpr int H2 = FftSize<F>::H2, LOG = FftSize<F>::LOG;
     extern __shared__ float2 sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -118,9 +140,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, int 
     __syncthreads();
     for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
         const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
-        if (c < ldc)
-            out[((int64_t)bin * ntile + tile) * ldc + c] =
-                c < nch ? spec[ch * F * H2 + bin] : make_float2(0.f, 0.f);
+        if (c < ldc) out(bin, tile, c, c < nch ? spec[ch * F * H2 + bin] : make_float2(0.f, 0.f));
     }
 }
 
@@ -439,9 +459,33 @@ __global__ void __launch_bounds__(256) k_update_cm(const float* __restrict__ vin
         const int t = (int)(e / L2);
         const int64_t l = e % L2;
         float mx = 0.f;
-#pragma unroll 4
-        for (int z = 0; z < g.Nz; ++z) {
-            const int64_t o = (int64_t)(z * g.S + t) * L2 + l;
+        const int64_t zs = (int64_t)g.S * L2;  // stride between depths
+        const int64_t o0 = (int64_t)t * L2 + l;
+        int z = 0;
+        for (; z + 4 <= g.Nz; z += 4) {  // four depths' loads in flight
+            float iv[4], vo[4], xx[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t o = o0 + (z + q) * zs;
+                iv[q] = inv[o];
+                vo[q] = vin[o];
+                xx[q] = x[o];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float vn = 0.f;
+                if (iv[q] > 0.f) {
+                    const float vx = vo[q] * xx[q];
+                    vn = vx * iv[q];
+                    flux += (double)vx;
+                }
+                vn = vn > 0.f ? vn : 0.f;
+                vout[o0 + (z + q) * zs] = vn;
+                mx = fmaxf(mx, vn);
+            }
+        }
+        for (; z < g.Nz; ++z) {
+            const int64_t o = o0 + z * zs;
             const float iv = inv[o], vo = vin[o];
             float vn = 0.f;
             if (iv > 0.f) {
@@ -493,15 +537,27 @@ cudaError_t upload_twiddles() {
     return e;
 }
 
-template <int F, class Src>
-cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, float2* out, cudaStream_t st) {
+template <int F, class Src, class Out>
+cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, Out out, cudaStream_t st) {
     const size_t smem = fft_smem<F>();
-    cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)ntile, (unsigned)((ldc + kCPB - 1) / kCPB));
-    k_fft_r2c<F, Src><<<grid, 256, smem, st>>>(src, nch, ldc, ntile, out);
+    k_fft_r2c<F, Src, Out><<<grid, 256, smem, st>>>(src, nch, ldc, out);
     count_launch();
     return cudaGetLastError();
+}
+
+// R2C into complex64 (FP32 contraction) or BF16 planes (tensor-core contraction)
+template <class Src>
+cudaError_t r2c_any(const FftPlan& p, Src src, int nch, int ldc, int ntile, float2* c64,
+                    __nv_bfloat16* const* planes, int plane_tiles, cudaStream_t st) {
+    if (planes) {
+        OutPlanes o{{planes[0], planes[1], planes[2], planes[3]}, plane_tiles, ldc};
+        return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
+    }
+    OutC64 o{c64, ntile, ldc};
+    return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
 }
 
 template <int F, class Dst>
@@ -537,6 +593,8 @@ bool fft_plan_for(const Geo& g, FftPlan* p) {
         q.bins = F * (F / 2 + 1);
         q.Cf = (g.C + 3) & ~3;
         q.Sf = (g.S + 3) & ~3;
+        q.Cw = (g.C + 7) & ~7;
+        q.Sw = (g.S + 7) & ~7;
         const double spectra = (double)q.bins * g.S * q.Cf * 8.0;
         if (spectra > 96e9) continue;  // keep the cached spectra well inside HBM
         const double flops = (double)q.bins * g.S * q.ntile * g.C * 8.0;
@@ -552,51 +610,53 @@ bool fft_plan_for(const Geo& g, FftPlan* p) {
 }
 
 // -------------------------------------------------------------- launchers --
-cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* Wf, cudaStream_t st) {
+cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const FftBuffers& b,
+                     cudaStream_t st) {
     cudaError_t e = upload_twiddles();
     if (e != cudaSuccess) return e;
     TapSrc src{W32, g.T, g.Spad, g.Cpad};
-    // "tiles" = phases s, channels = c: output Wf[bin][s][c] with row length Cf
-    if (p.F == 64) return run_r2c<64>(src, g.C, p.Cf, g.S, Wf, st);
-    return run_r2c<32>(src, g.C, p.Cf, g.S, Wf, st);
+    // "tiles" = phases s, channels = c: Wf[bin][s][c]
+    if (b.cg) return r2c_any(p, src, g.C, p.Cw, g.S, nullptr, b.Wp, g.S, st);
+    return r2c_any(p, src, g.C, p.Cf, g.S, b.Wf, nullptr, 0, st);
 }
 
-cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
-                        float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
-                        float* rimg, float eps, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* vcm,
+                        float* img_out, float* rcm, const float* ycm, float* rimg, float eps,
+                        cudaStream_t st, cudaEvent_t* ev) {
     ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
-    cudaError_t e = p.F == 64 ? run_r2c<64>(src, g.C, p.Cf, p.ntile, Xh, st)
-                              : run_r2c<32>(src, g.C, p.Cf, p.ntile, Xh, st);
+    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, p.ntile, nullptr, b.Xp, 16, st)
+                         : r2c_any(p, src, g.C, p.Cf, p.ntile, b.Xh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (p.ntile <= 1) e = run_contract_fwd<1>(p, g, Wf, Xh, Yh, st);
-    else if (p.ntile <= 4) e = run_contract_fwd<4>(p, g, Wf, Xh, Yh, st);
-    else if (p.ntile <= 9) e = run_contract_fwd<9>(p, g, Wf, Xh, Yh, st);
-    else e = run_contract_fwd<16>(p, g, Wf, Xh, Yh, st);
+    if (b.cg) e = cgemm_forward(b.cg, st);
+    else if (p.ntile <= 1) e = run_contract_fwd<1>(p, g, b.Wf, b.Xh, b.Yh, st);
+    else if (p.ntile <= 4) e = run_contract_fwd<4>(p, g, b.Wf, b.Xh, b.Yh, st);
+    else if (p.ntile <= 9) e = run_contract_fwd<9>(p, g, b.Wf, b.Xh, b.Yh, st);
+    else e = run_contract_fwd<16>(p, g, b.Wf, b.Xh, b.Yh, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
-    return p.F == 64 ? run_c2r<64>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st);
 }
 
-cudaError_t fft_backward(const FftPlan& p, const Geo& g, const float2* Wf, const float* rcm,
-                         float2* Xh, float2* Yh, float* xcm, float* stack_out, cudaStream_t st,
-                         cudaEvent_t* ev) {
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* rcm,
+                         float* xcm, float* stack_out, cudaStream_t st, cudaEvent_t* ev) {
     ImgSrc src{rcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
-    cudaError_t e = p.F == 64 ? run_r2c<64>(src, g.S, p.Sf, p.ntile, Yh, st)
-                              : run_r2c<32>(src, g.S, p.Sf, p.ntile, Yh, st);
+    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, p.ntile, nullptr, b.Yp, 16, st)
+                         : r2c_any(p, src, g.S, p.Sf, p.ntile, b.Yh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (p.ntile <= 1) e = run_contract_adj<1>(p, g, Wf, Yh, Xh, st);
-    else if (p.ntile <= 4) e = run_contract_adj<4>(p, g, Wf, Yh, Xh, st);
-    else if (p.ntile <= 9) e = run_contract_adj<9>(p, g, Wf, Yh, Xh, st);
-    else e = run_contract_adj<16>(p, g, Wf, Yh, Xh, st);
+    if (b.cg) e = cgemm_adjoint(b.cg, st);
+    else if (p.ntile <= 1) e = run_contract_adj<1>(p, g, b.Wf, b.Yh, b.Xh, st);
+    else if (p.ntile <= 4) e = run_contract_adj<4>(p, g, b.Wf, b.Yh, b.Xh, st);
+    else if (p.ntile <= 9) e = run_contract_adj<9>(p, g, b.Wf, b.Yh, b.Xh, st);
+    else e = run_contract_adj<16>(p, g, b.Wf, b.Yh, b.Xh, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
-    return p.F == 64 ? run_c2r<64>(Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st)
-                     : run_c2r<32>(Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st)
+                     : run_c2r<32>(b.Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st);
 }
 
 cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st) {
@@ -634,7 +694,8 @@ cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, 
     return cudaGetLastError();
 }
 
-int update_cm_blocks(const Geo& g) { return grid_for((int64_t)g.S * g.Ly * g.Lx, 4096); }
+// one item per thread (no grid-stride tail), one flux partial per block
+int update_cm_blocks(const Geo& g) { return (int)(((int64_t)g.S * g.Ly * g.Lx + 255) / 256); }
 cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
                              const Geo& g, float* mip, double* flux_part, cudaStream_t st) {
     k_update_cm<<<update_cm_blocks(g), 256, 0, st>>>(vin, vout, x, inv, g, mip, flux_part);

@@ -11,26 +11,41 @@ struct FftPlan {
     int tiles_y = 0, tiles_x = 0, ntile = 0;
     int bins = 0;       // F * (F/2 + 1)
     int Cf = 0, Sf = 0; // channel / phase counts padded to 4 (row lengths of the spectra)
+    int Cw = 0, Sw = 0; // padded to 8 (row lengths of the BF16 planes)
+};
+
+// Spectra buffers. FP32 contraction: Wf, Xh, Yh (complex64). Tensor-core
+// contraction (cg != null): BF16 planes Wp[4] [bins][S][Cw], Xp[4] [bins][16][Cw],
+// Yp[4] [bins][16][Sw] (real hi, real lo, imag hi, imag lo) as inputs, and
+// Yh / Xh as the contractions' complex64 outputs.
+struct FftBuffers {
+    float2* Wf = nullptr;
+    float2* Xh = nullptr;
+    float2* Yh = nullptr;
+    __nv_bfloat16* Wp[4] = {};
+    __nv_bfloat16* Xp[4] = {};
+    __nv_bfloat16* Yp[4] = {};
+    void* cg = nullptr;
 };
 
 // picks F by a bandwidth / FP32 cost model; false if no plan fits (> 16 tiles,
 // spectra too large, or more than 225 phases)
 bool fft_plan_for(const Geo& g, FftPlan* p);
 
-// Wf[bin][s][Cf] = half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad])
-cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, float2* Wf, cudaStream_t st);
+// half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad]) into b.Wf or b.Wp
+cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const FftBuffers& b,
+                     cudaStream_t st);
 // ev (may be null): two events recorded after the transform and after the
 // contraction, for per-kernel timing.
 // forward projection of the channel-major volume vcm [C][Ly][Lx]; writes the
 // image Hv to img_out [H][W] and / or r = y / (Hv + eps) to rcm [S][Ly][Lx]
 // (and to rimg [H][W] in image layout when rimg is not null)
-cudaError_t fft_forward(const FftPlan& p, const Geo& g, const float2* Wf, const float* vcm,
-                        float2* Xh, float2* Yh, float* img_out, float* rcm, const float* ycm,
-                        float* rimg, float eps, cudaStream_t st, cudaEvent_t* ev);
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* vcm,
+                        float* img_out, float* rcm, const float* ycm, float* rimg, float eps,
+                        cudaStream_t st, cudaEvent_t* ev);
 // backprojection of rcm [S][Ly][Lx] into xcm [C][Ly][Lx] and / or a stack-order volume
-cudaError_t fft_backward(const FftPlan& p, const Geo& g, const float2* Wf, const float* rcm,
-                         float2* Xh, float2* Yh, float* xcm, float* stack_out, cudaStream_t st,
-                         cudaEvent_t* ev);
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* rcm,
+                         float* xcm, float* stack_out, cudaStream_t st, cudaEvent_t* ev);
 
 cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st);
 cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cudaStream_t st);

@@ -8,6 +8,7 @@
 
 #include "lfd_internal.h"
 #include "fft_proj.h"
+#include "tc_cgemm.h"
 #include "tc_gemm.h"
 
 using namespace lfd;
@@ -105,8 +106,24 @@ lfd_status dalloc(lfd_ctx* ctx, T** p, int64_t count, bool zero) {
         if (s_ != LFD_OK) return s_;     \
     } while (0)
 
+FftBuffers fbufs(const lfd_ctx* ctx) {
+    FftBuffers b;
+    b.Wf = ctx->Wf;
+    b.Xh = ctx->Xh;
+    b.Yh = ctx->Yh;
+    for (int i = 0; i < 4; ++i) {
+        b.Wp[i] = ctx->Wp[i];
+        b.Xp[i] = ctx->Xp[i];
+        b.Yp[i] = ctx->Yp[i];
+    }
+    b.cg = ctx->cg;
+    return b;
+}
+
+// direct-variant tensor-core path
 bool uses_tc(const lfd_ctx* ctx) {
-    return ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3;
+    return ctx->opt.variant == LFD_DIRECT &&
+           (ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3);
 }
 bool uses_lo(const lfd_ctx* ctx) { return ctx->opt.precision == LFD_BF16X3; }
 
@@ -158,7 +175,9 @@ void free_all(lfd_ctx* ctx) {
                     ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
                     ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
                     ctx->Wf, ctx->Xh, ctx->Yh, ctx->Vcm[0], ctx->Vcm[1], ctx->Rcm, ctx->Xcm,
-                    ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg, ctx->low_list};
+                    ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg, ctx->low_list,
+                    ctx->Wp[0], ctx->Wp[1], ctx->Wp[2], ctx->Wp[3], ctx->Xp[0], ctx->Xp[1],
+                    ctx->Xp[2], ctx->Xp[3], ctx->Yp[0], ctx->Yp[1], ctx->Yp[2], ctx->Yp[3]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -166,6 +185,8 @@ void free_all(lfd_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     ctx->prof.ev.clear();
     tc_destroy(ctx);
+    cgemm_destroy(ctx->cg);
+    ctx->cg = nullptr;
     delete static_cast<FftPlan*>(ctx->fft);
     ctx->fft = nullptr;
 }
@@ -268,7 +289,8 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         return LFD_EINVAL;
     if (!(opt.eps >= 0.f)) return LFD_EINVAL;
     if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
-    if (opt.variant == LFD_FFT && opt.precision != LFD_FP32) return LFD_EINVAL;
+    if (opt.variant == LFD_FFT && opt.precision != LFD_FP32 && opt.precision != LFD_BF16X3)
+        return LFD_EINVAL;
     int XS = opt.XS, YS = opt.YS;
     if (XS <= 0 || YS <= 0) {
         if (lfd_region_size(Nnum, H, W, opt.dML_um, opt.Q, opt.NA, opt.lambda_um, &XS, &YS) != LFD_OK)
@@ -336,7 +358,15 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     CREATE_TRY(dalloc(ctx, &ctx->W32, wcount, false));
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     if (fft) {
-        CREATE_TRY(dalloc(ctx, &ctx->Wf, (int64_t)fplan.bins * g.S * fplan.Cf, false));
+        if (ctx->opt.precision == LFD_BF16X3) {
+            for (int i = 0; i < 4; ++i) {
+                CREATE_TRY(dalloc(ctx, &ctx->Wp[i], (int64_t)fplan.bins * g.S * fplan.Cw, false));
+                CREATE_TRY(dalloc(ctx, &ctx->Xp[i], (int64_t)fplan.bins * 16 * fplan.Cw, true));
+                CREATE_TRY(dalloc(ctx, &ctx->Yp[i], (int64_t)fplan.bins * 16 * fplan.Sw, true));
+            }
+        } else {
+            CREATE_TRY(dalloc(ctx, &ctx->Wf, (int64_t)fplan.bins * g.S * fplan.Cf, false));
+        }
         CREATE_TRY(dalloc(ctx, &ctx->Xh, (int64_t)fplan.bins * fplan.ntile * fplan.Cf, true));
         CREATE_TRY(dalloc(ctx, &ctx->Yh, (int64_t)fplan.bins * fplan.ntile * fplan.Sf, true));
         for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vcm[b], (int64_t)g.C * L2, true));
@@ -402,9 +432,39 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
 
     if (fft) {
         // PSF spectra, then H^T 1 by the FFT backprojection of ones
-        CREATE_CK(fft_init(fplan, g, ctx->W32, ctx->Wf, st));
+        if (ctx->opt.precision == LFD_BF16X3) {
+            int major = 0;
+            CREATE_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device));
+            if (major != 10) {
+                ctx->err = "the split-BF16 FFT contraction needs an sm_10x (Blackwell) device";
+                return bail(LFD_EUNSUPPORTED);
+            }
+            CgemmBuffers cb{};
+            cb.bins = fplan.bins;
+            cb.ntile = fplan.ntile;
+            cb.S = g.S;
+            cb.C = g.C;
+            cb.Sw = fplan.Sw;
+            cb.Cw = fplan.Cw;
+            cb.Sf = fplan.Sf;
+            cb.Cf = fplan.Cf;
+            for (int i = 0; i < 4; ++i) {
+                cb.W[i] = ctx->Wp[i];
+                cb.X[i] = ctx->Xp[i];
+                cb.Y[i] = ctx->Yp[i];
+            }
+            cb.Yout = ctx->Yh;
+            cb.Xout = ctx->Xh;
+            std::string why2;
+            cudaError_t ce = cgemm_init(cb, ctx->sm_count, &ctx->cg, &why2);
+            if (ce != cudaSuccess) {
+                ctx->err = "cgemm_init: " + (why2.empty() ? std::string(cudaGetErrorString(ce)) : why2);
+                return bail(LFD_ECUDA);
+            }
+        }
+        CREATE_CK(fft_init(fplan, g, ctx->W32, fbufs(ctx), st));
         CREATE_CK(launch_fill_cm(ctx->Rcm, (int64_t)g.S * L2, 1.0f, st));
-        CREATE_CK(fft_backward(fplan, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st, nullptr));
+        CREATE_CK(fft_backward(fplan, g, fbufs(ctx), ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
         // Voxels whose sensitivity H^T 1 is below kLowSensitivity of the largest
         // are dominated by the transforms' absolute error floor (~1e-7 of a
         // tile's largest value); list them once and backproject them exactly,
@@ -507,8 +567,8 @@ lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_st
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
-        LFD_CK(fft_forward(fp, g, ctx->Wf, ctx->Vcm[0], ctx->Xh, ctx->Yh, yd, nullptr, nullptr, nullptr,
-                           0.f, st, nullptr));
+        LFD_CK(fft_forward(fp, g, fbufs(ctx), ctx->Vcm[0], yd, nullptr, nullptr, nullptr, 0.f, st,
+                           nullptr));
     } else {
         LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
         LFD_TRY(run_forward(ctx, 0, st));
@@ -545,7 +605,7 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_image_cm(rd, g, ctx->Rcm, st));
-        LFD_CK(fft_backward(fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st, nullptr));
+        LFD_CK(fft_backward(fp, g, fbufs(ctx), ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
         LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, rd, ctx->psf_dev, g, ctx->Xcm, st));
         LFD_CK(launch_depoly_volume_cm(ctx->Xcm, g, vd, st));
     } else {
@@ -607,6 +667,7 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         vd = ctx->stage_vol;
     }
     const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
+    const FftBuffers fb = fbufs(ctx);
     int cur = 0;
     if (fp) {
         LFD_CK(launch_poly_image_cm(yd, g, ctx->ycm, st));
@@ -639,11 +700,10 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         LFD_CK(mark(0));
         if (fp) {
             // forward with the ratio fused into its last transform
-            LFD_CK(fft_forward(*fp, g, ctx->Wf, ctx->Vcm[cur], ctx->Xh, ctx->Yh, nullptr, ctx->Rcm,
-                               ctx->ycm, ctx->rimg, ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
+            LFD_CK(fft_forward(*fp, g, fb, ctx->Vcm[cur], nullptr, ctx->Rcm, ctx->ycm, ctx->rimg,
+                               ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
             LFD_CK(mark(3));
-            LFD_CK(fft_backward(*fp, g, ctx->Wf, ctx->Rcm, ctx->Xh, ctx->Yh, ctx->Xcm, nullptr, st,
-                                prof ? e9 + 4 : nullptr));
+            LFD_CK(fft_backward(*fp, g, fb, ctx->Rcm, ctx->Xcm, nullptr, st, prof ? e9 + 4 : nullptr));
             LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
             LFD_CK(mark(6));
             LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, ctx->mip,
@@ -690,6 +750,13 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
     LFD_CK(cudaMemcpyAsync(hbuf.data() + ran, ctx->hist + ctx->hist_cap, ran * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
     LFD_CK(cudaStreamSynchronize(st));
+    if (ctx->cg) {
+        const int te = cgemm_error(ctx->cg);
+        if (te != 0) {
+            ctx->err = "tensor-core contraction gave up waiting (code " + std::to_string(te) + ")";
+            return LFD_ETIMEDOUT;
+        }
+    }
     if (uses_tc(ctx)) {
         const int te = tc_error(ctx);
         if (te != 0) {

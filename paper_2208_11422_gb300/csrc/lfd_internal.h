@@ -110,6 +110,10 @@ struct lfd_ctx {
     float2* Wf = nullptr;        // [bins][S][Cf]
     float2* Xh = nullptr;        // [bins][tiles][Cf]
     float2* Yh = nullptr;        // [bins][tiles][Sf]
+    __nv_bfloat16* Wp[4] = {};   // split-BF16 planes of the spectra (tensor-core contraction)
+    __nv_bfloat16* Xp[4] = {};
+    __nv_bfloat16* Yp[4] = {};
+    void* cg = nullptr;          // tensor-core contraction state
     float* Vcm[2] = {nullptr, nullptr};  // [C][Ly][Lx]
     float* Rcm = nullptr;        // [S][Ly][Lx]
     float* Xcm = nullptr;        // [C][Ly][Lx]

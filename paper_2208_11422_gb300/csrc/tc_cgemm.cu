@@ -1,0 +1,365 @@
+// Split-BF16 complex contractions of the FFT variant on the tcgen05 tensor
+// cores (per frequency bin of the overlap-save transforms):
+//
+//   forward  Yh[bin][t][s] = sum_c       Wf[bin][s][c]  Xh[bin][t][c]
+//   adjoint  Xh[bin][t][c] = sum_s  conj(Wf[bin][s][c]) Yh[bin][t][s]
+//
+// Every complex operand is held as four BF16 planes (real hi, real lo, imag
+// hi, imag lo; x = hi + lo) and every complex product becomes real MMAs:
+//   forward  re += Wr Xr - Wi Xi,   im += Wr Xi + Wi Xr
+//   adjoint  re += Wr Yr + Wi Yi,   im += Wr Yi - Wi Yr
+// each of them in three passes hi*hi + hi*lo + lo*hi (negation through the
+// instruction descriptor). One block owns 128 output rows (phases s for the
+// forward, channels c for the adjoint) by the 16 tiles of one bin; its K loop
+// streams 64-wide blocks of all eight planes through a 3-stage TMA ring. The
+// accumulators (real and imaginary, 16 columns each) alternate between two
+// TMEM buffers so the drain of one chunk overlaps the next; chains are cut
+// every 64 k-blocks (1536 MMA steps) and added into the FP32 output at L2
+// (the same rounding control as the direct projections). The spectra (all of
+// Wf, 8 bytes per complex value) are read once per projection: the kernel is
+// bound by HBM bandwidth.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "tc_cgemm.h"
+#include "tc_ptx.h"
+
+namespace lfd {
+namespace {
+
+using namespace tcx;
+
+constexpr int kStages = 3;
+constexpr int kPlaneA = 128 * 64 * 2;  // 16 KB
+constexpr int kPlaneB = 16 * 64 * 2;   // 2 KB
+constexpr int kStageBytes = 4 * kPlaneA + 4 * kPlaneB;
+constexpr int kThreads = 192;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 MMA steps
+
+struct CgArgs {
+    int nbins, ntile;
+    int mtiles;        // row tiles of 128 per bin
+    int nkb;           // k-blocks of 64 per unit
+    int nrows;         // valid rows (S or C)
+    int ld;            // row length of the output (Sf or Cf)
+    float2* out;       // [bins][ntile][ld]
+    int* err;
+};
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
+           const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
+           const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
+           const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
+           const CgArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t* smem = smem_raw + (sbase - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* acc_full = empty + kStages;   // [2]
+    uint64_t* acc_empty = acc_full + 2;     // [2]
+    uint64_t* mma_done = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = a.nbins * a.mtiles;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        *consumed_ctr = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(64));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------- TMA producer --
+            const CUtensorMap* A[4] = {&a0, &a1, &a2, &a3};
+            const CUtensorMap* B[4] = {&b0, &b1, &b2, &b3};
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const int bin = u / a.mtiles, mt = u % a.mtiles;
+                for (int kb = 0; kb < a.nkb && ok; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[stage], kStageBytes);
+                    const uint32_t sA = sbase + stage * kStageBytes, sB = sA + 4 * kPlaneA;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (ADJ) {  // MN-major: two 64-channel atoms of 64 phases
+                            tma_3d(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage]);
+                            tma_3d(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage]);
+                        } else {
+                            tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
+                        }
+                        tma_3d(sB + i * kPlaneB, B[i], kb * 64, 0, bin, &full[stage]);
+                    }
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok)
+                for (int i = *consumed_ctr; i < issued; ++i)
+                    mbar_wait_drain(&full[i % kStages], (uint32_t)((i / kStages) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer --
+            const uint32_t id_p = idesc_bf16(128, 16, false, ADJ, false);
+            const uint32_t id_n = idesc_bf16(128, 16, false, ADJ, true);
+            int stage = 0, consumed = 0, ci = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                for (int c0 = 0; c0 < a.nkb && ok; c0 += kChunkKb, ++ci) {
+                    const int c1 = min(a.nkb, c0 + kChunkKb);
+                    const int buf = ci & 1;
+                    if (ci >= 2 &&
+                        !mbar_wait(&acc_empty[buf], (uint32_t)(((ci - 2) >> 1) & 1), abort_flag, a.err, 12)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dR = tmem + buf * 32, dI = dR + 16;
+                    bool first = true;
+                    for (int kb = c0; kb < c1 && ok; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + 4 * kPlaneA;
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            // planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo
+                            uint64_t ad[4], bd[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                ad[i] = ADJ ? sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024)
+                                            : sdesc(sA + i * kPlaneA + ks * 32, 16, 1024);
+                                bd[i] = sdesc(sB + i * kPlaneB + ks * 32, 16, 1024);
+                            }
+#pragma unroll
+                            for (int p = 0; p < 3; ++p) {
+                                const int ia = p == 2 ? 1 : 0;  // hi, hi, lo
+                                const int ib = p == 1 ? 1 : 0;  // hi, lo, hi
+                                const uint32_t acc0 = (first && ks == 0 && p == 0) ? 0u : 1u;
+                                if (!ADJ) {
+                                    umma_bf16(dR, ad[ia], bd[ib], id_p, acc0);          // + Wr Xr
+                                    umma_bf16(dR, ad[2 + ia], bd[2 + ib], id_n, 1u);    // - Wi Xi
+                                    umma_bf16(dI, ad[ia], bd[2 + ib], id_p, acc0);      // + Wr Xi
+                                    umma_bf16(dI, ad[2 + ia], bd[ib], id_p, 1u);        // + Wi Xr
+                                } else {
+                                    umma_bf16(dR, ad[ia], bd[ib], id_p, acc0);          // + Wr Yr
+                                    umma_bf16(dR, ad[2 + ia], bd[2 + ib], id_p, 1u);    // + Wi Yi
+                                    umma_bf16(dI, ad[ia], bd[2 + ib], id_p, acc0);      // + Wr Yi
+                                    umma_bf16(dI, ad[2 + ia], bd[ib], id_n, 1u);        // - Wi Yr
+                                }
+                            }
+                        }
+                        first = false;
+                        umma_commit(&empty[stage]);
+                        *consumed_ctr = ++consumed;
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (ok) umma_commit(&acc_full[buf]);
+                }
+            }
+            umma_commit(mma_done);
+            mbar_wait_drain(mma_done, 0);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int lg = warp & 3;
+        const int row = lg * 32 + lane;
+        int ci = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int bin = u / a.mtiles, mt = u % a.mtiles;
+            const int grow = mt * 128 + row;
+            for (int c0 = 0; c0 < a.nkb; c0 += kChunkKb, ++ci) {
+                const int buf = ci & 1;
+                if (!mbar_wait(&acc_full[buf], (uint32_t)((ci >> 1) & 1), abort_flag, a.err, 14)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t re[16], im[16];
+                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16) + buf * 32;
+                tmem_ld16(tb, re);
+                tmem_ld16(tb + 16, im);
+                tmem_wait_ld();
+                if (grow < a.nrows) {
+                    float2* o = a.out + (int64_t)bin * a.ntile * a.ld + grow;
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        if (t < a.ntile) {
+                            float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.ld);
+                            const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
+                            if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
+                            else red_add_v2(dst, vr, vi);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acc_empty[buf]);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+          uint32_t b1) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t str[2] = {d0 * 2, d0 * 2 * d1};
+    const cuuint32_t box[3] = {b0, b1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, str, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct CgState {
+    CUtensorMap fa[4], fb[4], aa[4], ab[4];
+    CgArgs fwd, adj;
+    int fwd_grid = 0, adj_grid = 0;
+    int* err = nullptr;
+};
+
+}  // namespace
+
+cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::string* why) {
+    CgState* s = new (std::nothrow) CgState();
+    if (!s) return cudaErrorMemoryAllocation;
+    std::memset(s, 0, sizeof(*s));
+    *state = s;
+    cudaError_t e = cudaMalloc(&s->err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemset(s->err, 0, sizeof(int))) != cudaSuccess) return e;
+    for (int i = 0; i < 4; ++i) {
+        bool ok = map3(&s->fa[i], b.W[i], b.Cw, b.S, b.bins, 64, 128) &&
+                  map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64) &&
+                  map3(&s->fb[i], b.X[i], b.Cw, 16, b.bins, 64, 16) &&
+                  map3(&s->ab[i], b.Y[i], b.Sw, 16, b.bins, 64, 16);
+        if (!ok) {
+            if (why) *why = "cuTensorMapEncodeTiled failed for the spectra planes";
+            return cudaErrorInvalidValue;
+        }
+    }
+    CgArgs& f = s->fwd;
+    f.nbins = b.bins;
+    f.ntile = b.ntile;
+    f.mtiles = (b.S + 127) / 128;
+    f.nkb = (b.Cw + 63) / 64;
+    f.nrows = b.S;
+    f.ld = b.Sf;
+    f.out = b.Yout;
+    f.err = s->err;
+    CgArgs& g = s->adj;
+    g = f;
+    g.mtiles = (b.C + 127) / 128;
+    g.nkb = (b.Sw + 63) / 64;
+    g.nrows = b.C;
+    g.ld = b.Cf;
+    g.out = b.Xout;
+    s->fwd_grid = std::min(f.nbins * f.mtiles, sm_count);
+    s->adj_grid = std::min(g.nbins * g.mtiles, sm_count);
+    e = cudaFuncSetAttribute(k_tc_cgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_cgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+cudaError_t cgemm_forward(void* state, cudaStream_t st) {
+    CgState* s = static_cast<CgState*>(state);
+    k_tc_cgemm<false><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fa[2], s->fa[3],
+                                                                 s->fb[0], s->fb[1], s->fb[2], s->fb[3],
+                                                                 s->fwd);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cgemm_adjoint(void* state, cudaStream_t st) {
+    CgState* s = static_cast<CgState*>(state);
+    k_tc_cgemm<true><<<s->adj_grid, kThreads, kSmemBytes, st>>>(s->aa[0], s->aa[1], s->aa[2], s->aa[3],
+                                                                s->ab[0], s->ab[1], s->ab[2], s->ab[3],
+                                                                s->adj);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int cgemm_error(void* state) {
+    CgState* s = static_cast<CgState*>(state);
+    if (!s || !s->err) return 0;
+    int h = 0;
+    if (cudaMemcpy(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (h) cudaMemset(s->err, 0, sizeof(int));
+    return h;
+}
+
+void cgemm_destroy(void* state) {
+    CgState* s = static_cast<CgState*>(state);
+    if (!s) return;
+    if (s->err) cudaFree(s->err);
+    delete s;
+}
+
+}  // namespace lfd

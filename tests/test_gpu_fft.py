@@ -1,6 +1,8 @@
-"""Parity of the FFT variant (overlap-save on the lenslet grid, FP32) with the
-FP64 oracle through the C ABI: relative L2 <= 1e-5 per projection and <= 1e-4
-after RL iterations, predicted iteration equal to the oracle's."""
+"""Parity of the FFT variant (overlap-save on the lenslet grid) with the FP64
+oracle through the C ABI. FP32 contractions: relative L2 <= 1e-5 per
+projection and <= 1e-4 after RL iterations. Split-BF16 tensor-core
+contractions: <= 1e-4 per projection and <= 5e-4 after RL iterations. The
+predicted iteration must equal the oracle's."""
 import os
 
 import numpy as np
@@ -16,6 +18,9 @@ from gpu_util import Ctx, lib, rel_l2
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL_PROJ = {"fp32": 1e-5, "bf16x3": 1e-4}
+TOL_RL = {"fp32": 1e-4, "bf16x3": 5e-4}
+PRECS = ["fp32", "bf16x3"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,60 +40,64 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_fft_projections_match_oracle(shape):
+def test_fft_projections_match_oracle(shape, prec):
     N, Ly, Lx, Nz, k = shape
     H, W, P = Ly * N, Lx * N, k * N
     psf = synth.random_psf(21, N, Nz, P, density=0.8)
     v = synth.random_volume(22, Nz, H, W)
     r = synth.random_image(23, H, W, 0.1, 2.0)
-    with Ctx(psf, N, H, W, variant="fft") as c:
+    with Ctx(psf, N, H, W, variant="fft", precision=prec) as c:
         hv = c.forward(v)
         ht = c.backward(r)
     ef = rel_l2(hv, oracle.forward(psf, N, v))
     eb = rel_l2(ht, oracle.backward(psf, N, r))
-    print("%s fft forward %.2e backward %.2e" % (shape, ef, eb))
-    assert ef <= 1e-5 and eb <= 1e-5
+    print("%s fft %s forward %.2e backward %.2e" % (shape, prec, ef, eb))
+    assert ef <= TOL_PROJ[prec] and eb <= TOL_PROJ[prec]
 
 
-def test_fft_rl_config0():
+@pytest.mark.parametrize("prec", PRECS)
+def test_fft_rl_config0(prec):
     g = synth.CONFIGS[0]
     psf = synth.make_psf(0)
     y = synth.poisson_data(oracle.forward(psf, g.nnum, synth.ground_truth(0)), g.scale,
                            g.background, 200)
     XS, YS = metric.region_size(g.nnum, g.H, g.W)
     ref = orl.rl(psf, g.nnum, y, g.iterations, XS, YS)
-    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision=prec) as c:
         v, done, pred, ent, flux = c.rl(y, g.iterations)
         vs, done_s, pred_s, _, _ = c.rl(y, g.iterations, stop=True)
-    assert rel_l2(v, ref.v) <= 1e-4
+    assert rel_l2(v, ref.v) <= TOL_RL[prec]
     assert pred == ref.predicted
-    np.testing.assert_allclose(ent, ref.entropy, rtol=1e-5)
-    np.testing.assert_allclose(flux, ref.flux, rtol=1e-5)
+    np.testing.assert_allclose(ent, ref.entropy, rtol=1e-5 if prec == "fp32" else 1e-3)
+    np.testing.assert_allclose(flux, ref.flux, rtol=1e-5 if prec == "fp32" else 1e-4)
     assert done_s == pred_s == ref.predicted
 
 
-def test_fft_rl_config1_against_stored_oracle_run():
+@pytest.mark.parametrize("prec", PRECS)
+def test_fft_rl_config1_against_stored_oracle_run(prec):
     d = np.load(os.path.join(GOLDEN, "lf_mid_615px_31z_psf165.npz"))
     g = synth.CONFIGS[1]
     psf = synth.make_psf(1)
     y = (d["y_counts"].astype(np.float64) + float(d["background"])).astype(np.float32)
     vox = d["sample_vox"]
-    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision=prec) as c:
         v, done, pred, ent, flux = c.rl(y, int(d["n_iter"]))
     e = rel_l2(v[vox[:, 0], vox[:, 1], vox[:, 2]], d["v_last"])
-    print("config 1 fft: sampled rel-L2 %.2e, predicted %d" % (e, pred))
-    assert e <= 1e-4
+    print("config 1 fft %s: sampled rel-L2 %.2e, predicted %d" % (prec, e, pred))
+    assert e <= TOL_RL[prec]
     assert pred == int(d["predicted"])
     # The transforms leave an absolute error floor (~1e-6 of each patch's
     # largest value); in dark voxels that is a larger relative error, and the
     # z-maximum turns it into a small upward bias of the MIP background, which
     # moves the entropy by up to ~1e-4 relative (measured 8e-5). The volume and
     # the predicted iteration stay within their tolerances.
-    np.testing.assert_allclose(ent, d["entropy"], rtol=2e-4)
+    np.testing.assert_allclose(ent, d["entropy"], rtol=2e-4 if prec == "fp32" else 1e-3)
 
 
-def test_fft_full_size_sampled_projections():
+@pytest.mark.parametrize("prec", PRECS)
+def test_fft_full_size_sampled_projections(prec):
     g = synth.CONFIGS[2]
     psf = synth.make_psf(2)
     v = synth.beads(102, g.nz, g.H, g.W, g.beads, g.bead_radius, g.amp_lo).astype(np.float32)
@@ -97,16 +106,16 @@ def test_fft_full_size_sampled_projections():
     vox = synth.sample_indices(9, 256, (g.nz, g.H, g.W))
     pix[:4] = [[0, 0], [g.H - 1, g.W - 1], [0, g.W - 1], [g.H - 1, 0]]
     vox[:2] = [[0, 0, 0], [g.nz - 1, g.H - 1, g.W - 1]]
-    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision=prec) as c:
         hv = c.forward(v)
         ht = c.backward(r)
     ef = rel_l2(hv[pix[:, 0], pix[:, 1]], oracle.forward_at(psf, g.nnum, v, pix))
     eb = rel_l2(ht[vox[:, 0], vox[:, 1], vox[:, 2]], oracle.backward_at(psf, g.nnum, r, vox))
-    print("config 2 fft: sampled forward %.2e backward %.2e" % (ef, eb))
-    assert ef <= 1e-5 and eb <= 1e-5
+    print("config 2 fft %s: sampled forward %.2e backward %.2e" % (prec, ef, eb))
+    assert ef <= TOL_PROJ[prec] and eb <= TOL_PROJ[prec]
 
 
-def test_fft_rejects_tensor_core_precision():
+def test_fft_rejects_plain_bf16():
     from paper_2208_11422_gb300 import lfd
     g = synth.CONFIGS[0]
     psf = synth.make_psf(0)
