@@ -79,6 +79,13 @@ typedef struct {
     int l2_over_region;   /* 1: L2 norm of Eq. 12 over the region S (default);
                              0: over the whole DCT (= 2-norm of the MIP)            */
     int variant;          /* projection formulation, lfd_variant                     */
+    int max_frames;       /* frames one lfd_rl_iterate_batch call may carry (>= 1;
+                             more than 1 needs LFD_FFT); buffers are sized for it   */
+    int use_graph;        /* 1 (default): replay each RL iteration as a captured CUDA
+                             graph (not while profiling); 0: plain launches         */
+    int fft_size;         /* LFD_FFT transform size per axis: 32 or 64; 0 (default)
+                             picks by a bandwidth / arithmetic cost model (see
+                             lfd_autotune for picking by measurement)               */
 } lfd_options;
 
 /* How the two projections are computed (same results up to rounding). */
@@ -138,6 +145,38 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
 lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n,
                           int stop_at_predicted, int* iters_done, int* predicted,
                           double* entropy_hist, double* flux_hist, void* cuda_stream);
+
+/* lfd_rl_iterate for nframes frames that share the context's PSF and sensor
+ * shape (e.g. a time-lapse), all advanced together: every stage of an
+ * iteration is one launch over all frames, and the iteration is replayed as a
+ * captured CUDA graph. Each frame keeps its own entropy history and, with
+ * stop_at_predicted, stops at its own predicted iteration (the other frames
+ * go on, up to n).
+ *   nframes      1 .. max_frames given at lfd_create
+ *   y            [nframes][H][W], v [nframes][Nz][H][W] (host or device)
+ *   iters_done, predicted      arrays of nframes ints (may be NULL)
+ *   entropy_hist, flux_hist    host arrays of nframes * n doubles (frame-major,
+ *                              may be NULL); entries past a frame's last
+ *                              iteration are NaN
+ * The other arguments and the errors are those of lfd_rl_iterate, plus
+ * LFD_EINVAL when nframes is outside 1 .. max_frames. Synchronises the stream. */
+lfd_status lfd_rl_iterate_batch(lfd_ctx* ctx, int nframes, const float* y, float* v, int n,
+                                int stop_at_predicted, int* iters_done, int* predicted,
+                                double* entropy_hist, double* flux_hist, void* cuda_stream);
+
+/* Picks the fastest LFD_FFT transform size for this PSF, sensor shape and
+ * opt->max_frames by measurement: for each feasible size a context is created,
+ * one RL iteration of max_frames frames of a constant image is run to warm up
+ * and two more are timed with CUDA events; the contexts are destroyed again.
+ *   opt          options of the context to tune (variant must be LFD_FFT)
+ *   best_size    (out) 32 or 64, to pass as opt->fft_size to lfd_create
+ *   ms_per_iter  (out, may be NULL) measured time of one batched iteration of
+ *                the winner, in milliseconds
+ * Errors: LFD_EINVAL, LFD_EUNSUPPORTED (no size fits), and those of lfd_create.
+ * Allocates and frees device memory; synchronises the stream. */
+lfd_status lfd_autotune(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                        const lfd_options* opt, void* cuda_stream, int* best_size,
+                        float* ms_per_iter);
 
 /* DCT entropy (Eq. 12 over the region of Eq. 6) of the z-maximum projection of
  * the volume v [Nz][H][W] (host or device); result in *entropy (host).

@@ -19,6 +19,7 @@
 // Transforms are radix-2 in shared memory, one warp per 1-D transform; the
 // contractions run on the CUDA cores in FP32, streaming the spectra once per
 // projection with every tile's accumulators in registers.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -67,13 +68,18 @@ __device__ __forceinline__ void warp_fft(float2* a) {
 
 // channel-major images [nch][Ly][Lx]; patch of tile (ty, tx) starts at
 // lenslet (ty*B - h, tx*B - h), zero outside the grid
+// (several frames: column col = frame * ntile + tile, frames fstride floats apart)
 struct ImgSrc {
     const float* img;
-    int Ly, Lx, h, B, tiles_x;
-    __device__ float operator()(int c, int tile, int r, int x) const {
+    int Ly, Lx, h, B, tiles_x, ntile;
+    int64_t fstride;
+    __device__ float operator()(int c, int col, int r, int x) const {
+        const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
         const int Iy = ty * B - h + r, Ix = tx * B - h + x;
-        return (Iy >= 0 && Iy < Ly && Ix >= 0 && Ix < Lx) ? img[((int64_t)c * Ly + Iy) * Lx + Ix] : 0.f;
+        return (Iy >= 0 && Iy < Ly && Ix >= 0 && Ix < Lx)
+                   ? img[f * fstride + ((int64_t)c * Ly + Iy) * Lx + Ix]
+                   : 0.f;
     }
 };
 
@@ -147,23 +153,26 @@ __global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, Out 
 // forward output: Hv of polyphase channel s for lenslet (Iy, Ix); optionally
 // stored as an image [H][W] and / or turned into r = y / (Hv + eps)
 struct HvDst {
-    float* img;        // [H][W] or null
-    float* rcm;        // [S][Ly][Lx] ratio or null
-    const float* ycm;  // [S][Ly][Lx]
-    float* rimg;       // [H][W] ratio in image layout or null
+    float* img;        // [frames][H][W] or null
+    float* rcm;        // [frames][S][Ly][Lx] ratio or null
+    const float* ycm;  // [frames][S][Ly][Lx]
+    float* rimg;       // [frames][H][W] ratio in image layout or null
     float eps;
-    int N, W, Ly, Lx, B, tiles_x;
-    __device__ void operator()(int s, int tile, int i, int j, float hv) const {
+    int N, W, Ly, Lx, B, tiles_x, ntile;
+    int64_t fs_cm, fs_img;  // frame strides
+    __device__ void operator()(int s, int col, int i, int j, float hv) const {
+        const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
         const int Iy = ty * B + i, Ix = tx * B + j;
         if (Iy >= Ly || Ix >= Lx) return;
-        if (img) img[((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N] = hv;
+        const int64_t pix = f * fs_img + ((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N;
+        if (img) img[pix] = hv;
         if (rcm) {
-            const int64_t o = ((int64_t)s * Ly + Iy) * Lx + Ix;
+            const int64_t o = f * fs_cm + ((int64_t)s * Ly + Iy) * Lx + Ix;
             const float den = hv + eps;
             const float r = den > 0.f ? ycm[o] / den : 0.f;
             rcm[o] = r;
-            if (rimg) rimg[((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N] = r;
+            if (rimg) rimg[pix] = r;
         }
     }
 };
@@ -171,17 +180,19 @@ struct HvDst {
 // backward output: H^T r of channel c = (z, t) for lenslet (Iy, Ix), into a
 // channel-major volume or a stack-order volume [Nz][H][W]
 struct VolDst {
-    float* cm;     // [C][Ly][Lx] or null
-    float* stack;  // [Nz][H][W] or null
-    int N, S, H, W, Ly, Lx, B, tiles_x;
-    __device__ void operator()(int c, int tile, int i, int j, float x) const {
+    float* cm;     // [frames][C][Ly][Lx] or null
+    float* stack;  // [frames][Nz][H][W] or null
+    int N, S, H, W, Ly, Lx, B, tiles_x, ntile;
+    int64_t fs_cm, fs_stack;  // frame strides
+    __device__ void operator()(int c, int col, int i, int j, float x) const {
+        const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
         const int Iy = ty * B + i, Ix = tx * B + j;
         if (Iy >= Ly || Ix >= Lx) return;
-        if (cm) cm[((int64_t)c * Ly + Iy) * Lx + Ix] = x;
+        if (cm) cm[f * fs_cm + ((int64_t)c * Ly + Iy) * Lx + Ix] = x;
         if (stack) {
             const int z = c / S, t = c % S;
-            stack[((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
+            stack[f * fs_stack + ((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
         }
     }
 };
@@ -243,13 +254,13 @@ template <int NT>
 __global__ void __launch_bounds__(256) k_contract_fwd(const float2* __restrict__ Wf,
                                                       const float2* __restrict__ Xh,
                                                       float2* __restrict__ Yh, int S, int Sf,
-                                                      int C, int Cf, int ntile) {
+                                                      int C, int Cf, int ntile, int col0, int ncol) {
     __shared__ __align__(16) float2 Xs[kFC][NT];
     const int bin = blockIdx.x;
     const int s = threadIdx.x;
     const bool active = s < S;
     const float2* wrow = Wf + ((int64_t)bin * S + (active ? s : 0)) * Cf;
-    const float2* Xb = Xh + (int64_t)bin * ntile * Cf;
+    const float2* Xb = Xh + ((int64_t)bin * ncol + col0) * Cf;
     float ar[NT], ai[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) ar[t] = ai[t] = 0.f;
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(256) k_contract_fwd(const float2* __restrict__
         }
     }
     if (!active) return;
-    float2* Yb = Yh + (int64_t)bin * ntile * Sf;
+    float2* Yb = Yh + ((int64_t)bin * ncol + col0) * Sf;
 #pragma unroll
     for (int t = 0; t < NT; ++t)
         if (t < ntile) Yb[(int64_t)t * Sf + s] = make_float2(ar[t], ai[t]);
@@ -306,12 +317,12 @@ template <int NT>
 __global__ void __launch_bounds__(256) k_contract_adj(const float2* __restrict__ Wf,
                                                       const float2* __restrict__ Yh,
                                                       float2* __restrict__ Xh, int S, int Sf,
-                                                      int C, int Cf, int ntile) {
+                                                      int C, int Cf, int ntile, int col0, int ncol) {
     extern __shared__ float2 Ys[];  // [S][NT]
     const int bin = blockIdx.x;
     const int c = blockIdx.y * 512 + 2 * threadIdx.x;
     const float2* Wb = Wf + (int64_t)bin * S * Cf;
-    const float2* Yb = Yh + (int64_t)bin * ntile * Sf;
+    const float2* Yb = Yh + ((int64_t)bin * ncol + col0) * Sf;
     for (int e = threadIdx.x; e < S * NT; e += blockDim.x) {
         const int sidx = e / NT, t = e % NT;
         Ys[e] = t < ntile ? Yb[(int64_t)t * Sf + sidx] : make_float2(0.f, 0.f);
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(256) k_contract_adj(const float2* __restrict__
         }
         w = wn;
     }
-    float2* Xb = Xh + (int64_t)bin * ntile * Cf;
+    float2* Xb = Xh + ((int64_t)bin * ncol + col0) * Cf;
 #pragma unroll
     for (int t = 0; t < NT; ++t)
         if (t < ntile)
@@ -345,21 +356,48 @@ __global__ void __launch_bounds__(256) k_contract_adj(const float2* __restrict__
 
 template <int NT>
 cudaError_t run_contract_fwd(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Xh,
-                             float2* Yh, cudaStream_t st) {
-    k_contract_fwd<NT><<<p.bins, 256, 0, st>>>(Wf, Xh, Yh, g.S, p.Sf, g.C, p.Cf, p.ntile);
+                             float2* Yh, int col0, int ngrp, int ncol, cudaStream_t st) {
+    k_contract_fwd<NT><<<p.bins, 256, 0, st>>>(Wf, Xh, Yh, g.S, p.Sf, g.C, p.Cf, ngrp, col0, ncol);
     count_launch();
     return cudaGetLastError();
 }
 template <int NT>
 cudaError_t run_contract_adj(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Yh,
-                             float2* Xh, cudaStream_t st) {
+                             float2* Xh, int col0, int ngrp, int ncol, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)g.S * NT;
     cudaError_t e = cudaFuncSetAttribute(k_contract_adj<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)p.bins, (unsigned)((p.Cf + 511) / 512));
-    k_contract_adj<NT><<<grid, 256, smem, st>>>(Wf, Yh, Xh, g.S, p.Sf, g.C, p.Cf, p.ntile);
+    k_contract_adj<NT><<<grid, 256, smem, st>>>(Wf, Yh, Xh, g.S, p.Sf, g.C, p.Cf, ngrp, col0, ncol);
     count_launch();
     return cudaGetLastError();
+}
+
+// FP32 contractions over all ncol columns, in groups of at most 16 (each
+// group streams the spectra once)
+cudaError_t contract_fwd_all(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Xh,
+                             float2* Yh, int ncol, cudaStream_t st) {
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
+        const int n = std::min(16, ncol - c0);
+        cudaError_t e = n <= 1 ? run_contract_fwd<1>(p, g, Wf, Xh, Yh, c0, n, ncol, st)
+                        : n <= 4 ? run_contract_fwd<4>(p, g, Wf, Xh, Yh, c0, n, ncol, st)
+                        : n <= 9 ? run_contract_fwd<9>(p, g, Wf, Xh, Yh, c0, n, ncol, st)
+                                 : run_contract_fwd<16>(p, g, Wf, Xh, Yh, c0, n, ncol, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+cudaError_t contract_adj_all(const FftPlan& p, const Geo& g, const float2* Wf, const float2* Yh,
+                             float2* Xh, int ncol, cudaStream_t st) {
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
+        const int n = std::min(16, ncol - c0);
+        cudaError_t e = n <= 1 ? run_contract_adj<1>(p, g, Wf, Yh, Xh, c0, n, ncol, st)
+                        : n <= 4 ? run_contract_adj<4>(p, g, Wf, Yh, Xh, c0, n, ncol, st)
+                        : n <= 9 ? run_contract_adj<9>(p, g, Wf, Yh, Xh, c0, n, ncol, st)
+                                 : run_contract_adj<16>(p, g, Wf, Yh, Xh, c0, n, ncol, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Exact backprojection at listed voxels, by direct summation over each voxel's
@@ -369,14 +407,17 @@ cudaError_t run_contract_adj(const FftPlan& p, const Geo& g, const float2* Wf, c
 // with c = (z, t = ty*N + tx), i' = Iy*N + ty, j' = Ix*N + tx. The FFT variant
 // uses it for voxels whose sensitivity H^T 1 is so small that the transforms'
 // absolute error floor would dominate their update.
-__global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, const float* __restrict__ rimg,
-                            const float* __restrict__ psf, Geo g, float* __restrict__ xcm) {
+__global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, int nf,
+                            const float* __restrict__ rimg, const float* __restrict__ psf, Geo g,
+                            float* __restrict__ xcm) {
     const int lane = threadIdx.x & 31;
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     const int c0 = (g.P - 1) / 2;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < n;
-         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t idx = list[q];
+    for (int64_t qq = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; qq < n * nf;
+         qq += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int f = (int)(qq / n);
+        const int64_t idx = list[qq % n];
+        const float* rimg_f = rimg + (int64_t)f * g.H * g.W;
         const int c = (int)(idx / L2);
         const int64_t l = idx % L2;
         const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
@@ -387,14 +428,14 @@ __global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, const f
         const int mj0 = max(0, c0 - jp), mj1 = min(g.P, g.W + c0 - jp);
         float acc = 0.f;
         for (int mi = mi0; mi < mi1; ++mi) {
-            const float* rr = rimg + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
+            const float* rr = rimg_f + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
             const float* kk = K + (int64_t)mi * g.P;
             float row = 0.f;
             for (int mj = mj0 + lane; mj < mj1; mj += 32) row = fmaf(rr[mj], kk[mj], row);
             acc += row;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) xcm[idx] = acc;
+        if (lane == 0) xcm[(int64_t)f * g.C * L2 + idx] = acc;
     }
 }
 
@@ -453,6 +494,14 @@ __global__ void __launch_bounds__(256) k_update_cm(const float* __restrict__ vin
                                                    double* __restrict__ flux_part) {
     __shared__ double red[8];
     const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.S * L2;
+    {  // frame blockIdx.y: shift the per-frame arrays (H^T 1 is shared)
+        const int64_t fv = (int64_t)blockIdx.y * g.C * L2;
+        vin += fv;
+        vout += fv;
+        x += fv;
+        mip += (int64_t)blockIdx.y * g.H * g.W;
+        flux_part += (int64_t)blockIdx.y * gridDim.x;
+    }
     double flux = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -575,10 +624,11 @@ cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int 
 }  // namespace
 
 // ------------------------------------------------------------------ plan --
-bool fft_plan_for(const Geo& g, FftPlan* p) {
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames) {
     FftPlan best{};
     double best_t = 1e300;
     for (int F : {32, 64}) {
+        if (force_F && F != force_F) continue;
         const int B = F - 2 * g.h;
         if (B < 4) continue;
         FftPlan q{};
@@ -588,8 +638,8 @@ bool fft_plan_for(const Geo& g, FftPlan* p) {
         q.tiles_y = (g.Ly + B - 1) / B;
         q.tiles_x = (g.Lx + B - 1) / B;
         q.ntile = q.tiles_y * q.tiles_x;
-        if (q.ntile > 16) continue;
-        if (g.S > 256) continue;  // one thread per phase in the forward contraction
+        if (q.ntile > 64) continue;
+        if (g.S > 256) continue;  // one thread per phase in the FP32 forward contraction
         q.bins = F * (F / 2 + 1);
         q.Cf = (g.C + 3) & ~3;
         q.Sf = (g.S + 3) & ~3;
@@ -597,8 +647,10 @@ bool fft_plan_for(const Geo& g, FftPlan* p) {
         q.Sw = (g.S + 7) & ~7;
         const double spectra = (double)q.bins * g.S * q.Cf * 8.0;
         if (spectra > 96e9) continue;  // keep the cached spectra well inside HBM
-        const double flops = (double)q.bins * g.S * q.ntile * g.C * 8.0;
-        const double t = std::max(spectra / 6.0e12, flops / 6.0e13);
+        const double flops = (double)q.bins * g.S * q.ntile * frames * g.C * 8.0;
+        // transforms: one F x F patch per tile, frame and channel
+        const double xform = (double)q.ntile * frames * (g.C + g.S) * 2.0 * F * F * 8.0;
+        const double t = std::max(spectra / 6.0e12, flops / 6.0e13) + xform / 4.0e12;
         if (t < best_t) {
             best_t = t;
             best = q;
@@ -620,43 +672,41 @@ cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const Fft
     return r2c_any(p, src, g.C, p.Cf, g.S, b.Wf, nullptr, 0, st);
 }
 
-cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* vcm,
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* vcm,
                         float* img_out, float* rcm, const float* ycm, float* rimg, float eps,
                         cudaStream_t st, cudaEvent_t* ev) {
-    ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, p.ntile, nullptr, b.Xp, 16, st)
-                         : r2c_any(p, src, g.C, p.Cf, p.ntile, b.Xh, nullptr, 0, st);
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const int ncol = nf * p.ntile;
+    ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x, p.ntile, (int64_t)g.C * L2};
+    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, ncol, nullptr, b.Xp, b.ncolp, st)
+                         : r2c_any(p, src, g.C, p.Cf, ncol, b.Xh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (b.cg) e = cgemm_forward(b.cg, st);
-    else if (p.ntile <= 1) e = run_contract_fwd<1>(p, g, b.Wf, b.Xh, b.Yh, st);
-    else if (p.ntile <= 4) e = run_contract_fwd<4>(p, g, b.Wf, b.Xh, b.Yh, st);
-    else if (p.ntile <= 9) e = run_contract_fwd<9>(p, g, b.Wf, b.Xh, b.Yh, st);
-    else e = run_contract_fwd<16>(p, g, b.Wf, b.Xh, b.Yh, st);
+    e = b.cg ? cgemm_forward(b.cg, ncol, st) : contract_fwd_all(p, g, b.Wf, b.Xh, b.Yh, ncol, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
-    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(b.Yh, g.S, p.Sf, p.ntile, 2 * p.h, p.B, dst, st);
+    HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
+              (int64_t)g.S * L2, (int64_t)g.H * g.W};
+    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
 }
 
-cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* rcm,
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* rcm,
                          float* xcm, float* stack_out, cudaStream_t st, cudaEvent_t* ev) {
-    ImgSrc src{rcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, p.ntile, nullptr, b.Yp, 16, st)
-                         : r2c_any(p, src, g.S, p.Sf, p.ntile, b.Yh, nullptr, 0, st);
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const int ncol = nf * p.ntile;
+    ImgSrc src{rcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x, p.ntile, (int64_t)g.S * L2};
+    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, ncol, nullptr, b.Yp, b.ncolp, st)
+                         : r2c_any(p, src, g.S, p.Sf, ncol, b.Yh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (b.cg) e = cgemm_adjoint(b.cg, st);
-    else if (p.ntile <= 1) e = run_contract_adj<1>(p, g, b.Wf, b.Yh, b.Xh, st);
-    else if (p.ntile <= 4) e = run_contract_adj<4>(p, g, b.Wf, b.Yh, b.Xh, st);
-    else if (p.ntile <= 9) e = run_contract_adj<9>(p, g, b.Wf, b.Yh, b.Xh, st);
-    else e = run_contract_adj<16>(p, g, b.Wf, b.Yh, b.Xh, st);
+    e = b.cg ? cgemm_adjoint(b.cg, ncol, st) : contract_adj_all(p, g, b.Wf, b.Yh, b.Xh, ncol, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x};
-    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st)
-                     : run_c2r<32>(b.Xh, g.C, p.Cf, p.ntile, 0, p.B, dst, st);
+    VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
+               (int64_t)g.C * L2, (int64_t)g.Nz * g.H * g.W};
+    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st) {
@@ -684,12 +734,12 @@ cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st
     count_launch();
     return cudaGetLastError();
 }
-cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, const float* psf,
-                             const Geo& g, float* xcm, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n * 32 + 255) / 256;
+cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, int nf, const float* rimg,
+                             const float* psf, const Geo& g, float* xcm, cudaStream_t st) {
+    if (n <= 0 || nf <= 0) return cudaSuccess;
+    int64_t blocks = (n * nf * 32 + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    k_exact_bwd<<<(unsigned)blocks, 256, 0, st>>>(list, n, rimg, psf, g, xcm);
+    k_exact_bwd<<<(unsigned)blocks, 256, 0, st>>>(list, n, nf, rimg, psf, g, xcm);
     count_launch();
     return cudaGetLastError();
 }
@@ -697,8 +747,9 @@ cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, 
 // one item per thread (no grid-stride tail), one flux partial per block
 int update_cm_blocks(const Geo& g) { return (int)(((int64_t)g.S * g.Ly * g.Lx + 255) / 256); }
 cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
-                             const Geo& g, float* mip, double* flux_part, cudaStream_t st) {
-    k_update_cm<<<update_cm_blocks(g), 256, 0, st>>>(vin, vout, x, inv, g, mip, flux_part);
+                             const Geo& g, int nf, float* mip, double* flux_part, cudaStream_t st) {
+    dim3 grid((unsigned)update_cm_blocks(g), (unsigned)nf);
+    k_update_cm<<<grid, 256, 0, st>>>(vin, vout, x, inv, g, mip, flux_part);
     count_launch();
     return cudaGetLastError();
 }

@@ -25,12 +25,14 @@ struct FftBuffers {
     __nv_bfloat16* Wp[4] = {};
     __nv_bfloat16* Xp[4] = {};
     __nv_bfloat16* Yp[4] = {};
+    int ncolp = 16;           // rows per bin of the Xp / Yp planes (columns padded to 16)
     void* cg = nullptr;
 };
 
-// picks F by a bandwidth / FP32 cost model; false if no plan fits (> 16 tiles,
-// spectra too large, or more than 225 phases)
-bool fft_plan_for(const Geo& g, FftPlan* p);
+// picks F (or uses force_F if non-zero) by a bandwidth / arithmetic cost model
+// for `frames` frames; false if no plan fits (> 64 tiles, spectra too large,
+// or more than 256 phases)
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F = 0, int frames = 1);
 
 // half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad]) into b.Wf or b.Wp
 cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const FftBuffers& b,
@@ -40,11 +42,15 @@ cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const Fft
 // forward projection of the channel-major volume vcm [C][Ly][Lx]; writes the
 // image Hv to img_out [H][W] and / or r = y / (Hv + eps) to rcm [S][Ly][Lx]
 // (and to rimg [H][W] in image layout when rimg is not null)
-cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* vcm,
+// nf frames share one transform / contraction launch: column col = frame *
+// ntile + tile; per-frame arrays follow each other (frame strides C*Ly*Lx for
+// channel-major volumes, S*Ly*Lx for polyphase images, H*W / Nz*H*W for images
+// and stack-order volumes)
+cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* vcm,
                         float* img_out, float* rcm, const float* ycm, float* rimg, float eps,
                         cudaStream_t st, cudaEvent_t* ev);
 // backprojection of rcm [S][Ly][Lx] into xcm [C][Ly][Lx] and / or a stack-order volume
-cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, const float* rcm,
+cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* rcm,
                          float* xcm, float* stack_out, cudaStream_t st, cudaEvent_t* ev);
 
 cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st);
@@ -55,10 +61,11 @@ cudaError_t launch_inv_cm(const float* x, int64_t n, float* inv, cudaStream_t st
 // exact backprojection of rimg [H][W] at the voxels list[0..n) (linear
 // channel-major indices c*Ly*Lx + Iy*Lx + Ix), written into xcm; psf is the
 // original [Nz][Nnum][Nnum][P][P] array
-cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, const float* rimg, const float* psf,
-                             const Geo& g, float* xcm, cudaStream_t st);
+cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, int nf, const float* rimg,
+                             const float* psf, const Geo& g, float* xcm, cudaStream_t st);
 int update_cm_blocks(const Geo& g);
+// one flux partial per block: update_cm_blocks(g) per frame, frame-major
 cudaError_t launch_update_cm(const float* vin, float* vout, const float* x, const float* inv,
-                             const Geo& g, float* mip, double* flux_part, cudaStream_t st);
+                             const Geo& g, int nf, float* mip, double* flux_part, cudaStream_t st);
 
 }  // namespace lfd

@@ -102,6 +102,12 @@ __global__ void k_dct_rows(const float* __restrict__ f, const double* __restrict
     extern __shared__ float row[];
     __shared__ double red[32];
     const int y = blockIdx.x;
+    {  // frame blockIdx.y
+        const int64_t H = gridDim.x;
+        f += (int64_t)blockIdx.y * H * W;
+        G += (int64_t)blockIdx.y * H * XS;
+        rowE2 += (int64_t)blockIdx.y * H;
+    }
     double e2 = 0.0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const float a = f[(int64_t)y * W + x];
@@ -125,6 +131,8 @@ __global__ void k_dct_rows(const float* __restrict__ f, const double* __restrict
 __global__ void k_dct_cols(const double* __restrict__ G, const double* __restrict__ cosH, int H,
                            int XS, int YS, double* __restrict__ coef) {
     const int u = blockIdx.x;
+    G += (int64_t)blockIdx.y * H * XS;  // frame blockIdx.y
+    coef += (int64_t)blockIdx.y * XS * YS;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int v = w; v < YS; v += nw) {
         double s = 0.0;
@@ -142,8 +150,17 @@ __global__ void k_dct_cols(const double* __restrict__ G, const double* __restric
 // flux total; single block, fixed reduction order.
 __global__ void k_entropy(const double* __restrict__ coef, const double* __restrict__ rowE2, int H,
                           int XS, int YS, int l2_over_region, const double* __restrict__ flux_part,
-                          int nflux, double* __restrict__ out_entropy, double* __restrict__ out_flux) {
+                          int nflux, double* __restrict__ out_entropy, double* __restrict__ out_flux,
+                          int out_stride) {
     __shared__ double red[32];
+    {  // frame blockIdx.x
+        const int fr = blockIdx.x;
+        coef += (int64_t)fr * XS * YS;
+        rowE2 += (int64_t)fr * H;
+        if (flux_part) flux_part += (int64_t)fr * nflux;
+        out_entropy += (int64_t)fr * out_stride;
+        if (out_flux) out_flux += (int64_t)fr * out_stride;
+    }
     const int n = XS * YS;
     double a = 0.0;
     if (l2_over_region) {
@@ -164,7 +181,7 @@ __global__ void k_entropy(const double* __restrict__ coef, const double* __restr
     }
     const double ent = block_sum(e, red);
     double fl = 0.0;
-    for (int i = threadIdx.x; i < nflux; i += blockDim.x) fl += flux_part[i];
+    for (int i = threadIdx.x; flux_part && i < nflux; i += blockDim.x) fl += flux_part[i];
     const double flux = block_sum(fl, red);
     if (threadIdx.x == 0) {
         out_entropy[0] = norm > 0.0 ? -ent / (0.5 * (double)XS * (double)YS) : 0.0;
@@ -201,17 +218,17 @@ cudaError_t launch_mip_stack(const float* v, int Nz, int64_t HW, float* mip, cud
 cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH, int H, int W,
                           int XS, int YS, int l2_over_region, double* G, double* rowE2,
                           double* coef, const double* flux_part, int nflux, double* out_entropy,
-                          double* out_flux, cudaStream_t st) {
+                          double* out_flux, cudaStream_t st, int nf, int out_stride) {
     const size_t smem = (size_t)W * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_dct_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_dct_rows<<<H, 256, smem, st>>>(mip, cosW, W, XS, G, rowE2);
-    k_dct_cols<<<XS, 256, 0, st>>>(G, cosH, H, XS, YS, coef);
-    k_entropy<<<1, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
-                                 out_entropy, out_flux);
+    k_dct_rows<<<dim3(H, nf), 256, smem, st>>>(mip, cosW, W, XS, G, rowE2);
+    k_dct_cols<<<dim3(XS, nf), 256, 0, st>>>(G, cosH, H, XS, YS, coef);
+    k_entropy<<<nf, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
+                                  out_entropy, out_flux, out_stride);
     count_launch(3);
     return cudaGetLastError();
 }

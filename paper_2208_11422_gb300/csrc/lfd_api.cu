@@ -117,6 +117,8 @@ FftBuffers fbufs(const lfd_ctx* ctx) {
         b.Yp[i] = ctx->Yp[i];
     }
     b.cg = ctx->cg;
+    if (ctx->fft)
+        b.ncolp = (ctx->mf * static_cast<const FftPlan*>(ctx->fft)->ntile + 15) / 16 * 16;
     return b;
 }
 
@@ -164,8 +166,9 @@ int bwd_parts(const lfd_ctx* ctx, bool force_fp32 = false) {
 
 lfd_status ensure_stage(lfd_ctx* ctx, bool vol) {
     const Geo& g = ctx->g;
-    if (vol && !ctx->stage_vol) return dalloc(ctx, &ctx->stage_vol, (int64_t)g.Nz * g.H * g.W, false);
-    if (!vol && !ctx->stage_img) return dalloc(ctx, &ctx->stage_img, (int64_t)g.H * g.W, false);
+    if (vol && !ctx->stage_vol)
+        return dalloc(ctx, &ctx->stage_vol, (int64_t)ctx->mf * g.Nz * g.H * g.W, false);
+    if (!vol && !ctx->stage_img) return dalloc(ctx, &ctx->stage_img, (int64_t)ctx->mf * g.H * g.W, false);
     return LFD_OK;
 }
 
@@ -181,6 +184,12 @@ void free_all(lfd_ctx* ctx) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+    for (auto& ge : ctx->graph)
+        if (ge) cudaGraphExecDestroy(ge);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->wstream) cudaStreamDestroy(ctx->wstream);
     for (auto& e : ctx->prof.ev)
         if (e) cudaEventDestroy(e);
     ctx->prof.ev.clear();
@@ -219,6 +228,9 @@ void lfd_default_options(lfd_options* opt) {
     opt->YS = 0;
     opt->l2_over_region = 1;
     opt->variant = LFD_DIRECT;
+    opt->max_frames = 1;
+    opt->use_graph = 1;
+    opt->fft_size = 0;
 }
 
 lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q, double NA,
@@ -291,6 +303,9 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
     if (opt.variant == LFD_FFT && opt.precision != LFD_FP32 && opt.precision != LFD_BF16X3)
         return LFD_EINVAL;
+    if (opt.max_frames < 1 || opt.max_frames > 4096) return LFD_EINVAL;
+    if (opt.fft_size != 0 && opt.fft_size != 32 && opt.fft_size != 64) return LFD_EINVAL;
+    if (opt.max_frames > 1 && opt.variant != LFD_FFT) return LFD_EUNSUPPORTED;
     int XS = opt.XS, YS = opt.YS;
     if (XS <= 0 || YS <= 0) {
         if (lfd_region_size(Nnum, H, W, opt.dML_um, opt.Q, opt.NA, opt.lambda_um, &XS, &YS) != LFD_OK)
@@ -344,8 +359,8 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     const bool fft = ctx->opt.variant == LFD_FFT;
     FftPlan fplan{};
     if (fft) {
-        if (!fft_plan_for(g, &fplan)) {
-            ctx->err = "no FFT tiling fits this geometry (at most 16 tiles of 64 x 64, Nnum <= 15)";
+        if (!fft_plan_for(g, &fplan, ctx->opt.fft_size, ctx->opt.max_frames)) {
+            ctx->err = "no FFT tiling fits this geometry (at most 64 tiles, Nnum <= 15)";
             return bail(LFD_EUNSUPPORTED);
         }
         FftPlan* hp = new (std::nothrow) FftPlan(fplan);
@@ -357,24 +372,26 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     const int64_t wcount = g.taps() * g.Spad * (int64_t)g.Cpad;
     CREATE_TRY(dalloc(ctx, &ctx->W32, wcount, false));
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const int mf = ctx->mf = fft ? ctx->opt.max_frames : 1;
     if (fft) {
+        const int ncol = mf * fplan.ntile, ncolp = (ncol + 15) / 16 * 16;
         if (ctx->opt.precision == LFD_BF16X3) {
             for (int i = 0; i < 4; ++i) {
                 CREATE_TRY(dalloc(ctx, &ctx->Wp[i], (int64_t)fplan.bins * g.S * fplan.Cw, false));
-                CREATE_TRY(dalloc(ctx, &ctx->Xp[i], (int64_t)fplan.bins * 16 * fplan.Cw, true));
-                CREATE_TRY(dalloc(ctx, &ctx->Yp[i], (int64_t)fplan.bins * 16 * fplan.Sw, true));
+                CREATE_TRY(dalloc(ctx, &ctx->Xp[i], (int64_t)fplan.bins * ncolp * fplan.Cw, true));
+                CREATE_TRY(dalloc(ctx, &ctx->Yp[i], (int64_t)fplan.bins * ncolp * fplan.Sw, true));
             }
         } else {
             CREATE_TRY(dalloc(ctx, &ctx->Wf, (int64_t)fplan.bins * g.S * fplan.Cf, false));
         }
-        CREATE_TRY(dalloc(ctx, &ctx->Xh, (int64_t)fplan.bins * fplan.ntile * fplan.Cf, true));
-        CREATE_TRY(dalloc(ctx, &ctx->Yh, (int64_t)fplan.bins * fplan.ntile * fplan.Sf, true));
-        for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vcm[b], (int64_t)g.C * L2, true));
-        CREATE_TRY(dalloc(ctx, &ctx->Rcm, (int64_t)g.S * L2, true));
-        CREATE_TRY(dalloc(ctx, &ctx->Xcm, (int64_t)g.C * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Xh, (int64_t)fplan.bins * ncol * fplan.Cf, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Yh, (int64_t)fplan.bins * ncol * fplan.Sf, true));
+        for (int b = 0; b < 2; ++b) CREATE_TRY(dalloc(ctx, &ctx->Vcm[b], (int64_t)mf * g.C * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Rcm, (int64_t)mf * g.S * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->Xcm, (int64_t)mf * g.C * L2, true));
         CREATE_TRY(dalloc(ctx, &ctx->invcm, (int64_t)g.C * L2, true));
-        CREATE_TRY(dalloc(ctx, &ctx->ycm, (int64_t)g.S * L2, true));
-        CREATE_TRY(dalloc(ctx, &ctx->rimg, (int64_t)g.H * g.W, true));
+        CREATE_TRY(dalloc(ctx, &ctx->ycm, (int64_t)mf * g.S * L2, true));
+        CREATE_TRY(dalloc(ctx, &ctx->rimg, (int64_t)mf * g.H * g.W, true));
         CREATE_TRY(dalloc(ctx, &ctx->psf_dev, (int64_t)Nz * Nnum * Nnum * P * P, false));
         ctx->nflux = update_cm_blocks(g);
     } else {
@@ -397,16 +414,18 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         }
         ctx->nflux = g.Ly * g.Lx;
     }
-    CREATE_TRY(dalloc(ctx, &ctx->mip, (int64_t)g.H * g.W, true));
+    CREATE_TRY(dalloc(ctx, &ctx->mip, (int64_t)mf * g.H * g.W, true));
     CREATE_TRY(dalloc(ctx, &ctx->cosW, (int64_t)XS * g.W, false));
     CREATE_TRY(dalloc(ctx, &ctx->cosH, (int64_t)YS * g.H, false));
-    CREATE_TRY(dalloc(ctx, &ctx->G, (int64_t)g.H * XS, true));
-    CREATE_TRY(dalloc(ctx, &ctx->rowE2, (int64_t)g.H, true));
-    CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)XS * YS, true));
-    CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)std::max<int64_t>(ctx->nflux, L2), true));
-    ctx->hist_cap = 64;
-    CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * ctx->hist_cap, true));
+    CREATE_TRY(dalloc(ctx, &ctx->G, (int64_t)mf * g.H * XS, true));
+    CREATE_TRY(dalloc(ctx, &ctx->rowE2, (int64_t)mf * g.H, true));
+    CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)mf * XS * YS, true));
+    CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)mf * std::max<int64_t>(ctx->nflux, L2), true));
+    CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * mf, true));
     CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned, 4 * sizeof(double)));
+    CREATE_CK(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
+    CREATE_CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CREATE_CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
 
     // PSF to the device (a device pointer is read in place)
     const int64_t psf_count = (int64_t)Nz * Nnum * Nnum * P * P;
@@ -442,6 +461,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
             CgemmBuffers cb{};
             cb.bins = fplan.bins;
             cb.ntile = fplan.ntile;
+            cb.ncolp = (ctx->mf * fplan.ntile + 15) / 16 * 16;
             cb.S = g.S;
             cb.C = g.C;
             cb.Sw = fplan.Sw;
@@ -464,7 +484,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         }
         CREATE_CK(fft_init(fplan, g, ctx->W32, fbufs(ctx), st));
         CREATE_CK(launch_fill_cm(ctx->Rcm, (int64_t)g.S * L2, 1.0f, st));
-        CREATE_CK(fft_backward(fplan, g, fbufs(ctx), ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
+        CREATE_CK(fft_backward(fplan, g, fbufs(ctx), 1, ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
         // Voxels whose sensitivity H^T 1 is below kLowSensitivity of the largest
         // are dominated by the transforms' absolute error floor (~1e-7 of a
         // tile's largest value); list them once and backproject them exactly,
@@ -487,7 +507,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
                                           cudaMemcpyHostToDevice, st));
                 CREATE_TRY(ensure_stage(ctx, false));
                 CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
-                CREATE_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, ctx->stage_img, ctx->psf_dev, g,
+                CREATE_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, 1, ctx->stage_img, ctx->psf_dev, g,
                                            ctx->Xcm, st));
             }
         }
@@ -567,7 +587,7 @@ lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_st
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
-        LFD_CK(fft_forward(fp, g, fbufs(ctx), ctx->Vcm[0], yd, nullptr, nullptr, nullptr, 0.f, st,
+        LFD_CK(fft_forward(fp, g, fbufs(ctx), 1, ctx->Vcm[0], yd, nullptr, nullptr, nullptr, 0.f, st,
                            nullptr));
     } else {
         LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
@@ -605,8 +625,8 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_image_cm(rd, g, ctx->Rcm, st));
-        LFD_CK(fft_backward(fp, g, fbufs(ctx), ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
-        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, rd, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(fft_backward(fp, g, fbufs(ctx), 1, ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
+        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, 1, rd, ctx->psf_dev, g, ctx->Xcm, st));
         LFD_CK(launch_depoly_volume_cm(ctx->Xcm, g, vd, st));
     } else {
         LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
@@ -636,48 +656,139 @@ lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n) {
     return LFD_OK;
 }
 
-lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int stop_at_predicted,
-                          int* iters_done, int* predicted, double* entropy_hist, double* flux_hist,
-                          void* cuda_stream) {
-    if (!ctx) return LFD_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Enqueues one RL iteration for nf frames: reads iterate buffer `cur`, writes
+// the other one, leaves the frames' entropy and flux in ctx->hist. e9: nine
+// events to record between stages (profiling), or null.
+lfd_status iter_body(lfd_ctx* ctx, int nf, int cur, cudaStream_t st, cudaEvent_t* e9) {
+    const Geo& g = ctx->g;
+    const int nxt = cur ^ 1;
+    auto mark = [&](int i) -> cudaError_t { return e9 ? cudaEventRecord(e9[i], st) : cudaSuccess; };
+    const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
+    LFD_CK(mark(0));
+    if (fp) {
+        const FftBuffers fb = fbufs(ctx);
+        // forward with the ratio fused into its last transform
+        LFD_CK(fft_forward(*fp, g, fb, nf, ctx->Vcm[cur], nullptr, ctx->Rcm, ctx->ycm, ctx->rimg,
+                           ctx->opt.eps, st, e9 ? e9 + 1 : nullptr));
+        LFD_CK(mark(3));
+        LFD_CK(fft_backward(*fp, g, fb, nf, ctx->Rcm, ctx->Xcm, nullptr, st, e9 ? e9 + 4 : nullptr));
+        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, nf, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(mark(6));
+        LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, nf, ctx->mip,
+                                ctx->flux_part, st));
+    } else {
+        const int fpart = fwd_parts(ctx), bp = bwd_parts(ctx);
+        __nv_bfloat16* rhi = uses_tc(ctx) ? ctx->Rpb[0] : nullptr;
+        __nv_bfloat16* rlo = uses_lo(ctx) ? ctx->Rpb[1] : nullptr;
+        __nv_bfloat16* vhi = uses_tc(ctx) ? ctx->Vpb[0] : nullptr;
+        __nv_bfloat16* vlo = uses_lo(ctx) ? ctx->Vpb[1] : nullptr;
+        LFD_CK(mark(1));
+        LFD_TRY(run_forward(ctx, cur, st));
+        LFD_CK(mark(2));
+        LFD_CK(launch_fwd_finish_ratio(ctx->Fwd, fpart, ctx->ypoly, ctx->opt.eps, g, ctx->Rp32, rhi, rlo, st));
+        LFD_CK(mark(3));
+        LFD_CK(mark(4));
+        LFD_TRY(run_backward(ctx, st));
+        LFD_CK(mark(5));
+        LFD_CK(mark(6));
+        LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
+                             ctx->mip, ctx->flux_part, st));
+    }
+    LFD_CK(mark(7));
+    LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
+                         ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, ctx->flux_part,
+                         ctx->nflux, ctx->hist, ctx->hist + ctx->mf, st, nf, 1));
+    LFD_CK(mark(8));
+    return LFD_OK;
+}
+
+// (re)captures the two iteration graphs for nf frames
+lfd_status ensure_graphs(lfd_ctx* ctx, int nf) {
+    if (ctx->graph[0] && ctx->graph_nf == nf) return LFD_OK;
+    for (auto& ge : ctx->graph)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
+    for (int cur = 0; cur < 2; ++cur) {
+        const uint64_t before = g_launches.load();
+        LFD_CK(cudaStreamBeginCapture(ctx->wstream, cudaStreamCaptureModeRelaxed));
+        lfd_status s = iter_body(ctx, nf, cur, ctx->wstream, nullptr);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->wstream, &graph);
+        g_launches.store(before);  // capture enqueues nothing; replays are counted
+        if (s != LFD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        LFD_CK(ec);
+        ctx->graph_launches = 0;
+        size_t nnodes = 0;
+        LFD_CK(cudaGraphGetNodes(graph, nullptr, &nnodes));
+        ctx->graph_launches = nnodes;
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph[cur], graph, 0);
+        cudaGraphDestroy(graph);
+        LFD_CK(ei);
+    }
+    ctx->graph_nf = nf;
+    return LFD_OK;
+}
+
+lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int stop_at_predicted,
+                  int* iters_done, int* predicted, double* entropy_hist, double* flux_hist,
+                  cudaStream_t ust) {
     if (!y || !v || n < 1) {
         ctx->err = "invalid argument (NULL pointer or n < 1)";
         return LFD_EINVAL;
     }
-    const Geo& g = ctx->g;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W;
-    if (n > ctx->hist_cap) {
-        cudaFree(ctx->hist);
-        ctx->hist = nullptr;
-        ctx->hist_cap = n;
-        LFD_TRY(dalloc(ctx, &ctx->hist, 2LL * n, true));
+    if (nf < 1 || nf > ctx->mf) {
+        ctx->err = "nframes must lie in 1 .. max_frames (" + std::to_string(ctx->mf) + ")";
+        return LFD_EINVAL;
     }
+    const Geo& g = ctx->g;
+    const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W, L2 = (int64_t)g.Ly * g.Lx;
+    const bool prof = ctx->prof.on;
+    const bool graphs = ctx->opt.use_graph && !prof;
+    // all work runs on the context's stream, ordered after the caller's
+    cudaStream_t st = ctx->wstream;
+    LFD_CK(cudaEventRecord(ctx->ev_in, ust));
+    LFD_CK(cudaStreamWaitEvent(st, ctx->ev_in, 0));
+    if ((int64_t)n * nf > (int64_t)ctx->host_hist_n * ctx->mf || !ctx->host_hist) {
+        if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+        ctx->host_hist = nullptr;
+        LFD_CK(cudaMallocHost((void**)&ctx->host_hist, 2 * sizeof(double) * (size_t)n * ctx->mf));
+        ctx->host_hist_n = n;
+    }
+    double* hE = ctx->host_hist;            // [nf][n]
+    double* hF = ctx->host_hist + (size_t)nf * n;
     const bool ydev = is_device_ptr(y), vdev = is_device_ptr(v);
     const float* yd = y;
     float* vd = v;
     if (!ydev) {
         LFD_TRY(ensure_stage(ctx, false));
-        LFD_CK(cudaMemcpyAsync(ctx->stage_img, y, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_img, y, nf * nimg * sizeof(float), cudaMemcpyHostToDevice, st));
         yd = ctx->stage_img;
     }
     if (!vdev) {
         LFD_TRY(ensure_stage(ctx, true));
-        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nvol * sizeof(float), cudaMemcpyHostToDevice, st));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, nf * nvol * sizeof(float), cudaMemcpyHostToDevice, st));
         vd = ctx->stage_vol;
     }
     const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
-    const FftBuffers fb = fbufs(ctx);
     int cur = 0;
-    if (fp) {
-        LFD_CK(launch_poly_image_cm(yd, g, ctx->ycm, st));
-        LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[cur], st));
-    } else {
-        LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
-        LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
+    for (int f = 0; f < nf; ++f) {
+        if (fp) {
+            LFD_CK(launch_poly_image_cm(yd + f * nimg, g, ctx->ycm + f * g.S * L2, st));
+            LFD_CK(launch_poly_volume_cm(vd + f * nvol, g, ctx->Vcm[cur] + f * g.C * L2, st));
+        } else {
+            LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
+            LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
+        }
     }
-
-    const bool prof = ctx->prof.on;
     constexpr int kEv = 9;  // events per iteration (see lfd_stage_times)
     if (prof && ctx->prof.ev.size() < kEv * (size_t)n) {
         const size_t old = ctx->prof.ev.size();
@@ -685,70 +796,54 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         for (size_t i = old; i < ctx->prof.ev.size(); ++i) LFD_CK(cudaEventCreate(&ctx->prof.ev[i]));
     }
     cudaEvent_t* ev = prof ? ctx->prof.ev.data() : nullptr;
-    std::vector<double> E;
-    int ran = 0;
-    bool stopped = false;
-    const int fpart = fp ? 1 : fwd_parts(ctx), bp = fp ? 1 : bwd_parts(ctx);
-    __nv_bfloat16* rhi = uses_tc(ctx) ? ctx->Rpb[0] : nullptr;
-    __nv_bfloat16* rlo = uses_lo(ctx) ? ctx->Rpb[1] : nullptr;
-    __nv_bfloat16* vhi = uses_tc(ctx) ? ctx->Vpb[0] : nullptr;
-    __nv_bfloat16* vlo = uses_lo(ctx) ? ctx->Vpb[1] : nullptr;
+    if (graphs) LFD_TRY(ensure_graphs(ctx, nf));
+
+    // per frame: still iterating, iterations whose result is final, iterations run
+    std::vector<char> active(nf, 1);
+    std::vector<int> done(nf, 0), ran_f(nf, 0);
+    int ran = 0, n_active = nf;
+    auto deposit = [&](int f, int buf) -> cudaError_t {  // frame f's result from buffer buf
+        if (fp) return launch_depoly_volume_cm(ctx->Vcm[buf] + f * g.C * L2, g, vd + f * nvol, st);
+        return launch_depoly_volume(ctx->Vp32[buf], g.m_base, g, vd, st);
+    };
     for (int k = 0; k < n; ++k) {
-        const int nxt = cur ^ 1;
-        cudaEvent_t* e9 = prof ? ev + kEv * k : nullptr;
-        auto mark = [&](int i) -> cudaError_t { return prof ? cudaEventRecord(e9[i], st) : cudaSuccess; };
-        LFD_CK(mark(0));
-        if (fp) {
-            // forward with the ratio fused into its last transform
-            LFD_CK(fft_forward(*fp, g, fb, ctx->Vcm[cur], nullptr, ctx->Rcm, ctx->ycm, ctx->rimg,
-                               ctx->opt.eps, st, prof ? e9 + 1 : nullptr));
-            LFD_CK(mark(3));
-            LFD_CK(fft_backward(*fp, g, fb, ctx->Rcm, ctx->Xcm, nullptr, st, prof ? e9 + 4 : nullptr));
-            LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
-            LFD_CK(mark(6));
-            LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, ctx->mip,
-                                    ctx->flux_part, st));
+        if (graphs) {
+            LFD_CK(cudaGraphLaunch(ctx->graph[cur], st));
+            count_launch(ctx->graph_launches);
         } else {
-            LFD_CK(mark(1));
-            LFD_TRY(run_forward(ctx, cur, st));
-            LFD_CK(mark(2));
-            LFD_CK(launch_fwd_finish_ratio(ctx->Fwd, fpart, ctx->ypoly, ctx->opt.eps, g, ctx->Rp32, rhi,
-                                           rlo, st));
-            LFD_CK(mark(3));
-            LFD_CK(mark(4));
-            LFD_TRY(run_backward(ctx, st));
-            LFD_CK(mark(5));
-            LFD_CK(mark(6));
-            LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
-                                 ctx->mip, ctx->flux_part, st));
+            LFD_TRY(iter_body(ctx, nf, cur, st, prof ? ev + kEv * k : nullptr));
         }
-        LFD_CK(mark(7));
-        LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
-                             ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, ctx->flux_part,
-                             ctx->nflux, ctx->hist + k, ctx->hist + ctx->hist_cap + k, st));
-        LFD_CK(mark(8));
+        // this iteration's entropy and flux of every frame into the histories
+        LFD_CK(cudaMemcpy2DAsync(hE + k, n * sizeof(double), ctx->hist, sizeof(double), sizeof(double),
+                                 nf, cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaMemcpy2DAsync(hF + k, n * sizeof(double), ctx->hist + ctx->mf, sizeof(double),
+                                 sizeof(double), nf, cudaMemcpyDeviceToHost, st));
         ran = k + 1;
+        for (int f = 0; f < nf; ++f)
+            if (active[f]) ran_f[f] = ran;
         if (stop_at_predicted) {
-            LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist + k, sizeof(double),
-                                   cudaMemcpyDeviceToHost, st));
             LFD_CK(cudaStreamSynchronize(st));
-            E.push_back(ctx->host_pinned[0]);
-            if (k >= 1 && E[k] < E[k - 1]) {  // E_{k+1} < E_k: keep v^k, still in Vp32[cur]
-                stopped = true;
-                break;
+            for (int f = 0; f < nf; ++f) {
+                // E_{k+1} < E_k: frame f keeps v^k, still in buffer cur
+                if (active[f] && k >= 1 && hE[(size_t)f * n + k] < hE[(size_t)f * n + k - 1]) {
+                    LFD_CK(deposit(f, cur));
+                    active[f] = 0;
+                    done[f] = k;
+                    --n_active;
+                }
             }
+            if (n_active == 0) break;
         }
-        cur = nxt;
+        cur ^= 1;
     }
-    const int result = cur;
-    const int done = stopped ? ran - 1 : ran;
-    if (fp) LFD_CK(launch_depoly_volume_cm(ctx->Vcm[result], g, vd, st));
-    else LFD_CK(launch_depoly_volume(ctx->Vp32[result], g.m_base, g, vd, st));
-    if (!vdev) LFD_CK(cudaMemcpyAsync(v, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
-    std::vector<double> hbuf(2 * (size_t)ran);
-    LFD_CK(cudaMemcpyAsync(hbuf.data(), ctx->hist, ran * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LFD_CK(cudaMemcpyAsync(hbuf.data() + ran, ctx->hist + ctx->hist_cap, ran * sizeof(double),
-                           cudaMemcpyDeviceToHost, st));
+    for (int f = 0; f < nf; ++f)
+        if (active[f]) {
+            LFD_CK(deposit(f, cur));
+            done[f] = ran;
+        }
+    if (!vdev) LFD_CK(cudaMemcpyAsync(v, vd, nf * nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
+    LFD_CK(cudaEventRecord(ctx->ev_out, st));
+    LFD_CK(cudaStreamWaitEvent(ust, ctx->ev_out, 0));
     LFD_CK(cudaStreamSynchronize(st));
     if (ctx->cg) {
         const int te = cgemm_error(ctx->cg);
@@ -783,13 +878,37 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int sto
         }
         ctx->prof.count += ran;
     }
-    if (entropy_hist)
-        for (int k = 0; k < n; ++k) entropy_hist[k] = k < ran ? hbuf[k] : NAN;
-    if (flux_hist)
-        for (int k = 0; k < n; ++k) flux_hist[k] = k < ran ? hbuf[ran + k] : NAN;
-    if (iters_done) *iters_done = done;
-    if (predicted) *predicted = lfd_predict_stop(hbuf.data(), ran);
+    for (int f = 0; f < nf; ++f) {
+        const double* Ef = hE + (size_t)f * n;
+        const double* Ff = hF + (size_t)f * n;
+        if (entropy_hist)
+            for (int k = 0; k < n; ++k) entropy_hist[(size_t)f * n + k] = k < ran_f[f] ? Ef[k] : NAN;
+        if (flux_hist)
+            for (int k = 0; k < n; ++k) flux_hist[(size_t)f * n + k] = k < ran_f[f] ? Ff[k] : NAN;
+        if (iters_done) iters_done[f] = done[f];
+        if (predicted) predicted[f] = lfd_predict_stop(Ef, ran_f[f]);
+    }
     return LFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n, int stop_at_predicted,
+                          int* iters_done, int* predicted, double* entropy_hist, double* flux_hist,
+                          void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    return rl_run(ctx, 1, y, v, n, stop_at_predicted, iters_done, predicted, entropy_hist, flux_hist,
+                  (cudaStream_t)cuda_stream);
+}
+
+lfd_status lfd_rl_iterate_batch(lfd_ctx* ctx, int nframes, const float* y, float* v, int n,
+                                int stop_at_predicted, int* iters_done, int* predicted,
+                                double* entropy_hist, double* flux_hist, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    return rl_run(ctx, nframes, y, v, n, stop_at_predicted, iters_done, predicted, entropy_hist,
+                  flux_hist, (cudaStream_t)cuda_stream);
 }
 
 lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda_stream) {
@@ -814,6 +933,61 @@ lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda
     LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist, sizeof(double), cudaMemcpyDeviceToHost, st));
     LFD_CK(cudaStreamSynchronize(st));
     *entropy = ctx->host_pinned[0];
+    return LFD_OK;
+}
+
+lfd_status lfd_autotune(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                        const lfd_options* opt, void* cuda_stream, int* best_size,
+                        float* ms_per_iter) {
+    if (!psf || !opt || !best_size || opt->variant != LFD_FFT) return LFD_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nf = opt->max_frames;
+    const int64_t nimg = (int64_t)nf * H * W, nvol = (int64_t)nf * Nz * H * W;
+    float best = 0.f;
+    int bestF = 0;
+    lfd_status last = LFD_EUNSUPPORTED;
+    for (int F : {32, 64}) {
+        lfd_options o = *opt;
+        o.fft_size = F;
+        o.use_graph = 1;
+        lfd_ctx* ctx = nullptr;
+        lfd_status s = lfd_create(psf, P, Nnum, Nz, H, W, &o, cuda_stream, &ctx);
+        if (s != LFD_OK) {
+            if (s != LFD_EUNSUPPORTED) last = s;
+            continue;
+        }
+        float* y = nullptr;
+        float* v = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        float ms = -1.f;
+        bool ok = cudaMalloc(&y, nimg * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&v, nvol * sizeof(float)) == cudaSuccess &&
+                  cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+        ok = ok && launch_fill(y, nimg, 10.f, st) == cudaSuccess && launch_fill(v, nvol, 1.f, st) == cudaSuccess;
+        ok = ok && lfd_rl_iterate_batch(ctx, nf, y, v, 1, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK;
+        ok = ok && cudaEventRecord(a, st) == cudaSuccess &&
+             lfd_rl_iterate_batch(ctx, nf, y, v, 2, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK &&
+             cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (y) cudaFree(y);
+        if (v) cudaFree(v);
+        lfd_destroy(ctx);
+        if (!ok) {
+            cudaGetLastError();
+            last = LFD_ECUDA;
+            continue;
+        }
+        ms *= 0.5f;
+        if (bestF == 0 || ms < best) {
+            best = ms;
+            bestF = F;
+        }
+    }
+    if (bestF == 0) return last;
+    *best_size = bestF;
+    if (ms_per_iter) *ms_per_iter = best;
     return LFD_OK;
 }
 

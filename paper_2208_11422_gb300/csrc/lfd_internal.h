@@ -95,9 +95,17 @@ struct lfd_ctx {
     double* rowE2 = nullptr;     // [H] sum of mip^2 per row
     double* coef = nullptr;      // [YS][XS]
     double* flux_part = nullptr; // [Ly*Lx]
-    double* hist = nullptr;      // [2][hist_cap]: entropy, flux
-    int hist_cap = 0;
+    double* hist = nullptr;      // [2][mf]: entropy, flux of the latest iteration
     double* host_pinned = nullptr;  // [4]
+    double* host_hist = nullptr;    // pinned [2][mf][host_hist_n] histories
+    int host_hist_n = 0;
+    int mf = 1;                  // frames per batch (max_frames)
+    // CUDA graphs of one RL iteration (reading iterate buffer 0 or 1)
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_nf = 0;
+    uint64_t graph_launches = 0;  // kernels per graph replay
     // staging for host pointers
     float* stage_vol = nullptr;  // [Nz][H][W]
     float* stage_img = nullptr;  // [H][W]
@@ -156,11 +164,14 @@ cudaError_t launch_update(const float* vin, float* vout, __nv_bfloat16* hi, __nv
                           const float* parts, int nsplit, const float* inv, const Geo& g,
                           float* mip, double* flux_part, cudaStream_t st);
 cudaError_t launch_mip(const float* vp32, const Geo& g, float* mip, cudaStream_t st);
+// DCT entropy of nf frames' MIPs (frame-major arrays: mip H*W, G H*XS, rowE2 H,
+// coef XS*YS, flux_part nflux per frame); frame f writes out_entropy[f*out_stride]
+// and out_flux[f*out_stride]
 cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH,
                           int H, int W, int XS, int YS, int l2_over_region,
                           double* G, double* rowE2, double* coef,
                           const double* flux_part, int nflux, double* out_entropy,
-                          double* out_flux, cudaStream_t st);
+                          double* out_flux, cudaStream_t st, int nf = 1, int out_stride = 1);
 
 // FP32 SIMT implicit-GEMM projections (CUDA cores)
 int simt_fwd_splits(const Geo& g, int sm_count);

@@ -10,7 +10,9 @@
 //   adjoint  re += Wr Yr + Wi Yi,   im += Wr Yi - Wi Yr
 // each of them in three passes hi*hi + hi*lo + lo*hi (negation through the
 // instruction descriptor). One block owns 128 output rows (phases s for the
-// forward, channels c for the adjoint) by the 16 tiles of one bin; its K loop
+// forward, channels c for the adjoint) by 16 columns (frame x tile) of one bin;
+// units are ordered bin-major so the blocks working on one bin share its
+// spectra in L2. Its K loop
 // streams 64-wide blocks of all eight planes through a 3-stage TMA ring. The
 // accumulators (real and imaginary, 16 columns each) alternate between two
 // TMEM buffers so the drain of one chunk overlaps the next; chains are cut
@@ -42,7 +44,9 @@ constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 MMA steps
 
 struct CgArgs {
-    int nbins, ntile;
+    int nbins;
+    int ncol;          // output columns (frames x tiles) of this launch
+    int ncg;           // column groups of 16
     int mtiles;        // row tiles of 128 per bin
     int nkb;           // k-blocks of 64 per unit
     int nrows;         // valid rows (S or C)
@@ -72,7 +76,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_units = a.nbins * a.mtiles;
+    const int n_units = a.nbins * a.ncg * a.mtiles;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -108,7 +112,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
             uint32_t phase = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int bin = u / a.mtiles, mt = u % a.mtiles;
+                const int bin = u / (a.ncg * a.mtiles), rem = u % (a.ncg * a.mtiles);
+                const int cg = rem / a.mtiles, mt = rem % a.mtiles;
                 for (int kb = 0; kb < a.nkb && ok; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
                         ok = false;
@@ -124,7 +129,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         } else {
                             tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
-                        tma_3d(sB + i * kPlaneB, B[i], kb * 64, 0, bin, &full[stage]);
+                        tma_3d(sB + i * kPlaneB, B[i], kb * 64, cg * 16, bin, &full[stage]);
                     }
                     ++issued;
                     if (++stage == kStages) {
@@ -213,7 +218,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
         int ci = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const int bin = u / a.mtiles, mt = u % a.mtiles;
+            const int bin = u / (a.ncg * a.mtiles), rem = u % (a.ncg * a.mtiles);
+            const int cg = rem / a.mtiles, mt = rem % a.mtiles;
             const int grow = mt * 128 + row;
             for (int c0 = 0; c0 < a.nkb; c0 += kChunkKb, ++ci) {
                 const int buf = ci & 1;
@@ -228,10 +234,10 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                 tmem_ld16(tb + 16, im);
                 tmem_wait_ld();
                 if (grow < a.nrows) {
-                    float2* o = a.out + (int64_t)bin * a.ntile * a.ld + grow;
+                    float2* o = a.out + ((int64_t)bin * a.ncol + cg * 16) * a.ld + grow;
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
-                        if (t < a.ntile) {
+                        if (cg * 16 + t < a.ncol) {
                             float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.ld);
                             const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
                             if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
@@ -281,7 +287,7 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
 struct CgState {
     CUtensorMap fa[4], fb[4], aa[4], ab[4];
     CgArgs fwd, adj;
-    int fwd_grid = 0, adj_grid = 0;
+    int sm_count = 0, ncolp = 16;
     int* err = nullptr;
 };
 
@@ -298,8 +304,8 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     for (int i = 0; i < 4; ++i) {
         bool ok = map3(&s->fa[i], b.W[i], b.Cw, b.S, b.bins, 64, 128) &&
                   map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64) &&
-                  map3(&s->fb[i], b.X[i], b.Cw, 16, b.bins, 64, 16) &&
-                  map3(&s->ab[i], b.Y[i], b.Sw, 16, b.bins, 64, 16);
+                  map3(&s->fb[i], b.X[i], b.Cw, b.ncolp, b.bins, 64, 16) &&
+                  map3(&s->ab[i], b.Y[i], b.Sw, b.ncolp, b.bins, 64, 16);
         if (!ok) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the spectra planes";
             return cudaErrorInvalidValue;
@@ -307,7 +313,8 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     }
     CgArgs& f = s->fwd;
     f.nbins = b.bins;
-    f.ntile = b.ntile;
+    f.ncol = 16;
+    f.ncg = 1;
     f.mtiles = (b.S + 127) / 128;
     f.nkb = (b.Cw + 63) / 64;
     f.nrows = b.S;
@@ -321,27 +328,35 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.nrows = b.C;
     g.ld = b.Cf;
     g.out = b.Xout;
-    s->fwd_grid = std::min(f.nbins * f.mtiles, sm_count);
-    s->adj_grid = std::min(g.nbins * g.mtiles, sm_count);
+    s->sm_count = sm_count;
+    s->ncolp = b.ncolp;
     e = cudaFuncSetAttribute(k_tc_cgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_tc_cgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
-cudaError_t cgemm_forward(void* state, cudaStream_t st) {
+cudaError_t cgemm_forward(void* state, int ncol, cudaStream_t st) {
     CgState* s = static_cast<CgState*>(state);
-    k_tc_cgemm<false><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fa[2], s->fa[3],
-                                                                 s->fb[0], s->fb[1], s->fb[2], s->fb[3],
-                                                                 s->fwd);
+    if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
+    CgArgs a = s->fwd;
+    a.ncol = ncol;
+    a.ncg = (ncol + 15) / 16;
+    const int grid = std::min(a.nbins * a.ncg * a.mtiles, s->sm_count);
+    k_tc_cgemm<false><<<grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fa[2], s->fa[3],
+                                                          s->fb[0], s->fb[1], s->fb[2], s->fb[3], a);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t cgemm_adjoint(void* state, cudaStream_t st) {
+cudaError_t cgemm_adjoint(void* state, int ncol, cudaStream_t st) {
     CgState* s = static_cast<CgState*>(state);
-    k_tc_cgemm<true><<<s->adj_grid, kThreads, kSmemBytes, st>>>(s->aa[0], s->aa[1], s->aa[2], s->aa[3],
-                                                                s->ab[0], s->ab[1], s->ab[2], s->ab[3],
-                                                                s->adj);
+    if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
+    CgArgs a = s->adj;
+    a.ncol = ncol;
+    a.ncg = (ncol + 15) / 16;
+    const int grid = std::min(a.nbins * a.ncg * a.mtiles, s->sm_count);
+    k_tc_cgemm<true><<<grid, kThreads, kSmemBytes, st>>>(s->aa[0], s->aa[1], s->aa[2], s->aa[3],
+                                                         s->ab[0], s->ab[1], s->ab[2], s->ab[3], a);
     count_launch();
     return cudaGetLastError();
 }

@@ -42,6 +42,9 @@ class lfd_options(ctypes.Structure):
         ("YS", ctypes.c_int),
         ("l2_over_region", ctypes.c_int),
         ("variant", ctypes.c_int),
+        ("max_frames", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("fft_size", ctypes.c_int),
     ]
 
 
@@ -59,7 +62,11 @@ _SIGS = {
     "lfd_backward": (_I, [_VP, _VP, _VP, _VP]),
     "lfd_rl_iterate": (_I, [_VP, _VP, _VP, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
+    "lfd_rl_iterate_batch": (_I, [_VP, _I, _VP, _VP, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
     "lfd_quality": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
+    "lfd_autotune": (_I, [_VP, _I, _I, _I, _I, _I, ctypes.POINTER(lfd_options), _VP,
+                          ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "lfd_quality_mip_static": (_I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
     "lfd_destroy": (None, [_VP]),
     "lfd_last_error": (ctypes.c_char_p, [_VP]),
@@ -174,6 +181,22 @@ def lfd_rl_iterate(ctx, y, v, n: int, stop_at_predicted: bool = False, stream=No
     return done.value, pred.value, list(ent), list(flux)
 
 
+def lfd_rl_iterate_batch(ctx, nframes: int, y, v, n: int, stop_at_predicted: bool = False,
+                         stream=None):
+    """Returns (iters_done[F], predicted[F], entropy[F][n], flux[F][n])."""
+    done = (_I * nframes)()
+    pred = (_I * nframes)()
+    ent = (_D * (nframes * n))()
+    flux = (_D * (nframes * n))()
+    _check(load().lfd_rl_iterate_batch(ctx, nframes, _ptr(y), _ptr(v), n,
+                                       int(bool(stop_at_predicted)), done, pred, ent, flux,
+                                       _stream(stream)), ctx)
+    e = list(ent)
+    f = list(flux)
+    return (list(done), list(pred), [e[i * n:(i + 1) * n] for i in range(nframes)],
+            [f[i * n:(i + 1) * n] for i in range(nframes)])
+
+
 def lfd_quality(ctx, v, stream=None) -> float:
     e = _D(0)
     _check(load().lfd_quality(ctx, _ptr(v), ctypes.byref(e), _stream(stream)), ctx)
@@ -189,6 +212,17 @@ def lfd_quality_mip_static(mip, H: int, W: int, XS: int, YS: int, l2_over_region
                                        _stream(stream))
     if st != LFD_OK:
         raise LfdError(st, "lfd_quality_mip_static: %s" % lfd_status_string(st))
+
+
+def lfd_autotune(psf, P: int, Nnum: int, Nz: int, H: int, W: int, opt: lfd_options, stream=None):
+    """Returns (best FFT size, measured ms per batched iteration)."""
+    best = _I(0)
+    ms = ctypes.c_float(0)
+    st = load().lfd_autotune(_ptr(psf), P, Nnum, Nz, H, W, ctypes.byref(opt), _stream(stream),
+                             ctypes.byref(best), ctypes.byref(ms))
+    if st != LFD_OK:
+        raise LfdError(st, "lfd_autotune failed: %s" % lfd_status_string(st))
+    return best.value, ms.value
 
 
 def lfd_destroy(ctx):

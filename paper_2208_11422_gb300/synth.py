@@ -195,6 +195,34 @@ def ground_truth(cfg: int | Geometry, seed: int | None = None) -> np.ndarray:
     return v
 
 
+def timelapse_beads(cfg: int | Geometry, frames: int, seed: int, step_sigma: float = 0.5,
+                    seed_offset: int = 0):
+    """Bead volumes of a time-lapse: frame 0 has the configuration's beads, and
+    every later frame moves each bead centre by an N(0, step_sigma^2) step per
+    axis (cumulative). Returns a list of float64 volumes [Nz][H][W]."""
+    g = CONFIGS[cfg] if isinstance(cfg, int) else cfg
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(0, g.W, g.beads)
+    cy = rng.uniform(0, g.H, g.beads)
+    cz = rng.uniform(0, g.nz, g.beads)
+    amp = rng.uniform(g.amp_lo, 1.0, g.beads)
+    vols = []
+    for _f in range(frames):
+        v = np.zeros((g.nz, g.H, g.W), np.float64)
+        for q in range(g.beads):
+            _gauss_blob(v, cz[q], cy[q], cx[q], amp[q], g.bead_radius)
+        vols.append(v)
+        cx = cx + rng.normal(0, step_sigma, g.beads)
+        cy = cy + rng.normal(0, step_sigma, g.beads)
+        cz = cz + rng.normal(0, step_sigma, g.beads)
+    return vols
+
+
+def timelapse_scales(frames: int, seed: int, lo: float = 100.0, hi: float = 2000.0) -> np.ndarray:
+    """Photon scale of every frame, uniform in [lo, hi]."""
+    return np.random.default_rng(seed).uniform(lo, hi, frames)
+
+
 def poisson_data(expected, scale: float, background: float, seed: int) -> np.ndarray:
     """y = float32(Poisson(scale * expected) + background)."""
     rng = np.random.default_rng(seed)

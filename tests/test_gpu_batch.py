@@ -1,0 +1,117 @@
+"""Batched RL (lfd_rl_iterate_batch): frames that share one PSF advance
+together through one launch per stage (FFT variant), and every frame gets the
+same result as when it is reconstructed alone, including its own stopping
+iteration. Frame 0 is also checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import metric
+from oracle import rl as orl
+from paper_2208_11422_gb300 import synth
+
+from gpu_util import lib, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_RL = {"fp32": 1e-4, "bf16x3": 5e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib()
+
+
+def make_frames(nf):
+    g = synth.CONFIGS[0]
+    psf = synth.make_psf(0)
+    vols = synth.timelapse_beads(0, nf, 300, step_sigma=1.0)
+    scales = synth.timelapse_scales(nf, 301, 100.0, 2000.0)
+    ys = [synth.poisson_data(oracle.forward(psf, g.nnum, vols[f]), scales[f], g.background, 310 + f)
+          for f in range(nf)]
+    return g, psf, np.stack(ys).astype(np.float32)
+
+
+def ctx_for(psf, g, prec, nf, use_graph=1):
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    return lfd.lfd_create(torch.from_numpy(psf).to("cuda:0"), g.P, g.nnum, g.nz, g.H, g.W,
+                          lfd.lfd_default_options(precision=prec, variant="fft", max_frames=nf,
+                                                  use_graph=use_graph))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("stop", [False, True])
+def test_batch_equals_single_frames(prec, stop):
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    nf, n = 5, 8
+    g, psf, ys = make_frames(nf)
+    dev = torch.device("cuda:0")
+    ctx = ctx_for(psf, g, prec, nf)
+    try:
+        v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+        done, pred, ent, flux = lfd.lfd_rl_iterate_batch(ctx, nf, torch.from_numpy(ys).to(dev), v, n, stop)
+        vb = v.cpu().numpy()
+        for f in range(nf):
+            v1 = torch.ones((g.nz, g.H, g.W), device=dev)
+            d1, p1, e1, f1 = lfd.lfd_rl_iterate(ctx, torch.from_numpy(ys[f]).to(dev), v1, n, stop)
+            assert (done[f], pred[f]) == (d1, p1), f
+            assert rel_l2(vb[f], v1.cpu().numpy()) <= 1e-6, f
+            np.testing.assert_allclose(np.nan_to_num(ent[f], nan=-1), np.nan_to_num(e1, nan=-1), rtol=1e-9)
+    finally:
+        lfd.lfd_destroy(ctx)
+    if stop:
+        assert len(set(done)) >= 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_batch_frame0_matches_oracle(prec):
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    nf, n = 3, 5
+    g, psf, ys = make_frames(nf)
+    XS, YS = metric.region_size(g.nnum, g.H, g.W)
+    ref = orl.rl(psf, g.nnum, ys[0], n, XS, YS)
+    ctx = ctx_for(psf, g, prec, nf)
+    try:
+        v = torch.ones((nf, g.nz, g.H, g.W), device="cuda:0")
+        done, pred, ent, _ = lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, n)   # host y
+        assert rel_l2(v[0].cpu().numpy(), ref.v) <= TOL_RL[prec]
+        assert pred[0] == ref.predicted
+    finally:
+        lfd.lfd_destroy(ctx)
+
+
+def test_graph_and_plain_launches_agree():
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    nf, n = 4, 6
+    g, psf, ys = make_frames(nf)
+    out = []
+    for use_graph in (1, 0):
+        ctx = ctx_for(psf, g, "fp32", nf, use_graph)
+        try:
+            v = torch.ones((nf, g.nz, g.H, g.W), device="cuda:0")
+            lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, n)
+            out.append(v.cpu().numpy())
+        finally:
+            lfd.lfd_destroy(ctx)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_batch_rejects_too_many_frames():
+    from paper_2208_11422_gb300 import lfd
+    g, psf, ys = make_frames(2)
+    ctx = ctx_for(psf, g, "fp32", 2)
+    try:
+        v = np.ones((3, g.nz, g.H, g.W), np.float32)
+        y3 = np.concatenate([ys, ys[:1]])
+        with pytest.raises(lfd.LfdError):
+            lfd.lfd_rl_iterate_batch(ctx, 3, y3, v, 2)
+    finally:
+        lfd.lfd_destroy(ctx)
+    with pytest.raises(lfd.LfdError):   # direct variant has no batch path
+        import torch
+        lfd.lfd_create(torch.from_numpy(psf).to("cuda:0"), g.P, g.nnum, g.nz, g.H, g.W,
+                       lfd.lfd_default_options(max_frames=2))
