@@ -221,30 +221,80 @@ PATH_NAMES = {("fft", "fp32"): "fft_fp32", ("fft", "bf16x3"): "fft_bf16x3",
               ("direct", "fp32"): "direct_fp32"}
 
 
-def fft_plan_numbers(g):
-    """The FFT tiling the library picks (same rule as fft_plan_for)."""
-    N, k = g.nnum, g.psf_lenslets
-    h = (k + 1) // 2
+def fft_plan_numbers(g, plan):
+    """(F, bins, tiles, Cf, S, C) of the FFT tiling the library chose (lfd_get_fft_plan)."""
+    N = g.nnum
     S, C = N * N, g.nz * N * N
-    L = g.lenslets
-    best = None
-    for F in (32, 64):
-        B = F - 2 * h
-        if B < 4:
+    return plan["F"], plan["bins"], plan["tiles"], (C + 3) // 4 * 4, S, C
+
+
+# DRAM bytes (read + write) per launch from one ncu capture, by (workload,
+# precision, kernel); each entry names its summary under profiles/ and is
+# removed when that kernel changes.
+NCU_TRAFFIC = {
+    ("lf_large_2025px_51z_psf345", "bf16x3", "forward contraction"):
+        (4.090e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+    ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
+        (3.740e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+    ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
+        (0.4788e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+}
+
+
+def fft_kernel_work(g, plan, prec):
+    """Algorithmic bytes (and contraction flops) per launch of the FFT
+    variant's four large kernels. Spectra are 8 bytes per complex value (BF16
+    hi/lo planes of real and imaginary part, or complex64)."""
+    F, bins, nt, _, S, C = fft_plan_numbers(g, plan)
+    L2 = (g.H // g.nnum) * (g.W // g.nnum)
+    vol = 4.0 * C * L2
+    xs, ys, ws = 8.0 * bins * nt * C, 8.0 * bins * nt * S, 8.0 * bins * S * C
+    flops = 8.0 * bins * S * nt * C * (3 if prec == "bf16x3" else 1)
+    return {"volume_r2c": {"bytes": vol + xs, "slot": 8, "kernel": "forward volume transform"},
+            "forward_contraction": {"bytes": ws + xs + ys, "flops": flops, "slot": 5,
+                                    "kernel": "forward contraction"},
+            "backward_contraction": {"bytes": ws + ys + xs, "flops": flops, "slot": 6,
+                                     "kernel": "backward contraction"},
+            "volume_c2r": {"bytes": xs + vol, "slot": 9, "kernel": "backward volume transform"}}, \
+        {"F": F, "bins": bins, "tiles": nt}
+
+
+def fft_roofline(g, plan, prec, stage, peaks, peak_src, fp32_peak, smax):
+    """Roofline of the slowest of the FFT variant's kernels (by the stage
+    times measured with CUDA events), and every kernel's fractions beside it."""
+    work, shape = fft_kernel_work(g, plan, prec)
+    kern = {}
+    for name, w in work.items():
+        ms = stage[w["slot"]]
+        if ms <= 0:
             continue
-        nt = math.ceil(L / B) ** 2
-        if nt > 16 or S > 256:
-            continue
-        bins = F * (F // 2 + 1)
-        Cf = (C + 3) // 4 * 4
-        spectra = bins * S * Cf * 8.0
-        if spectra > 96e9:
-            continue
-        flops = bins * S * nt * C * 8.0
-        t = max(spectra / 6.0e12, flops / 6.0e13)
-        if best is None or t < best[0]:
-            best = (t, F, bins, nt, Cf, S, C)
-    return best
+        gbs = w["bytes"] / (ms / 1e3) / 1e9
+        e = {"ms": ms, "algorithmic_bytes": w["bytes"], "GBps": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+        if "flops" in w:
+            tf = w["flops"] / (ms / 1e3) / 1e12
+            e["TFLOPs"] = tf
+            if prec == "fp32":
+                e["alu_frac"] = tf / fp32_peak
+        kern[name] = e
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    if prec == "fp32" and "alu_frac" in d and d["alu_frac"] > d["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": d["TFLOPs"], "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": d["alu_frac"],
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %g MHz" % smax}
+    else:
+        roof = {"bound": "hbm", "achieved": d["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": d["hbm_frac"], "peak_source": "hbm_gbs (%s, of measured)" % peak_src
+                if peak_src == "measured" else "hbm_gbs (fallback)"}
+    roof["kernel"] = work[dom]["kernel"]
+    roof["algorithmic_per_launch"] = dict(shape, bytes=work[dom]["bytes"],
+                                          **({"flops": work[dom]["flops"]} if "flops" in work[dom] else {}))
+    t = NCU_TRAFFIC.get((g.name, prec, work[dom]["kernel"]))
+    roof["traffic"] = t[0] if t else None
+    if t:
+        roof["traffic_source"] = t[1]
+    roof["kernels"] = kern
+    return roof
 
 
 def time_path(lfd, torch, dev, psf_d, g, y_d, variant, precision, iters, warm, stream):
@@ -286,6 +336,7 @@ def run_lfd(args, rank, world, local):
 
     ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W,
                          lfd.lfd_default_options(precision=prec, variant=variant))
+    fft_plan = lfd.lfd_get_fft_plan(ctx)
     # data: y = Poisson(scale * H v_true) + background; H v_true by this path's
     # forward projection (an input for timing, never an expected value)
     vt_d = torch.from_numpy(vt.astype(np.float32)).to(dev)
@@ -369,43 +420,11 @@ def run_lfd(args, rank, world, local):
     fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max clock
     fl = algorithmic_flops_per_projection(g)
     stage_names = ["forward", "ratio", "backward", "update", "metric", "forward_contraction",
-                   "backward_contraction", "fft_transforms"]
+                   "backward_contraction", "fft_transforms", "volume_r2c", "volume_c2r",
+                   "exact_low_sensitivity"]
     stage_ms = dict(zip(stage_names, stage))
-    if variant == "fft" and prec == "bf16x3":
-        # split-BF16 tensor-core contraction: streams the spectra planes once
-        plan = fft_plan_numbers(g)
-        _, F, bins, nt, Cf, S, C = plan
-        Cw = (C + 7) // 8 * 8
-        cbytes = 8.0 * bins * S * Cw
-        cflops = 8.0 * bins * S * nt * C
-        dom_ms = max(stage[5], stage[6])
-        dom = "forward contraction" if stage[5] >= stage[6] else "backward contraction"
-        hbm = cbytes / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": hbm, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
-                "peak_source": "hbm_gbs (%s)" % peak_src}
-        roof["algorithmic_per_launch"] = {"spectra_bytes": cbytes, "complex_mac_flops": cflops,
-                                          "F": F, "bins": bins, "tiles": nt}
-    elif variant == "fft":
-        plan = fft_plan_numbers(g)
-        _, F, bins, nt, Cf, S, C = plan
-        cflops = 8.0 * bins * S * nt * C
-        cbytes = 8.0 * bins * S * Cf
-        dom_ms = max(stage[5], stage[6])
-        dom = "forward contraction" if stage[5] >= stage[6] else "backward contraction"
-        alu = cflops / (dom_ms / 1e3) / 1e12
-        hbm = cbytes / (dom_ms / 1e3) / 1e9
-        alu_frac, hbm_frac = alu / fp32_peak, hbm / peaks["hbm_gbs"]
-        if alu_frac >= hbm_frac:
-            roof = {"bound": "alu", "kernel": dom, "achieved": alu, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": alu_frac,
-                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %g MHz" % smax}
-        else:
-            roof = {"bound": "hbm", "kernel": dom, "achieved": hbm, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": hbm_frac, "peak_source": "hbm_gbs (%s)" % peak_src}
-        roof["other"] = {"hbm_GBps": hbm, "hbm_frac": hbm_frac, "alu_TFLOPs": alu, "alu_frac": alu_frac}
-        roof["algorithmic_per_launch"] = {"flops": cflops, "spectra_bytes": cbytes,
-                                          "F": F, "bins": bins, "tiles": nt}
+    if variant == "fft":
+        roof = fft_roofline(g, fft_plan, prec, stage, peaks, peak_src, fp32_peak, smax)
     elif prec == "fp32":
         dom_ms = max(stage[0], stage[2])
         dom = "forward projection" if stage[0] >= stage[2] else "backprojection"
@@ -420,7 +439,7 @@ def run_lfd(args, rank, world, local):
         roof = {"bound": "tensor", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "peak_source": "bf16_tflops_sustained (%s)" % peak_src}
         roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof.setdefault("traffic", None)
     roof["stage_ms"] = stage_ms
 
     cpu = None

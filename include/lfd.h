@@ -237,6 +237,12 @@ int lfd_predict_stop(const double* E, int n);
 lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps,
                             int* precision, int64_t* device_bytes);
 
+/* FFT tiling of an LFD_FFT context: transform size F (lenslets per patch side),
+ * valid lenslets per tile side B = F - 2h, tiles per frame, and frequency bins
+ * F*(F/2+1) per channel. All four are 0 for an LFD_DIRECT context. Any output
+ * pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
+lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int* bins);
+
 /* Number of kernels the library has launched in this process (all contexts). */
 uint64_t lfd_launch_count(void);
 
@@ -245,10 +251,13 @@ uint64_t lfd_launch_count(void);
  * [0] forward projection (FFT variant: ratio included), [1] ratio (direct
  * variant), [2] backprojection, [3] update + MIP + flux, [4] metric,
  * [5] forward contraction kernel alone, [6] backward contraction kernel alone,
- * [7] the FFT variant's transforms (0 for the direct variant).
+ * [7] the FFT variant's transforms (0 for the direct variant), of which
+ * [8] the forward projection's volume transform (R2C) and [9] the
+ * backprojection's volume transform (C2R) alone, [10] the FFT variant's exact
+ * backprojection of low-sensitivity voxels (part of [2]).
  * lfd_set_profiling(ctx, 1) turns the events on and resets the averages;
  * lfd_stage_times writes the mean over every iteration run since then (zeros
- * if none) into ms[0..n-1] (entries past 7 are 0). */
+ * if none) into ms[0..n-1] (entries past 10 are 0). */
 lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n);
 
 #ifdef __cplusplus

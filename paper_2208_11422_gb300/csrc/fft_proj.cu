@@ -66,30 +66,67 @@ __device__ __forceinline__ void warp_fft(float2* a) {
     }
 }
 
-// channel-major images [nch][Ly][Lx]; patch of tile (ty, tx) starts at
-// lenslet (ty*B - h, tx*B - h), zero outside the grid
-// (several frames: column col = frame * ntile + tile, frames fstride floats apart)
+// A source or destination is bound to one column (one tile of one frame)
+// before a block's transforms: bind(col) returns a view whose operator()
+// takes (channel, row, column) within the tile's patch.
+
+// patch view of a channel-major image [nch][Ly][Lx]: patch row r, column x is
+// lenslet (y0 + r, x0 + x), zero outside the grid; base == null reads an
+// all-ones image (used for H^T 1)
+struct ImgView {
+    const float* base;
+    int Ly, Lx, y0, x0;
+    __device__ float operator()(int c, int r, int x) const {
+        const int Iy = y0 + r, Ix = x0 + x;
+        if (Iy < 0 || Iy >= Ly || Ix < 0 || Ix >= Lx) return 0.f;
+        return base ? base[((int64_t)c * Ly + Iy) * Lx + Ix] : 1.f;
+    }
+};
+
+// channel-major images, uniform frames; patch of tile (ty, tx) starts at
+// lenslet (ty*B - h, tx*B - h); column col = frame * ntile + tile, frames
+// fstride floats apart
 struct ImgSrc {
     const float* img;
     int Ly, Lx, h, B, tiles_x, ntile;
     int64_t fstride;
-    __device__ float operator()(int c, int col, int r, int x) const {
+    __device__ ImgView bind(int col) const {
         const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
-        const int Iy = ty * B - h + r, Ix = tx * B - h + x;
-        return (Iy >= 0 && Iy < Ly && Ix >= 0 && Ix < Lx)
-                   ? img[f * fstride + ((int64_t)c * Ly + Iy) * Lx + Ix]
-                   : 0.f;
+        return ImgView{img + f * fstride, Ly, Lx, ty * B - h, tx * B - h};
+    }
+};
+
+// frames of different shapes (serving): column gc = col0 + col belongs to
+// frame colf[gc]; vol selects the frame's volume or its ratio image
+struct TabSrc {
+    const FrameCols* fr;
+    const int* colf;
+    int col0, h, B;
+    bool vol;
+    __device__ ImgView bind(int col) const {
+        const int gc = col0 + col;
+        const FrameCols& d = fr[colf[gc]];
+        const int tile = gc - d.col0, ty = tile / d.tiles_x, tx = tile % d.tiles_x;
+        return ImgView{vol ? d.vsrc : d.rsrc, d.Ly, d.Lx, ty * B - h, tx * B - h};
     }
 };
 
 // packed PSF Wp[T*T][Spad][Cpad] read as one T x T kernel per (s, c); the
 // "tile" index is s here, and tap (qy, qx) = (Dy + h, Dx + h)
+struct TapView {
+    const float* W;  // at phase s
+    int T;
+    int64_t tap_stride;
+    __device__ float operator()(int c, int r, int x) const {
+        return (r < T && x < T) ? W[(int64_t)(r * T + x) * tap_stride + c] : 0.f;
+    }
+};
 struct TapSrc {
     const float* W;
     int T, Spad, Cpad;
-    __device__ float operator()(int c, int s, int r, int x) const {
-        return (r < T && x < T) ? W[(((int64_t)(r * T + x)) * Spad + s) * Cpad + c] : 0.f;
+    __device__ TapView bind(int s) const {
+        return TapView{W + (int64_t)s * Cpad, T, (int64_t)Spad * Cpad};
     }
 };
 
@@ -125,10 +162,11 @@ __global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, Out 
     float2* spec = sm;                               // [kCPB][F][H2]
     float2* scr = sm + kCPB * F * H2 + warp * F;     // per-warp [F]
     const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    const auto view = src.bind(tile);
     for (int job = warp; job < kCPB * F; job += 8) {  // rows
         const int ch = job / F, r = job % F, c = c0 + ch;
         for (int x = lane; x < F; x += 32)
-            scr[bitrev(x, LOG)] = make_float2(c < nch ? src(c, tile, r, x) : 0.f, 0.f);
+            scr[bitrev(x, LOG)] = make_float2(c < nch ? view(c, r, x) : 0.f, 0.f);
         __syncwarp();
         warp_fft<F, false>(scr);
         for (int k = lane; k < H2; k += 32) spec[(ch * F + r) * H2 + k] = scr[k];
@@ -150,8 +188,30 @@ __global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, Out 
     }
 }
 
-// forward output: Hv of polyphase channel s for lenslet (Iy, Ix); optionally
-// stored as an image [H][W] and / or turned into r = y / (Hv + eps)
+// forward output view of one tile: Hv of polyphase channel s at output (i, j)
+// of the tile = lenslet (y0 + i, x0 + j); optionally stored as an image
+// [H][W] and / or turned into r = y / (Hv + eps)
+struct HvView {
+    float* img;        // [H][W] or null
+    float* rcm;        // [S][Ly][Lx] ratio or null
+    const float* ycm;  // [S][Ly][Lx]
+    float* rimg;       // [H][W] ratio in image layout or null
+    float eps;
+    int N, W, Ly, Lx, y0, x0;
+    __device__ void operator()(int s, int i, int j, float hv) const {
+        const int Iy = y0 + i, Ix = x0 + j;
+        if (Iy >= Ly || Ix >= Lx) return;
+        const int64_t pix = ((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N;
+        if (img) img[pix] = hv;
+        if (rcm) {
+            const int64_t o = ((int64_t)s * Ly + Iy) * Lx + Ix;
+            const float den = hv + eps;
+            const float r = den > 0.f ? ycm[o] / den : 0.f;
+            rcm[o] = r;
+            if (rimg) rimg[pix] = r;
+        }
+    }
+};
 struct HvDst {
     float* img;        // [frames][H][W] or null
     float* rcm;        // [frames][S][Ly][Lx] ratio or null
@@ -160,40 +220,65 @@ struct HvDst {
     float eps;
     int N, W, Ly, Lx, B, tiles_x, ntile;
     int64_t fs_cm, fs_img;  // frame strides
-    __device__ void operator()(int s, int col, int i, int j, float hv) const {
+    __device__ HvView bind(int col) const {
         const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
-        const int Iy = ty * B + i, Ix = tx * B + j;
-        if (Iy >= Ly || Ix >= Lx) return;
-        const int64_t pix = f * fs_img + ((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N;
-        if (img) img[pix] = hv;
-        if (rcm) {
-            const int64_t o = f * fs_cm + ((int64_t)s * Ly + Iy) * Lx + Ix;
-            const float den = hv + eps;
-            const float r = den > 0.f ? ycm[o] / den : 0.f;
-            rcm[o] = r;
-            if (rimg) rimg[pix] = r;
-        }
+        const int64_t oc = f * fs_cm, oi = f * fs_img;
+        return HvView{img ? img + oi : nullptr, rcm ? rcm + oc : nullptr, ycm ? ycm + oc : nullptr,
+                      rimg ? rimg + oi : nullptr, eps, N, W, Ly, Lx, ty * B, tx * B};
+    }
+};
+struct TabHvDst {
+    const FrameCols* fr;
+    const int* colf;
+    int col0, N, B;
+    float eps;
+    __device__ HvView bind(int col) const {
+        const int gc = col0 + col;
+        const FrameCols& d = fr[colf[gc]];
+        const int tile = gc - d.col0, ty = tile / d.tiles_x, tx = tile % d.tiles_x;
+        return HvView{nullptr, d.rcm, d.ycm, d.rimg, eps, N, d.Lx * N, d.Ly, d.Lx, ty * B, tx * B};
     }
 };
 
-// backward output: H^T r of channel c = (z, t) for lenslet (Iy, Ix), into a
-// channel-major volume or a stack-order volume [Nz][H][W]
+// backward output view of one tile: H^T r of channel c = (z, t) at output
+// (i, j) = lenslet (y0 + i, x0 + j), into a channel-major volume and / or a
+// stack-order volume [Nz][H][W]
+struct VolView {
+    float* cm;     // [C][Ly][Lx] or null
+    float* stack;  // [Nz][H][W] or null
+    int N, S, H, W, Ly, Lx, y0, x0;
+    __device__ void operator()(int c, int i, int j, float x) const {
+        const int Iy = y0 + i, Ix = x0 + j;
+        if (Iy >= Ly || Ix >= Lx) return;
+        if (cm) cm[((int64_t)c * Ly + Iy) * Lx + Ix] = x;
+        if (stack) {
+            const int z = c / S, t = c % S;
+            stack[((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
+        }
+    }
+};
 struct VolDst {
     float* cm;     // [frames][C][Ly][Lx] or null
     float* stack;  // [frames][Nz][H][W] or null
     int N, S, H, W, Ly, Lx, B, tiles_x, ntile;
     int64_t fs_cm, fs_stack;  // frame strides
-    __device__ void operator()(int c, int col, int i, int j, float x) const {
+    __device__ VolView bind(int col) const {
         const int f = col / ntile, tile = col % ntile;
         const int ty = tile / tiles_x, tx = tile % tiles_x;
-        const int Iy = ty * B + i, Ix = tx * B + j;
-        if (Iy >= Ly || Ix >= Lx) return;
-        if (cm) cm[f * fs_cm + ((int64_t)c * Ly + Iy) * Lx + Ix] = x;
-        if (stack) {
-            const int z = c / S, t = c % S;
-            stack[f * fs_stack + ((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
-        }
+        return VolView{cm ? cm + f * fs_cm : nullptr, stack ? stack + f * fs_stack : nullptr,
+                       N, S, H, W, Ly, Lx, ty * B, tx * B};
+    }
+};
+struct TabVolDst {
+    const FrameCols* fr;
+    const int* colf;
+    int col0, N, S, B;
+    __device__ VolView bind(int col) const {
+        const int gc = col0 + col;
+        const FrameCols& d = fr[colf[gc]];
+        const int tile = gc - d.col0, ty = tile / d.tiles_x, tx = tile % d.tiles_x;
+        return VolView{d.xcm, nullptr, N, S, d.Ly * N, d.Lx * N, d.Ly, d.Lx, ty * B, tx * B};
     }
 };
 
@@ -208,6 +293,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const float2* __restrict__ in, 
     float2* spec = sm;
     float2* scr = sm + kCPB * F * H2 + warp * F;
     const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    const auto view = dst.bind(tile);
     for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
         const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
         spec[ch * F * H2 + bin] =
@@ -239,7 +325,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const float2* __restrict__ in, 
         __syncwarp();
         warp_fft<F, true>(scr);
         if (c < nch)
-            for (int j = lane; j < B; j += 32) dst(c, tile, i, j, scr[off + j].x * scale);
+            for (int j = lane; j < B; j += 32) view(c, i, j, scr[off + j].x * scale);
         __syncwarp();
     }
 }

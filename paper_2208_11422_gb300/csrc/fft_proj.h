@@ -29,6 +29,19 @@ struct FftBuffers {
     void* cg = nullptr;
 };
 
+// One frame of a batch whose frames differ in shape (serving): the transforms
+// find a column's frame through a column -> frame table, and the frame's
+// columns col0 .. col0 + tiles_y * tiles_x - 1 are its tiles in row-major order.
+struct FrameCols {
+    const float* vsrc;  // forward transform input: volume [C][Ly][Lx]
+    const float* rsrc;  // backward transform input: ratio [S][Ly][Lx]; null = all ones
+    float* rcm;         // forward output: ratio [S][Ly][Lx]
+    const float* ycm;   // data [S][Ly][Lx]
+    float* rimg;        // forward output: ratio image [H][W] (or null)
+    float* xcm;         // backward output [C][Ly][Lx]
+    int Ly, Lx, tiles_x, col0;
+};
+
 // picks F (or uses force_F if non-zero) by a bandwidth / arithmetic cost model
 // for `frames` frames; false if no plan fits (> 64 tiles, spectra too large,
 // or more than 256 phases)

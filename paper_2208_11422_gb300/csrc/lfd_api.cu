@@ -185,6 +185,7 @@ void free_all(lfd_ctx* ctx) {
         if (p) cudaFree(p);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+    if (ctx->host_pinned_slots) cudaFreeHost(ctx->host_pinned_slots);
     for (auto& ge : ctx->graph)
         if (ge) cudaGraphExecDestroy(ge);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
@@ -423,6 +424,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)mf * std::max<int64_t>(ctx->nflux, L2), true));
     CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * mf, true));
     CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned, 4 * sizeof(double)));
+    CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned_slots, 2 * sizeof(double) * mf));
     CREATE_CK(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
     CREATE_CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CREATE_CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
@@ -563,6 +565,16 @@ lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps, int
     return LFD_OK;
 }
 
+lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int* bins) {
+    if (!ctx) return LFD_EINVAL;
+    const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
+    if (F) *F = fp ? fp->F : 0;
+    if (B) *B = fp ? fp->B : 0;
+    if (tiles) *tiles = fp ? fp->ntile : 0;
+    if (bins) *bins = fp ? fp->bins : 0;
+    return LFD_OK;
+}
+
 lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_stream) {
     if (!ctx) return LFD_EINVAL;
     if (!v || !y_out) {
@@ -650,9 +662,9 @@ lfd_status lfd_set_profiling(lfd_ctx* ctx, int on) {
 
 lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n) {
     if (!ctx || !ms || n < 0) return LFD_EINVAL;
-    for (int i = 0; i < n && i < 8; ++i)
+    for (int i = 0; i < n && i < kStageSlots; ++i)
         ms[i] = ctx->prof.count ? (float)(ctx->prof.sum_ms[i] / ctx->prof.count) : 0.f;
-    for (int i = 8; i < n; ++i) ms[i] = 0.f;
+    for (int i = kStageSlots; i < n; ++i) ms[i] = 0.f;
     return LFD_OK;
 }
 
@@ -661,7 +673,7 @@ lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n) {
 namespace {
 
 // Enqueues one RL iteration for nf frames: reads iterate buffer `cur`, writes
-// the other one, leaves the frames' entropy and flux in ctx->hist. e9: nine
+// the other one, leaves the frames' entropy and flux in ctx->hist. e9: ten
 // events to record between stages (profiling), or null.
 lfd_status iter_body(lfd_ctx* ctx, int nf, int cur, cudaStream_t st, cudaEvent_t* e9) {
     const Geo& g = ctx->g;
@@ -676,8 +688,9 @@ lfd_status iter_body(lfd_ctx* ctx, int nf, int cur, cudaStream_t st, cudaEvent_t
                            ctx->opt.eps, st, e9 ? e9 + 1 : nullptr));
         LFD_CK(mark(3));
         LFD_CK(fft_backward(*fp, g, fb, nf, ctx->Rcm, ctx->Xcm, nullptr, st, e9 ? e9 + 4 : nullptr));
-        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, nf, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
         LFD_CK(mark(6));
+        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, nf, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(mark(7));
         LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, nf, ctx->mip,
                                 ctx->flux_part, st));
     } else {
@@ -695,14 +708,15 @@ lfd_status iter_body(lfd_ctx* ctx, int nf, int cur, cudaStream_t st, cudaEvent_t
         LFD_TRY(run_backward(ctx, st));
         LFD_CK(mark(5));
         LFD_CK(mark(6));
+        LFD_CK(mark(7));
         LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bp, ctx->invHt1, g,
                              ctx->mip, ctx->flux_part, st));
     }
-    LFD_CK(mark(7));
+    LFD_CK(mark(8));
     LFD_CK(launch_metric(ctx->mip, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS,
                          ctx->opt.l2_over_region, ctx->G, ctx->rowE2, ctx->coef, ctx->flux_part,
                          ctx->nflux, ctx->hist, ctx->hist + ctx->mf, st, nf, 1));
-    LFD_CK(mark(8));
+    LFD_CK(mark(9));
     return LFD_OK;
 }
 
@@ -789,7 +803,7 @@ lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int sto
             LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[cur], ctx->Vpb[0], ctx->Vpb[1], st));
         }
     }
-    constexpr int kEv = 9;  // events per iteration (see lfd_stage_times)
+    constexpr int kEv = 10;  // events per iteration (see lfd_stage_times)
     if (prof && ctx->prof.ev.size() < kEv * (size_t)n) {
         const size_t old = ctx->prof.ev.size();
         ctx->prof.ev.resize(kEv * (size_t)n, nullptr);
@@ -798,49 +812,87 @@ lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int sto
     cudaEvent_t* ev = prof ? ctx->prof.ev.data() : nullptr;
     if (graphs) LFD_TRY(ensure_graphs(ctx, nf));
 
-    // per frame: still iterating, iterations whose result is final, iterations run
+    // per frame: still iterating, iterations whose result is final, iterations run.
+    // Slots 0 .. nact-1 hold the frames still iterating (slot_frame[s]); with
+    // stop_at_predicted a stopped frame leaves its slot and the last active
+    // slot moves into it, so later iterations only process active frames.
     std::vector<char> active(nf, 1);
-    std::vector<int> done(nf, 0), ran_f(nf, 0);
-    int ran = 0, n_active = nf;
-    auto deposit = [&](int f, int buf) -> cudaError_t {  // frame f's result from buffer buf
-        if (fp) return launch_depoly_volume_cm(ctx->Vcm[buf] + f * g.C * L2, g, vd + f * nvol, st);
+    std::vector<int> done(nf, 0), ran_f(nf, 0), slot_frame(nf);
+    for (int f = 0; f < nf; ++f) slot_frame[f] = f;
+    int ran = 0, nact = nf;
+    auto deposit = [&](int f, int slot, int buf) -> cudaError_t {  // frame f's result from a slot of buf
+        if (fp) return launch_depoly_volume_cm(ctx->Vcm[buf] + slot * g.C * L2, g, vd + f * nvol, st);
         return launch_depoly_volume(ctx->Vp32[buf], g.m_base, g, vd, st);
     };
     for (int k = 0; k < n; ++k) {
         if (graphs) {
+            LFD_TRY(ensure_graphs(ctx, nact));
             LFD_CK(cudaGraphLaunch(ctx->graph[cur], st));
             count_launch(ctx->graph_launches);
         } else {
-            LFD_TRY(iter_body(ctx, nf, cur, st, prof ? ev + kEv * k : nullptr));
+            LFD_TRY(iter_body(ctx, nact, cur, st, prof ? ev + kEv * k : nullptr));
         }
-        // this iteration's entropy and flux of every frame into the histories
-        LFD_CK(cudaMemcpy2DAsync(hE + k, n * sizeof(double), ctx->hist, sizeof(double), sizeof(double),
-                                 nf, cudaMemcpyDeviceToHost, st));
-        LFD_CK(cudaMemcpy2DAsync(hF + k, n * sizeof(double), ctx->hist + ctx->mf, sizeof(double),
-                                 sizeof(double), nf, cudaMemcpyDeviceToHost, st));
         ran = k + 1;
-        for (int f = 0; f < nf; ++f)
-            if (active[f]) ran_f[f] = ran;
-        if (stop_at_predicted) {
-            LFD_CK(cudaStreamSynchronize(st));
-            for (int f = 0; f < nf; ++f) {
-                // E_{k+1} < E_k: frame f keeps v^k, still in buffer cur
-                if (active[f] && k >= 1 && hE[(size_t)f * n + k] < hE[(size_t)f * n + k - 1]) {
-                    LFD_CK(deposit(f, cur));
-                    active[f] = 0;
-                    done[f] = k;
-                    --n_active;
-                }
-            }
-            if (n_active == 0) break;
+        if (!stop_at_predicted) {
+            // slots never move: this iteration's values go straight to the histories
+            LFD_CK(cudaMemcpy2DAsync(hE + k, n * sizeof(double), ctx->hist, sizeof(double), sizeof(double),
+                                     nf, cudaMemcpyDeviceToHost, st));
+            LFD_CK(cudaMemcpy2DAsync(hF + k, n * sizeof(double), ctx->hist + ctx->mf, sizeof(double),
+                                     sizeof(double), nf, cudaMemcpyDeviceToHost, st));
+            for (int f = 0; f < nf; ++f) ran_f[f] = ran;
+            cur ^= 1;
+            continue;
         }
-        cur ^= 1;
+        LFD_CK(cudaMemcpyAsync(ctx->host_pinned_slots, ctx->hist, nact * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaMemcpyAsync(ctx->host_pinned_slots + ctx->mf, ctx->hist + ctx->mf, nact * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaStreamSynchronize(st));
+        const int nxt = cur ^ 1;
+        std::vector<char> freed(nact, 0);
+        for (int s2 = 0; s2 < nact; ++s2) {
+            const int f = slot_frame[s2];
+            hE[(size_t)f * n + k] = ctx->host_pinned_slots[s2];
+            hF[(size_t)f * n + k] = ctx->host_pinned_slots[ctx->mf + s2];
+            ran_f[f] = ran;
+            // E_{k+1} < E_k: frame f keeps v^k, still in buffer cur
+            if (k >= 1 && hE[(size_t)f * n + k] < hE[(size_t)f * n + k - 1]) {
+                LFD_CK(deposit(f, s2, cur));
+                active[f] = 0;
+                done[f] = k;
+                freed[s2] = 1;
+            }
+        }
+        // compact: the highest active slots move down into the freed ones
+        int hi = nact - 1;
+        for (int s2 = 0; s2 < nact; ++s2) {
+            if (!freed[s2]) continue;
+            while (hi > s2 && freed[hi]) --hi;
+            if (hi <= s2) break;
+            if (fp) {
+                LFD_CK(cudaMemcpyAsync(ctx->Vcm[nxt] + s2 * g.C * L2, ctx->Vcm[nxt] + hi * g.C * L2,
+                                       g.C * L2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                LFD_CK(cudaMemcpyAsync(ctx->ycm + s2 * g.S * L2, ctx->ycm + hi * g.S * L2,
+                                       g.S * L2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            }
+            slot_frame[s2] = slot_frame[hi];
+            freed[s2] = 0;
+            freed[hi] = 1;
+            --hi;
+        }
+        int na = 0;
+        for (int s2 = 0; s2 < nact; ++s2) na += freed[s2] ? 0 : 1;
+        nact = na;
+        cur = nxt;
+        if (nact == 0) break;
     }
-    for (int f = 0; f < nf; ++f)
+    for (int s2 = 0; s2 < nact; ++s2) {
+        const int f = slot_frame[s2];
         if (active[f]) {
-            LFD_CK(deposit(f, cur));
+            LFD_CK(deposit(f, s2, cur));
             done[f] = ran;
         }
+    }
     if (!vdev) LFD_CK(cudaMemcpyAsync(v, vd, nf * nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
     LFD_CK(cudaEventRecord(ctx->ev_out, st));
     LFD_CK(cudaStreamWaitEvent(ust, ctx->ev_out, 0));
@@ -867,14 +919,17 @@ lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int sto
                 LFD_CK(cudaEventElapsedTime(&t[i], ev[kEv * k], ev[kEv * k + i]));
             const bool f = fp != nullptr;
             double* sm = ctx->prof.sum_ms;
-            sm[0] += f ? t[3] : t[2];              // forward projection
-            sm[1] += f ? 0.0 : t[3] - t[2];        // ratio (fused in the FFT variant)
-            sm[2] += t[6] - t[3];                  // backprojection
-            sm[3] += t[7] - t[6];                  // update
-            sm[4] += t[8] - t[7];                  // metric
-            sm[5] += t[2] - t[1];                  // forward contraction
-            sm[6] += t[5] - t[4];                  // backward contraction
+            sm[0] += f ? t[3] : t[2];                        // forward projection
+            sm[1] += f ? 0.0 : t[3] - t[2];                  // ratio (fused in the FFT variant)
+            sm[2] += t[7] - t[3];                            // backprojection
+            sm[3] += t[8] - t[7];                            // update
+            sm[4] += t[9] - t[8];                            // metric
+            sm[5] += t[2] - t[1];                            // forward contraction
+            sm[6] += t[5] - t[4];                            // backward contraction
             sm[7] += f ? t[1] + (t[3] - t[2]) + (t[4] - t[3]) + (t[6] - t[5]) : 0.0;  // transforms
+            sm[8] += f ? t[1] : 0.0;                         // volume R2C (forward input)
+            sm[9] += f ? t[6] - t[5] : 0.0;                  // volume C2R (backward output)
+            sm[10] += f ? t[7] - t[6] : 0.0;                 // exact low-sensitivity backprojection
         }
         ctx->prof.count += ran;
     }

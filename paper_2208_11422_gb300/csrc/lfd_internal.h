@@ -53,12 +53,13 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-// CUDA events bracketing the five stages of every RL iteration while
-// profiling is on; read back (and averaged) at the end of lfd_rl_iterate.
+// CUDA events bracketing the stages of every RL iteration while profiling is
+// on; read back (and averaged) at the end of lfd_rl_iterate.
+constexpr int kStageSlots = 11;  // averaged stage times (lfd_stage_times)
 struct StageTimes {
-    std::vector<cudaEvent_t> ev;  // 6 per iteration slot
+    std::vector<cudaEvent_t> ev;  // 10 per iteration
     bool on = false;
-    double sum_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double sum_ms[kStageSlots] = {};
     int64_t count = 0;
 };
 
@@ -98,6 +99,7 @@ struct lfd_ctx {
     double* hist = nullptr;      // [2][mf]: entropy, flux of the latest iteration
     double* host_pinned = nullptr;  // [4]
     double* host_hist = nullptr;    // pinned [2][mf][host_hist_n] histories
+    double* host_pinned_slots = nullptr;  // pinned [2][mf] latest values per slot
     int host_hist_n = 0;
     int mf = 1;                  // frames per batch (max_frames)
     // CUDA graphs of one RL iteration (reading iterate buffer 0 or 1)

@@ -75,6 +75,8 @@ _SIGS = {
     "lfd_predict_stop": (_I, [ctypes.POINTER(_D), _I]),
     "lfd_get_geometry": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)]),
+    "lfd_get_fft_plan": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(_I)]),
     "lfd_launch_count": (ctypes.c_uint64, []),
     "lfd_set_profiling": (_I, [_VP, _I]),
     "lfd_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
@@ -259,6 +261,13 @@ def lfd_get_geometry(ctx) -> dict:
             "device_bytes": nbytes.value}
 
 
+def lfd_get_fft_plan(ctx) -> dict:
+    F, B, nt, bins = _I(0), _I(0), _I(0), _I(0)
+    _check(load().lfd_get_fft_plan(ctx, ctypes.byref(F), ctypes.byref(B), ctypes.byref(nt),
+                                   ctypes.byref(bins)), ctx)
+    return {"F": F.value, "B": B.value, "tiles": nt.value, "bins": bins.value}
+
+
 def lfd_launch_count() -> int:
     return int(load().lfd_launch_count())
 
@@ -269,7 +278,8 @@ def lfd_set_profiling(ctx, on: bool = True):
 
 def lfd_stage_times(ctx):
     """Mean stage times (ms): forward, ratio, backward, update, metric, forward
-    contraction, backward contraction, FFT transforms."""
-    arr = (ctypes.c_float * 8)()
-    _check(load().lfd_stage_times(ctx, arr, 8), ctx)
+    contraction, backward contraction, FFT transforms, volume R2C, volume C2R,
+    exact low-sensitivity backprojection."""
+    arr = (ctypes.c_float * 11)()
+    _check(load().lfd_stage_times(ctx, arr, 11), ctx)
     return list(arr)

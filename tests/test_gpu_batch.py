@@ -22,11 +22,12 @@ def _built():
     lib()
 
 
-def make_frames(nf):
+def make_frames(nf, scales=None):
     g = synth.CONFIGS[0]
     psf = synth.make_psf(0)
     vols = synth.timelapse_beads(0, nf, 300, step_sigma=1.0)
-    scales = synth.timelapse_scales(nf, 301, 100.0, 2000.0)
+    if scales is None:
+        scales = synth.timelapse_scales(nf, 301, 100.0, 2000.0)
     ys = [synth.poisson_data(oracle.forward(psf, g.nnum, vols[f]), scales[f], g.background, 310 + f)
           for f in range(nf)]
     return g, psf, np.stack(ys).astype(np.float32)
@@ -63,6 +64,38 @@ def test_batch_equals_single_frames(prec, stop):
         lfd.lfd_destroy(ctx)
     if stop:
         assert len(set(done)) >= 1
+
+
+# photon scales whose frames stop at iterations 9, 7, 12, 13, 8, 9 in the FP64
+# oracle: frames leave the batch at different iterations, so the remaining ones
+# move to other slots (and other FFT columns) while they keep iterating
+SPREAD_SCALES = [30.0, 100.0, 300.0, 1000.0, 3000.0, 10000.0]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_batch_slots_compact_as_frames_stop(prec, use_graph):
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    nf, n = len(SPREAD_SCALES), 16
+    g, psf, ys = make_frames(nf, SPREAD_SCALES)
+    dev = torch.device("cuda:0")
+    ctx = ctx_for(psf, g, prec, nf, use_graph)
+    try:
+        v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+        done, pred, ent, _ = lfd.lfd_rl_iterate_batch(ctx, nf, torch.from_numpy(ys).to(dev), v, n, True)
+        assert len(set(done)) >= 3, done
+        vb = v.cpu().numpy()
+        for f in range(nf):
+            v1 = torch.ones((g.nz, g.H, g.W), device=dev)
+            d1, p1, e1, _ = lfd.lfd_rl_iterate(ctx, torch.from_numpy(ys[f]).to(dev), v1, n, True)
+            assert (done[f], pred[f]) == (d1, p1), f
+            # a stopped frame's history ends after the iteration that showed the drop
+            assert np.isnan(ent[f][d1 + 1:]).all() and not np.isnan(ent[f][:d1 + 1]).any(), f
+            assert rel_l2(vb[f], v1.cpu().numpy()) <= 1e-6, f
+            np.testing.assert_allclose(ent[f][:d1 + 1], e1[:d1 + 1], rtol=1e-9)
+    finally:
+        lfd.lfd_destroy(ctx)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
