@@ -40,9 +40,14 @@ def parse():
     p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
     p.add_argument("--variant", default="fft", choices=["fft", "direct"])
     p.add_argument("--config", type=int, default=WORKLOAD_CFG)
-    p.add_argument("--workload", default="large", choices=["large", "batch"],
-                   help="large: one 2025x2025 px frame; batch: 64-frame time-lapse at 615x615 px")
+    p.add_argument("--workload", default="large", choices=["large", "batch", "serve"],
+                   help="large: one 2025x2025 px frame; batch: 64-frame time-lapse at 615x615 px; "
+                        "serve: Poisson request stream over 4 PSF sets")
     p.add_argument("--frames", type=int, default=64)
+    p.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    p.add_argument("--pool", type=int, default=32, help="serving: distinct frames")
+    p.add_argument("--serve-frames", type=int, default=32, help="serving: frames per PSF set batch")
     p.add_argument("--cap", type=int, default=40)
     p.add_argument("--depths", type=int, default=None,
                    help="override the number of depths (small cases for profiler captures)")
@@ -542,6 +547,145 @@ def run_batch(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def run_serve(args, rank, world, local):
+    """Serving: a Poisson stream of --requests requests (mean --rate per second)
+    over 4 resident PSF sets (Nnum, Nz drawn per set, PSF 11 lenslets wide).
+    Each request has its own lenslet grid (33..121 per axis), bead count
+    (50..5000) and photon scale (log-uniform 100..5000). The server admits
+    requests by device footprint, batches them per PSF set in split BF16 and
+    stops each at its predicted iteration (cap --cap). The frames' data come
+    from a pool of --pool distinct requests, projected once before the run;
+    arrival i uses pool entry i mod --pool. Host buffers are page-locked."""
+    import collections
+    import torch
+    from paper_2208_11422_gb300 import build, lfd, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    lfd.load()
+    sets = [synth.serve_psf_set(j) for j in (1, 2, 3, 4)]
+    pool = synth.serve_requests(args.pool, 910 + rank)
+    arrivals = synth.serve_requests(args.requests, 920 + rank, args.rate)
+    Lmax = synth.SERVE_LENSLETS[1]
+    # pool data: y = Poisson(scale * H v) + 5 with H v from an FP32 context at the
+    # largest sensor of the set (the volume is zero outside the request's frame,
+    # so the crop is the frame's own projection)
+    ys = [None] * len(pool)
+    for si, (nnum, nz, P, psf) in enumerate(sets):
+        Hm = Lmax * nnum
+        ctx = lfd.lfd_create(torch.from_numpy(psf).to(dev), P, nnum, nz, Hm, Hm,
+                             lfd.lfd_default_options(precision="fp32", variant="fft"))
+        vbig = torch.zeros((nz, Hm, Hm), device=dev)
+        hv = torch.empty((Hm, Hm), device=dev)
+        for k, rq in enumerate(pool):
+            if rq.set_id != si + 1:
+                continue
+            H, W = rq.ly * nnum, rq.lx * nnum
+            vbig.zero_()
+            vbig[:, :H, :W] = torch.from_numpy(synth.serve_volume(rq, nnum, nz)).to(dev)
+            lfd.lfd_forward(ctx, vbig, hv)
+            torch.cuda.synchronize()
+            ys[k] = torch.from_numpy(synth.poisson_data(hv[:H, :W].cpu().numpy(), rq.scale, 5.0,
+                                                        rq.seed + 7)).pin_memory()
+        lfd.lfd_destroy(ctx)
+        del vbig, hv
+        torch.cuda.empty_cache()
+
+    opt = lfd.lfd_server_default_options("bf16x3", max_iter=args.cap,
+                                         max_frames_per_set=args.serve_frames)
+    srv = lfd.lfd_server_create(opt)
+    ids = [lfd.lfd_server_add_psf(srv, torch.from_numpy(psf).to(dev), P, nnum, nz, Lmax * nnum, Lmax * nnum)
+           for nnum, nz, P, psf in sets]
+    torch.cuda.synchronize()
+    free_v = collections.defaultdict(list)   # pool entry -> page-locked result buffers
+
+    def v_buffer(k):
+        if free_v[k]:
+            return free_v[k].pop()
+        rq = pool[k]
+        nnum, nz = sets[rq.set_id - 1][0], sets[rq.set_id - 1][1]
+        return torch.empty((nz, rq.ly * nnum, rq.lx * nnum)).pin_memory()
+
+    pending = collections.deque()
+    cv = threading.Condition()
+    done_rec = []
+    submitted = len(arrivals)
+
+    def collector():
+        for _ in range(submitted):
+            with cv:
+                while not pending:
+                    cv.wait()
+                i, k, req, v, t_arr, t_sub = pending.popleft()
+            if req is None:
+                done_rec.append((i, None, t_arr, t_sub, time.perf_counter()))
+                continue
+            r = lfd.lfd_poll(srv, req, -1)
+            done_rec.append((i, r, t_arr, t_sub, time.perf_counter()))
+            with cv:
+                free_v[k].append(v)
+
+    l0 = lfd.lfd_launch_count()
+    th = threading.Thread(target=collector)
+    th.start()
+    rejected = 0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i, a in enumerate(arrivals):
+            dt = t0 + a.arrival_s - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            k = i % len(pool)
+            rq = pool[k]
+            with cv:
+                v = v_buffer(k)
+            t_sub = time.perf_counter()
+            try:
+                req = lfd.lfd_submit(srv, ids[rq.set_id - 1], ys[k], v, max_iter=args.cap,
+                                     stop_at_predicted=True, entropy_hist=True)
+            except lfd.LfdError:
+                req = None
+                rejected += 1
+            with cv:
+                pending.append((i, k, req, v, t0 + a.arrival_s, t_sub))
+                cv.notify()
+        th.join()
+        t_end = max(rec[4] for rec in done_rec)
+    stats = lfd.lfd_server_stats_get(srv)
+    lfd.lfd_server_destroy(srv)
+    ok = [rec for rec in done_rec if rec[1] is not None and rec[1]["status"] == lfd.LFD_OK]
+    lat = np.array([r["latency_us"] / 1e3 + (t_sub - t_arr) * 1e3 for _, r, t_arr, t_sub, _ in ok])
+    queue = np.array([r["queue_us"] / 1e3 for _, r, _, _, _ in ok])
+    iters = np.array([r["iters_run"] for _, r, _, _, _ in ok])
+    span = t_end - t0
+    frames_s = len(ok) / span
+    out = {
+        "metric": "served frames/s, Poisson stream of %d requests at %g req/s over 4 resident PSF sets "
+                  "(mixed sensor sizes, Nnum 11-15, 21-51 depths), split BF16, predicted stop (cap %d)"
+                  % (len(arrivals), args.rate, args.cap),
+        "value": frames_s, "unit": "frames/s", "n_gpus": world, "steps": len(arrivals), "warmup": 0,
+        "ms_per_step": span * 1e3 / max(1, len(ok)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3",
+        "data": "synthetic (beads, Poisson noise; %d distinct frames reused)" % len(pool),
+        "config": {"workload": "lf_serve_4sets_poisson%greq_s" % args.rate, "requests": len(arrivals),
+                   "rate_req_s": args.rate, "cap": args.cap, "pool": len(pool),
+                   "max_frames_per_set": args.serve_frames,
+                   "psf_sets": [{"Nnum": n, "Nz": z, "P": p} for n, z, p, _ in sets]},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean())},
+        "queue_ms_mean": float(queue.mean()),
+        "offered_req_s": len(arrivals) / max(a.arrival_s for a in arrivals),
+        "completed": len(ok), "rejected": rejected, "iterations_mean": float(iters.mean()),
+        "frame_iterations_per_s": float(iters.sum() / span),
+        "server": {k: stats[k] for k in ("ticks", "frame_iterations", "columns", "arena_bytes",
+                                         "arena_peak_bytes", "resident_bytes")},
+        "gpu_launches": lfd.lfd_launch_count() - l0, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
     if rank != 0:
@@ -581,6 +725,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch":
         run_batch(args, rank, world, local)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local)
     else:
         run_lfd(args, rank, world, local)
     if world > 1:

@@ -52,11 +52,14 @@ typedef enum {
     LFD_EINVAL = 1,       /* invalid argument or shape                         */
     LFD_ENOMEM = 2,       /* a device or host allocation failed                 */
     LFD_ECUDA = 3,        /* a CUDA runtime/driver call failed                  */
-    LFD_ENOTREADY = 4,    /* reserved for asynchronous request handles          */
-    LFD_ETIMEDOUT = 5,    /* a bounded device wait gave up (kernel error flag)  */
-    LFD_EBUSY = 6,        /* reserved                                           */
+    LFD_ENOTREADY = 4,    /* lfd_poll: the request has not finished yet         */
+    LFD_ETIMEDOUT = 5,    /* a bounded device wait gave up (kernel error flag),
+                             or lfd_poll's timeout passed                        */
+    LFD_EBUSY = 6,        /* lfd_submit: queue full; lfd_cancel: request already
+                             running; lfd_server_add_psf: server started        */
     LFD_EINTERNAL = 7,    /* internal consistency check failed                  */
-    LFD_EUNSUPPORTED = 8  /* option not available for this shape / device       */
+    LFD_EUNSUPPORTED = 8, /* option not available for this shape / device       */
+    LFD_ECANCELED = 9     /* the request was cancelled before it started        */
 } lfd_status;
 
 /* Arithmetic of the two projections (the ratio, update and metric are FP32 with
@@ -93,8 +96,8 @@ typedef enum {
     LFD_DIRECT = 0,  /* polyphase implicit GEMM: tcgen05 (BF16 precisions) or CUDA
                         cores (FP32)                                                */
     LFD_FFT = 1      /* overlap-save FFT on the lenslet grid with cached PSF spectra,
-                        FP32 transforms and FP32 complex contractions; precision
-                        must be LFD_FP32                                            */
+                        FP32 transforms; complex contractions in FP32 on the CUDA
+                        cores (LFD_FP32) or in split BF16 on tcgen05 (LFD_BF16X3) */
 } lfd_variant;
 
 /* Fills *opt with the defaults listed above. */
@@ -259,6 +262,117 @@ uint64_t lfd_launch_count(void);
  * lfd_stage_times writes the mean over every iteration run since then (zeros
  * if none) into ms[0..n-1] (entries past 10 are 0). */
 lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n);
+
+/* ------------------------------------------------------------------ serving --
+ * A server reconstructs a stream of light-field frames with continuous
+ * batching. Fig. 1 of the paper moves each PSF to the GPU once and reuses it
+ * for every reconstruction; here several PSF sets stay resident (as FFT
+ * spectra), frames of any sensor size up to a set's maximum are admitted when
+ * their device footprint fits (Fig. 1 estimates the memory a reconstruction
+ * needs before allocating it), frames of one set advance together through
+ * one launch per stage, and each frame stops at its metric-predicted
+ * iteration (Section 2.2) and leaves the batch while others join.
+ *
+ * Arithmetic is the LFD_FFT variant's (split BF16 or FP32), with the same
+ * results as an lfd_ctx made for the frame's shape with the same options and
+ * the same FFT size (up to rounding order).
+ *
+ * Threads: lfd_submit, lfd_poll, lfd_cancel and lfd_server_stats may be called
+ * from any host thread. One scheduler thread per server owns the GPU work; it
+ * runs on the device that was current in lfd_server_create. */
+typedef struct lfd_server lfd_server;
+
+typedef struct {
+    lfd_options opt;          /* precision (LFD_BF16X3 default, or LFD_FP32), eps,
+                                 optics, XS / YS, l2_over_region, fft_size; variant
+                                 is LFD_FFT; max_frames and use_graph are ignored  */
+    int64_t arena_bytes;      /* device memory for frames in flight; 0 (default):
+                                 85 % of the free memory at the first submit        */
+    int max_frames_per_set;   /* frames iterating together per PSF set (default 32) */
+    int max_cols;             /* FFT tiles per contraction launch (default 128; a
+                                 multiple of 16); larger batches take several
+                                 launches                                          */
+    int max_queue;            /* requests waiting for admission (default 4096)      */
+    int max_iter;             /* iteration cap of a request with max_iter 0
+                                 (default 40)                                       */
+} lfd_server_options;
+
+typedef struct {
+    int set_id;               /* from lfd_server_add_psf                           */
+    int H, W;                 /* sensor size in pixels: positive multiples of the
+                                 set's Nnum, at most the set's max_H x max_W       */
+    const float* y;           /* [H][W] light-field image, host or device           */
+    float* v_out;             /* [Nz][H][W] result, host or device                   */
+    int max_iter;             /* iteration cap (0: the server's)                     */
+    int stop_at_predicted;    /* 1: stop at the predicted iteration, as in
+                                 lfd_rl_iterate; 0: run max_iter iterations         */
+    double* entropy_hist;     /* optional host array [max_iter]: E after each
+                                 iteration run, NaN after the last                 */
+} lfd_request;
+/* The caller keeps y, v_out and entropy_hist alive and unchanged until
+ * lfd_poll reports the request finished (or it is cancelled). The start volume
+ * is all ones. Host buffers in page-locked memory are copied asynchronously;
+ * pageable ones stall the scheduler while they are copied. */
+
+typedef struct {
+    int status;               /* lfd_status of the request: LFD_OK, LFD_ECANCELED,
+                                 LFD_ECUDA, LFD_ETIMEDOUT                          */
+    int iters_done;           /* iterations whose result v_out holds                */
+    int iters_run;            /* iterations computed                                */
+    int predicted;            /* lfd_predict_stop of the entropy history            */
+    int64_t queue_us;         /* submit -> admission (device memory reserved)       */
+    int64_t latency_us;       /* submit -> result in v_out                          */
+} lfd_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected, cancelled;
+    int64_t frame_iterations; /* RL iterations over all frames                      */
+    int64_t ticks;            /* batched steps over all sets                        */
+    int64_t columns;          /* FFT tiles transformed in forward passes            */
+    int64_t arena_bytes, arena_peak_bytes, resident_bytes;
+    int queued, in_flight;
+} lfd_server_stats;
+
+/* Fills *opt with the defaults listed above. */
+void lfd_server_default_options(lfd_server_options* opt);
+
+/* Creates a server on the current device and starts its scheduler thread.
+ * Errors: LFD_EINVAL (options), LFD_ENOMEM, LFD_ECUDA. */
+lfd_status lfd_server_create(const lfd_server_options* opt, lfd_server** out);
+
+/* Makes a PSF set resident: PSF [Nz][Nnum][Nnum][P][P] (host or device, copied)
+ * for frames up to max_H x max_W pixels. Computes the PSF spectra (and keeps
+ * the PSF for the exact backprojection of low-sensitivity voxels).
+ * Only before the first lfd_submit (LFD_EBUSY after).
+ * Errors: LFD_EINVAL (shape rules of lfd_create), LFD_ENOMEM, LFD_ECUDA,
+ * LFD_EUNSUPPORTED (no FFT tiling fits, or split BF16 without tcgen05). */
+lfd_status lfd_server_add_psf(lfd_server* srv, const float* psf, int P, int Nnum, int Nz,
+                              int max_H, int max_W, int* set_id);
+
+/* Queues a request; *ticket identifies it. Returns at once.
+ * Errors: LFD_EINVAL (unknown set, shape, NULL y / v_out), LFD_ENOMEM (the
+ * frame alone needs more than the arena), LFD_EBUSY (queue full). */
+lfd_status lfd_submit(lfd_server* srv, const lfd_request* req, uint64_t* ticket);
+
+/* Waits up to timeout_us microseconds (0: do not wait; < 0: no limit) for the
+ * request to finish. LFD_OK: finished, *res filled, the ticket is released.
+ * LFD_ENOTREADY (timeout_us == 0) or LFD_ETIMEDOUT: not finished yet.
+ * LFD_EINVAL: unknown or released ticket. */
+lfd_status lfd_poll(lfd_server* srv, uint64_t ticket, int64_t timeout_us, lfd_result* res);
+
+/* Cancels a request that has not been admitted yet: LFD_OK (poll then reports
+ * status LFD_ECANCELED), LFD_EBUSY if it is already running or finished,
+ * LFD_EINVAL for an unknown ticket. */
+lfd_status lfd_cancel(lfd_server* srv, uint64_t ticket);
+
+lfd_status lfd_server_stats_get(const lfd_server* srv, lfd_server_stats* stats);
+
+/* Last error message of the server (scheduler or API), "" if none. */
+const char* lfd_server_last_error(const lfd_server* srv);
+
+/* Finishes the requests already admitted, cancels the queued ones, stops the
+ * scheduler and frees everything. Tickets not yet polled become invalid. */
+void lfd_server_destroy(lfd_server* srv);
 
 #ifdef __cplusplus
 }

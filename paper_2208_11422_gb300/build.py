@@ -31,7 +31,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-pthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -493,36 +493,81 @@ cudaError_t contract_adj_all(const FftPlan& p, const Geo& g, const float2* Wf, c
 // with c = (z, t = ty*N + tx), i' = Iy*N + ty, j' = Ix*N + tx. The FFT variant
 // uses it for voxels whose sensitivity H^T 1 is so small that the transforms'
 // absolute error floor would dominate their update.
-__global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, int nf,
-                            const float* __restrict__ rimg, const float* __restrict__ psf, Geo g,
-                            float* __restrict__ xcm) {
+// exact H^T r at channel-major voxel idx of one frame; rimg == null reads an
+// all-ones image (H^T 1); one warp, result valid in every lane
+__device__ float exact_bwd_voxel(int64_t idx, const float* __restrict__ rimg,
+                                 const float* __restrict__ psf, const Geo& g) {
     const int lane = threadIdx.x & 31;
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     const int c0 = (g.P - 1) / 2;
+    const int c = (int)(idx / L2);
+    const int64_t l = idx % L2;
+    const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
+    const int z = c / g.S, t = c % g.S, ty = t / g.N, tx = t % g.N;
+    const int ip = Iy * g.N + ty, jp = Ix * g.N + tx;
+    const float* K = psf + (((int64_t)z * g.N + ty) * g.N + tx) * g.P * g.P;
+    const int mi0 = max(0, c0 - ip), mi1 = min(g.P, g.H + c0 - ip);
+    const int mj0 = max(0, c0 - jp), mj1 = min(g.P, g.W + c0 - jp);
+    float acc = 0.f;
+    for (int mi = mi0; mi < mi1; ++mi) {
+        const float* kk = K + (int64_t)mi * g.P;
+        float row = 0.f;
+        if (rimg) {
+            const float* rr = rimg + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
+            for (int mj = mj0 + lane; mj < mj1; mj += 32) row = fmaf(rr[mj], kk[mj], row);
+        } else {
+            for (int mj = mj0 + lane; mj < mj1; mj += 32) row += kk[mj];
+        }
+        acc += row;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+__global__ void k_exact_bwd(const int64_t* __restrict__ list, int64_t n, int nf,
+                            const float* __restrict__ rimg, const float* __restrict__ psf, Geo g,
+                            float* __restrict__ xcm) {
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
     for (int64_t qq = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; qq < n * nf;
          qq += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int f = (int)(qq / n);
         const int64_t idx = list[qq % n];
-        const float* rimg_f = rimg + (int64_t)f * g.H * g.W;
-        const int c = (int)(idx / L2);
-        const int64_t l = idx % L2;
-        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
-        const int z = c / g.S, t = c % g.S, ty = t / g.N, tx = t % g.N;
-        const int ip = Iy * g.N + ty, jp = Ix * g.N + tx;
-        const float* K = psf + (((int64_t)z * g.N + ty) * g.N + tx) * g.P * g.P;
-        const int mi0 = max(0, c0 - ip), mi1 = min(g.P, g.H + c0 - ip);
-        const int mj0 = max(0, c0 - jp), mj1 = min(g.P, g.W + c0 - jp);
-        float acc = 0.f;
-        for (int mi = mi0; mi < mi1; ++mi) {
-            const float* rr = rimg_f + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
-            const float* kk = K + (int64_t)mi * g.P;
-            float row = 0.f;
-            for (int mj = mj0 + lane; mj < mj1; mj += 32) row = fmaf(rr[mj], kk[mj], row);
-            acc += row;
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) xcm[(int64_t)f * g.C * L2 + idx] = acc;
+        const float acc = exact_bwd_voxel(idx, rimg + (int64_t)f * g.H * g.W, psf, g);
+        if ((threadIdx.x & 31) == 0) xcm[(int64_t)f * g.C * L2 + idx] = acc;
     }
+}
+
+// the same for one frame whose voxel list and its length live on the device
+__global__ void k_exact_bwd_dev(const int* __restrict__ list, const int* __restrict__ n,
+                                const float* __restrict__ rimg, const float* __restrict__ psf, Geo g,
+                                float* __restrict__ xcm) {
+    const int cnt = *n;
+    for (int64_t qq = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; qq < cnt;
+         qq += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t idx = list[qq];
+        const float acc = exact_bwd_voxel(idx, rimg, psf, g);
+        if ((threadIdx.x & 31) == 0) xcm[idx] = acc;
+    }
+}
+
+// largest value of x[0..n) (clamped at 0) into *mx (zeroed beforehand); the
+// bit patterns of non-negative floats order like the floats themselves
+__global__ void k_max_nonneg(const float* __restrict__ x, int64_t n, unsigned* __restrict__ mx) {
+    float m = 0.f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, x[e]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(m));
+}
+
+// appends every index with !(x >= frac * max) to list (in no particular order)
+__global__ void k_low_list(const float* __restrict__ x, int64_t n, const unsigned* __restrict__ mx,
+                           float frac, int* __restrict__ list, int* __restrict__ count) {
+    const float thr = frac * __uint_as_float(*mx);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (!(x[e] >= thr)) list[atomicAdd(count, 1)] = (int)e;
 }
 
 // ------------------------------------------------ layout and update kernels --
@@ -710,7 +755,7 @@ cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int 
 }  // namespace
 
 // ------------------------------------------------------------------ plan --
-bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames) {
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, bool split_bf16) {
     FftPlan best{};
     double best_t = 1e300;
     for (int F : {32, 64}) {
@@ -733,10 +778,13 @@ bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames) {
         q.Sw = (g.S + 7) & ~7;
         const double spectra = (double)q.bins * g.S * q.Cf * 8.0;
         if (spectra > 96e9) continue;  // keep the cached spectra well inside HBM
+        // complex multiply-adds at 8 flops: FP32 FMA on the CUDA cores, or three
+        // BF16 tensor-core products per term (split BF16)
         const double flops = (double)q.bins * g.S * q.ntile * frames * g.C * 8.0;
+        const double rate = split_bf16 ? 1.7e15 / 3.0 : 6.0e13;
         // transforms: one F x F patch per tile, frame and channel
         const double xform = (double)q.ntile * frames * (g.C + g.S) * 2.0 * F * F * 8.0;
-        const double t = std::max(spectra / 6.0e12, flops / 6.0e13) + xform / 4.0e12;
+        const double t = std::max(spectra / 6.0e12, flops / rate) + xform / 4.0e12;
         if (t < best_t) {
             best_t = t;
             best = q;
@@ -828,6 +876,50 @@ cudaError_t launch_exact_bwd(const int64_t* list, int64_t n, int nf, const float
     k_exact_bwd<<<(unsigned)blocks, 256, 0, st>>>(list, n, nf, rimg, psf, g, xcm);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_exact_bwd_dev(const int* list, const int* n, const float* rimg, const float* psf,
+                                 const Geo& g, float* xcm, cudaStream_t st) {
+    k_exact_bwd_dev<<<152 * 8, 256, 0, st>>>(list, n, rimg, psf, g, xcm);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_low_list(const float* x, int64_t n, float frac, unsigned* mx, int* list, int* count,
+                            cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_max_nonneg<<<grid_for(n), 256, 0, st>>>(x, n, mx);
+    k_low_list<<<grid_for(n), 256, 0, st>>>(x, n, mx, frac, list, count);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
+                            const int* colf, int col0, int ncol, float eps, cudaStream_t st) {
+    TabSrc src{fr, colf, col0, p.h, p.B, true};
+    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, ncol, nullptr, b.Xp, b.ncolp, st)
+                         : r2c_any(p, src, g.C, p.Cf, ncol, b.Xh, nullptr, 0, st);
+    if (e != cudaSuccess) return e;
+    e = b.cg ? cgemm_forward(b.cg, ncol, st) : contract_fwd_all(p, g, b.Wf, b.Xh, b.Yh, ncol, st);
+    if (e != cudaSuccess) return e;
+    TabHvDst dst{fr, colf, col0, g.N, p.B, eps};
+    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
+}
+
+cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
+                             const int* colf, int col0, int ncol, cudaStream_t st) {
+    TabSrc src{fr, colf, col0, p.h, p.B, false};
+    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, ncol, nullptr, b.Yp, b.ncolp, st)
+                         : r2c_any(p, src, g.S, p.Sf, ncol, b.Yh, nullptr, 0, st);
+    if (e != cudaSuccess) return e;
+    e = b.cg ? cgemm_adjoint(b.cg, ncol, st) : contract_adj_all(p, g, b.Wf, b.Yh, b.Xh, ncol, st);
+    if (e != cudaSuccess) return e;
+    TabVolDst dst{fr, colf, col0, g.N, g.S, p.B};
+    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 // one item per thread (no grid-stride tail), one flux partial per block

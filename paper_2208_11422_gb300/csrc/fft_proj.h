@@ -43,9 +43,10 @@ struct FrameCols {
 };
 
 // picks F (or uses force_F if non-zero) by a bandwidth / arithmetic cost model
-// for `frames` frames; false if no plan fits (> 64 tiles, spectra too large,
-// or more than 256 phases)
-bool fft_plan_for(const Geo& g, FftPlan* p, int force_F = 0, int frames = 1);
+// for `frames` frames, with the contraction on the CUDA cores (FP32) or the
+// tensor cores (split_bf16); false if no plan fits (> 64 tiles, spectra too
+// large, or more than 256 phases)
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F = 0, int frames = 1, bool split_bf16 = false);
 
 // half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad]) into b.Wf or b.Wp
 cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const FftBuffers& b,
@@ -65,6 +66,23 @@ cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int
 // backprojection of rcm [S][Ly][Lx] into xcm [C][Ly][Lx] and / or a stack-order volume
 cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* rcm,
                          float* xcm, float* stack_out, cudaStream_t st, cudaEvent_t* ev);
+
+// Serving: the forward / backward projection of the columns col0 .. col0+ncol-1
+// of a frame table (frames of one PSF set, of different shapes); g supplies
+// the set's N, S, C. ncol <= b.ncolp. The forward writes each frame's ratio
+// (rcm, rimg); the backward reads each frame's rsrc (all ones where null) and
+// writes its xcm.
+cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
+                            const int* colf, int col0, int ncol, float eps, cudaStream_t st);
+cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
+                             const int* colf, int col0, int ncol, cudaStream_t st);
+// exact backprojection of one frame at the *n voxels of list (device count);
+// rimg == null backprojects an all-ones image
+cudaError_t launch_exact_bwd_dev(const int* list, const int* n, const float* rimg, const float* psf,
+                                 const Geo& g, float* xcm, cudaStream_t st);
+// list <- indices e < n with !(x[e] >= frac * max(0, max x)), *count <- their number
+cudaError_t launch_low_list(const float* x, int64_t n, float frac, unsigned* mx, int* list, int* count,
+                            cudaStream_t st);
 
 cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st);
 cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cudaStream_t st);

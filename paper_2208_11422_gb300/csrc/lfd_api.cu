@@ -62,13 +62,20 @@ bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why) {
     return true;
 }
 
+std::vector<double> dct_table(int n, int Z) {
+    // C_k(x; Z) = c(k, Z) cos((2x+1) pi k / (2Z)), c = sqrt(1/Z) for k = 0, sqrt(2/Z) otherwise
+    std::vector<double> t((size_t)n * Z);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        const double ck = k == 0 ? std::sqrt(1.0 / Z) : std::sqrt(2.0 / Z);
+        for (int x = 0; x < Z; ++x) t[(size_t)k * Z + x] = ck * std::cos((2.0 * x + 1.0) * pi * k / (2.0 * Z));
+    }
+    return t;
+}
+
 }  // namespace lfd
 
 namespace {
-
-// FFT variant: voxels with H^T 1 below this fraction of the largest are
-// backprojected by direct summation (see lfd_create)
-constexpr float kLowSensitivity = 1e-3f;
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -201,16 +208,6 @@ void free_all(lfd_ctx* ctx) {
     ctx->fft = nullptr;
 }
 
-std::vector<double> dct_table(int n, int Z) {
-    // C_k(x; Z) = c(k, Z) cos((2x+1) pi k / (2Z)), c = sqrt(1/Z) for k = 0, sqrt(2/Z) otherwise
-    std::vector<double> t((size_t)n * Z);
-    const double pi = 3.14159265358979323846;
-    for (int k = 0; k < n; ++k) {
-        const double ck = k == 0 ? std::sqrt(1.0 / Z) : std::sqrt(2.0 / Z);
-        for (int x = 0; x < Z; ++x) t[(size_t)k * Z + x] = ck * std::cos((2.0 * x + 1.0) * pi * k / (2.0 * Z));
-    }
-    return t;
-}
 
 }  // namespace
 
@@ -277,6 +274,7 @@ const char* lfd_status_string(lfd_status s) {
         case LFD_EBUSY: return "LFD_EBUSY";
         case LFD_EINTERNAL: return "LFD_EINTERNAL";
         case LFD_EUNSUPPORTED: return "LFD_EUNSUPPORTED";
+        case LFD_ECANCELED: return "LFD_ECANCELED";
     }
     return "unknown";
 }
@@ -360,7 +358,8 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     const bool fft = ctx->opt.variant == LFD_FFT;
     FftPlan fplan{};
     if (fft) {
-        if (!fft_plan_for(g, &fplan, ctx->opt.fft_size, ctx->opt.max_frames)) {
+        if (!fft_plan_for(g, &fplan, ctx->opt.fft_size, ctx->opt.max_frames,
+                          ctx->opt.precision == LFD_BF16X3)) {
             ctx->err = "no FFT tiling fits this geometry (at most 64 tiles, Nnum <= 15)";
             return bail(LFD_EUNSUPPORTED);
         }

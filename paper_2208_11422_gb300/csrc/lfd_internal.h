@@ -47,6 +47,14 @@ struct Geo {
 
 bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why);
 
+// FFT variant: voxels with H^T 1 below this fraction of the frame's largest are
+// backprojected by direct summation; the transforms' absolute error floor
+// (about 1e-7 of a tile's largest value) would dominate their update
+constexpr float kLowSensitivity = 1e-3f;
+
+// orthonormal DCT-II basis rows C_k(x; Z), k < n, x < Z (Eqs. 2-4), FP64, [n][Z]
+std::vector<double> dct_table(int n, int Z);
+
 // ------------------------------------------------------------ device buffers --
 struct DevBuf {
     void* p = nullptr;

@@ -17,7 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblfd.so")
 
 LFD_OK, LFD_EINVAL, LFD_ENOMEM, LFD_ECUDA, LFD_ENOTREADY, LFD_ETIMEDOUT, LFD_EBUSY, \
-    LFD_EINTERNAL, LFD_EUNSUPPORTED = range(9)
+    LFD_EINTERNAL, LFD_EUNSUPPORTED, LFD_ECANCELED = range(10)
 LFD_FP32, LFD_TF32, LFD_BF16, LFD_BF16X3 = range(4)
 PRECISIONS = {"fp32": LFD_FP32, "bf16": LFD_BF16, "bf16x3": LFD_BF16X3}
 LFD_DIRECT, LFD_FFT = 0, 1
@@ -46,6 +46,48 @@ class lfd_options(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("fft_size", ctypes.c_int),
     ]
+
+
+class lfd_server_options(ctypes.Structure):
+    _fields_ = [
+        ("opt", lfd_options),
+        ("arena_bytes", ctypes.c_int64),
+        ("max_frames_per_set", ctypes.c_int),
+        ("max_cols", ctypes.c_int),
+        ("max_queue", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+    ]
+
+
+class lfd_request(ctypes.Structure):
+    _fields_ = [
+        ("set_id", ctypes.c_int),
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("y", ctypes.c_void_p),
+        ("v_out", ctypes.c_void_p),
+        ("max_iter", ctypes.c_int),
+        ("stop_at_predicted", ctypes.c_int),
+        ("entropy_hist", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class lfd_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iters_done", ctypes.c_int),
+        ("iters_run", ctypes.c_int),
+        ("predicted", ctypes.c_int),
+        ("queue_us", ctypes.c_int64),
+        ("latency_us", ctypes.c_int64),
+    ]
+
+
+class lfd_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "admitted", "completed", "rejected", "cancelled", "frame_iterations", "ticks",
+        "columns", "arena_bytes", "arena_peak_bytes", "resident_bytes")] + [
+        ("queued", ctypes.c_int), ("in_flight", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -78,6 +120,15 @@ _SIGS = {
     "lfd_get_fft_plan": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
     "lfd_launch_count": (ctypes.c_uint64, []),
+    "lfd_server_default_options": (None, [ctypes.POINTER(lfd_server_options)]),
+    "lfd_server_create": (_I, [ctypes.POINTER(lfd_server_options), ctypes.POINTER(_VP)]),
+    "lfd_server_add_psf": (_I, [_VP, _VP, _I, _I, _I, _I, _I, ctypes.POINTER(_I)]),
+    "lfd_submit": (_I, [_VP, ctypes.POINTER(lfd_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "lfd_poll": (_I, [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(lfd_result)]),
+    "lfd_cancel": (_I, [_VP, ctypes.c_uint64]),
+    "lfd_server_stats_get": (_I, [_VP, ctypes.POINTER(lfd_server_stats)]),
+    "lfd_server_last_error": (ctypes.c_char_p, [_VP]),
+    "lfd_server_destroy": (None, [_VP]),
     "lfd_set_profiling": (_I, [_VP, _I]),
     "lfd_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
@@ -283,3 +334,100 @@ def lfd_stage_times(ctx):
     arr = (ctypes.c_float * 11)()
     _check(load().lfd_stage_times(ctx, arr, 11), ctx)
     return list(arr)
+
+
+# --------------------------------------------------------------- serving --
+def _check_srv(status: int, srv):
+    if status != LFD_OK:
+        lib = load()
+        msg = lib.lfd_server_last_error(srv).decode() if srv else ""
+        raise LfdError(status, "%s: %s" % (lib.lfd_status_string(status).decode(), msg))
+
+
+def lfd_server_default_options(precision: str = "bf16x3", **kw) -> lfd_server_options:
+    """Server options; ``opt_*`` keywords go to the embedded lfd_options
+    (e.g. opt_fft_size=32), the others to the server fields."""
+    o = lfd_server_options()
+    load().lfd_server_default_options(ctypes.byref(o))
+    o.opt.precision = PRECISIONS[precision]
+    for k, v in kw.items():
+        if k.startswith("opt_"):
+            setattr(o.opt, k[4:], v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def lfd_server_create(opt: lfd_server_options | None = None):
+    srv = _VP()
+    _check(load().lfd_server_create(ctypes.byref(opt) if opt is not None else None, ctypes.byref(srv)))
+    return srv
+
+
+def lfd_server_add_psf(srv, psf, P: int, nnum: int, nz: int, max_H: int, max_W: int) -> int:
+    sid = _I(0)
+    _check_srv(load().lfd_server_add_psf(srv, _ptr(psf), P, nnum, nz, max_H, max_W, ctypes.byref(sid)), srv)
+    return sid.value
+
+
+class Request:
+    """A submitted request; keeps its buffers alive until it is polled."""
+
+    def __init__(self, ticket, y, v_out, hist):
+        self.ticket, self.y, self.v_out, self.hist = ticket, y, v_out, hist
+
+
+def lfd_submit(srv, set_id: int, y, v_out, max_iter: int = 0, stop_at_predicted: bool = True,
+               entropy_hist: bool = True) -> Request:
+    """Queues y ([H][W]) for reconstruction into v_out ([Nz][H][W]); returns a
+    Request whose ``hist`` holds the entropy history once it is polled."""
+    shape = tuple(y.shape)
+    r = lfd_request()
+    r.set_id, r.H, r.W = set_id, shape[-2], shape[-1]
+    r.y, r.v_out = _ptr(y), _ptr(v_out)
+    r.max_iter = max_iter
+    r.stop_at_predicted = int(bool(stop_at_predicted))
+    hist = None
+    if entropy_hist:
+        n = max_iter if max_iter > 0 else 64
+        hist = (ctypes.c_double * n)()
+        if max_iter <= 0:
+            raise ValueError("entropy_hist needs an explicit max_iter")
+        r.entropy_hist = hist
+    t = ctypes.c_uint64(0)
+    _check_srv(load().lfd_submit(srv, ctypes.byref(r), ctypes.byref(t)), srv)
+    return Request(t.value, y, v_out, hist)
+
+
+def lfd_poll(srv, req, timeout_us: int = -1):
+    """None if not finished within the timeout, else a dict of the result."""
+    res = lfd_result()
+    ticket = req.ticket if isinstance(req, Request) else int(req)
+    st = load().lfd_poll(srv, ticket, timeout_us, ctypes.byref(res))
+    if st in (LFD_ENOTREADY, LFD_ETIMEDOUT):
+        return None
+    _check_srv(st, srv)
+    out = {"status": res.status, "iters_done": res.iters_done, "iters_run": res.iters_run,
+           "predicted": res.predicted, "queue_us": res.queue_us, "latency_us": res.latency_us}
+    if isinstance(req, Request) and req.hist is not None:
+        out["entropy"] = list(req.hist)
+    return out
+
+
+def lfd_cancel(srv, req) -> int:
+    ticket = req.ticket if isinstance(req, Request) else int(req)
+    return load().lfd_cancel(srv, ticket)
+
+
+def lfd_server_stats_get(srv) -> dict:
+    st = lfd_server_stats()
+    _check_srv(load().lfd_server_stats_get(srv, ctypes.byref(st)), srv)
+    return {n: getattr(st, n) for n, _ in lfd_server_stats._fields_}
+
+
+def lfd_server_last_error(srv) -> str:
+    return load().lfd_server_last_error(srv).decode()
+
+
+def lfd_server_destroy(srv):
+    load().lfd_server_destroy(srv)

@@ -257,3 +257,55 @@ def sample_indices(seed: int, count: int, dims) -> np.ndarray:
     """count random index tuples within dims (int32 [count][len(dims)])."""
     rng = np.random.default_rng(seed)
     return np.stack([rng.integers(0, d, count) for d in dims], axis=1).astype(np.int32)
+
+
+# ----------------------------------------------------------------- serving --
+SERVE_NNUM = (11, 13, 15)
+SERVE_NZ = (21, 31, 41, 51)
+SERVE_PSF_LENSLETS = 11
+SERVE_LENSLETS = (33, 121)     # lenslet grid per axis, uniform integers
+
+
+def serve_psf_set(j: int):
+    """PSF set j (1..4) of the serving workload: (Nnum, Nz) drawn with
+    default_rng(j), a PSF window 11 lenslets wide with the mid-size workload's
+    sigma(z) = 1 + 0.4 |z - z_c|, R(z) = ceil(|z - z_c| / 3), z_c = Nz // 2.
+    Returns (nnum, nz, P, psf)."""
+    rng = np.random.default_rng(j)
+    nnum = int(rng.choice(SERVE_NNUM))
+    nz = int(rng.choice(SERVE_NZ))
+    psf = psf_gaussian_spots(nnum, nz, SERVE_PSF_LENSLETS, nz // 2, 1.0, 0.4, 3)
+    return nnum, nz, SERVE_PSF_LENSLETS * nnum, psf
+
+
+@dataclass(frozen=True)
+class ServeRequest:
+    index: int
+    arrival_s: float   # Poisson arrivals
+    set_id: int        # 1..4
+    ly: int            # lenslet grid
+    lx: int
+    beads: int         # 50..5000
+    scale: float       # photons per unit signal, log-uniform [100, 5000]
+    seed: int
+
+
+def serve_requests(n: int, seed: int, rate_hz: float = 20.0, sets: int = 4):
+    """n requests of the serving workload: exponential inter-arrival times of
+    mean 1 / rate_hz, a PSF set uniform in 1..sets, lenslet grid uniform in
+    33..121 per axis, 50..5000 beads, photon scale log-uniform over [100, 5000]."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    set_id = rng.integers(1, sets + 1, n)
+    ly = rng.integers(SERVE_LENSLETS[0], SERVE_LENSLETS[1] + 1, n)
+    lx = rng.integers(SERVE_LENSLETS[0], SERVE_LENSLETS[1] + 1, n)
+    nb = rng.integers(50, 5001, n)
+    scale = np.exp(rng.uniform(math.log(100.0), math.log(5000.0), n))
+    return [ServeRequest(i, float(t[i]), int(set_id[i]), int(ly[i]), int(lx[i]), int(nb[i]),
+                         float(scale[i]), seed * 100003 + i) for i in range(n)]
+
+
+def serve_volume(req: ServeRequest, nnum: int, nz: int) -> np.ndarray:
+    """Bead volume [Nz][ly*Nnum][lx*Nnum] of a serving request (radius 2,
+    amplitudes U[0.3, 1]), float32."""
+    return beads(req.seed, nz, req.ly * nnum, req.lx * nnum, req.beads, 2.0, 0.3).astype(np.float32)

@@ -107,3 +107,61 @@ def test_predict_stop_matches_oracle():
         E = rng.integers(0, 4, n).astype(float).tolist()   # many ties on purpose
         assert lfd.lfd_predict_stop(E) == metric.predicted_iteration(E), E
     assert lfd.lfd_predict_stop([]) == 0
+
+
+STRUCTS = {
+    "lfd_options": ["precision", "eps", "dML_um", "XS", "l2_over_region", "fft_size"],
+    "lfd_server_options": ["opt", "arena_bytes", "max_frames_per_set", "max_iter"],
+    "lfd_request": ["set_id", "H", "y", "v_out", "max_iter", "entropy_hist"],
+    "lfd_result": ["status", "predicted", "queue_us", "latency_us"],
+    "lfd_server_stats": ["submitted", "columns", "resident_bytes", "queued", "in_flight"],
+}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof / offsetof of every ABI struct, from a C program compiled against
+    include/lfd.h, equal the ctypes layouts."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lfd.h"', "int main(void) {"]
+    for s, fields in STRUCTS.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f in fields:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for s, fields in STRUCTS.items():
+        cls = getattr(lfd, s)
+        assert int(out[s]) == ctypes.sizeof(cls), s
+        for f in fields:
+            assert int(out["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
+
+
+def test_server_rejects_bad_options_before_cuda(lib):
+    for kw in ({"max_cols": 8}, {"max_cols": 100}, {"max_frames_per_set": 0}, {"max_iter": 0},
+               {"max_queue": 0}, {"opt_fft_size": 48}):
+        o = lfd.lfd_server_default_options(**kw)
+        srv = ctypes.c_void_p()
+        assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL, kw
+        assert not srv.value
+    o = lfd.lfd_server_default_options(precision="bf16")   # split BF16 or FP32 only
+    srv = ctypes.c_void_p()
+    assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL
+
+
+def test_server_calls_reject_null_handles(lib):
+    r = lfd.lfd_request()
+    t = ctypes.c_uint64(0)
+    assert lib.lfd_submit(None, ctypes.byref(r), ctypes.byref(t)) == lfd.LFD_EINVAL
+    assert lib.lfd_poll(None, 1, 0, None) == lfd.LFD_EINVAL
+    assert lib.lfd_cancel(None, 1) == lfd.LFD_EINVAL
+    assert lib.lfd_server_add_psf(None, None, 3, 1, 1, 3, 3, None) == lfd.LFD_EINVAL
+    lib.lfd_server_destroy(None)
