@@ -241,8 +241,6 @@ NCU_TRAFFIC = {
         (4.090e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
         (3.740e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
-    ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
-        (0.4788e9 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
 
 

@@ -29,41 +29,68 @@
 namespace lfd {
 namespace {
 
-constexpr int kCPB = 4;  // channels per transform block
-
 __constant__ float2 c_tw[32];  // exp(-2 pi i k / 64), k < 32
 
 template <int F>
 struct FftSize {
     static constexpr int LOG = F == 64 ? 6 : 5;
-    static constexpr int H2 = F / 2 + 1;
+    static constexpr int HF = F / 2;           // lanes per channel in a transform warp
+    static constexpr int H2 = F / 2 + 1;       // half-spectrum columns
     static constexpr int BINS = F * H2;
+    static constexpr int CPW = 64 / F;         // channels per warp (lanes / HF)
+    static constexpr int R2C_WARPS = 8;        // per R2C block
+    static constexpr int R2C_CH = R2C_WARPS * CPW;
+    static constexpr int C2R_WARPS = 4;        // per C2R block
+    static constexpr int C2R_CH = C2R_WARPS * CPW;
 };
 
-__device__ __forceinline__ int bitrev(int i, int log) { return (int)(__brev((unsigned)i) >> (32 - log)); }
+__device__ __forceinline__ int brev_c(int i, int log) {
+    int r = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+        if (b < log) r |= ((i >> b) & 1) << (log - 1 - b);
+    return r;
+}
 
-// in-place radix-2 FFT of F points in shared memory by one warp; input must
-// already be in bit-reversed order. INV uses conjugate twiddles (no scaling).
-template <int F, bool INV>
-__device__ __forceinline__ void warp_fft(float2* a) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+
+// Radix-2 decimation-in-time FFT of N <= 64 points held in one thread's
+// registers: a[] in bit-reversed order on entry, natural order on exit. One
+// template instance per stage (LEN = 2, 4, ..., N) keeps every index a
+// compile-time constant, so a[] stays in registers and each twiddle
+// exp(-+2 pi i j / LEN) = c_tw[j * 64 / LEN] is a constant-bank operand; the
+// factors 1 and -+i are applied without a multiply. INV: conjugate twiddles
+// (no scaling).
+template <int N, int LEN, bool INV>
+__device__ __forceinline__ void fft_stage(float2 (&a)[N]) {
+    constexpr int HALF = LEN / 2;
 #pragma unroll
-    for (int st = 1; st <= FftSize<F>::LOG; ++st) {
-        const int half = 1 << (st - 1);
-        const int len = half << 1;
+    for (int g = 0; g < N / LEN; ++g) {
 #pragma unroll
-        for (int b = lane; b < F / 2; b += 32) {
-            const int j = b & (half - 1);
-            const int i0 = (b >> (st - 1)) * len + j, i1 = i0 + half;
-            float2 w = c_tw[j * (64 / len)];
-            if (INV) w.y = -w.y;
-            const float2 u = a[i0], v = a[i1];
-            const float2 t = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
-            a[i0] = make_float2(u.x + t.x, u.y + t.y);
-            a[i1] = make_float2(u.x - t.x, u.y - t.y);
+        for (int j = 0; j < HALF; ++j) {
+            const int i = g * LEN, tw = j * (64 / LEN);
+            const float2 u = a[i + j], v = a[i + j + HALF];
+            float2 t;
+            if (tw == 0) {
+                t = v;
+            } else if (tw == 16) {  // exp(-i pi / 2) = -i (forward), +i (inverse)
+                t = INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+            } else {
+                const float2 w = c_tw[tw];
+                const float wy = INV ? -w.y : w.y;
+                t = make_float2(fmaf(v.x, w.x, -v.y * wy), fmaf(v.x, wy, v.y * w.x));
+            }
+            a[i + j] = cadd(u, t);
+            a[i + j + HALF] = csub(u, t);
         }
-        __syncwarp();
     }
+    if constexpr (LEN < N) fft_stage<N, 2 * LEN, INV>(a);
+}
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg(float2 (&a)[N]) {
+    fft_stage<N, 2, INV>(a);
 }
 
 // A source or destination is bound to one column (one tile of one frame)
@@ -131,60 +158,131 @@ struct TapSrc {
 };
 
 // spectrum outputs of the R2C transform: complex64, or BF16 planes
-// (real hi, real lo, imag hi, imag lo; x = hi + lo) for the tensor cores
+// (real hi, real lo, imag hi, imag lo; x = hi + lo) for the tensor cores.
+// put8 writes channels c0 .. c0+7 of one bin and column that lie below the
+// row length ld (c0 and ld are multiples of 4, so 4 or 8 of them) with
+// 16-byte stores (8-byte for a group of 4 in the planes).
 struct OutC64 {
     float2* p;
     int ntile, ld;
-    __device__ void operator()(int bin, int tile, int c, float2 v) const {
-        p[((int64_t)bin * ntile + tile) * ld + c] = v;
+    __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
+        float4* q = reinterpret_cast<float4*>(p + ((int64_t)bin * ntile + tile) * ld + c0);
+        const int n4 = ld - c0 >= 8 ? 4 : 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < n4) q[k] = make_float4(v[2 * k].x, v[2 * k].y, v[2 * k + 1].x, v[2 * k + 1].y);
     }
 };
 struct OutPlanes {
     __nv_bfloat16* p[4];
     int ntile, ld;
-    __device__ void operator()(int bin, int tile, int c, float2 v) const {
-        const int64_t o = ((int64_t)bin * ntile + tile) * ld + c;
-        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-        p[0][o] = rh;
-        p[1][o] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
-        p[2][o] = ih;
-        p[3][o] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+    __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
+        const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
+        __align__(16) __nv_bfloat16 h[4][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const __nv_bfloat16 rh = __float2bfloat16_rn(v[k].x), ih = __float2bfloat16_rn(v[k].y);
+            h[0][k] = rh;
+            h[1][k] = __float2bfloat16_rn(v[k].x - __bfloat162float(rh));
+            h[2][k] = ih;
+            h[3][k] = __float2bfloat16_rn(v[k].y - __bfloat162float(ih));
+        }
+        if (ld - c0 >= 8) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(p[q] + o) = *reinterpret_cast<const uint2*>(h[q]);
+        }
     }
 };
 
-// R2C 2-D transform of kCPB channels' patches of one tile; bin = fy*(F/2+1)+fx,
-// out(bin, tile, c, value) for every c < ldc (zeros for c >= nch).
+// R2C 2-D transform of the F x F patches of FftSize<F>::R2C_CH channels of
+// one tile; bin = fy*(F/2+1) + fx, out.put8 for every channel below ldc (zeros
+// for channels >= nch). Each channel belongs to F/2 lanes of one warp:
+//   load:    the patch goes through shared memory (row stride F+1): lanes
+//            along x, so the global loads are coalesced, all issued before
+//            the first store;
+//   rows:    lane l transforms rows l and l + F/2 packed as one complex row
+//            (z = p_l + i p_{l+F/2}) and separates the two half spectra;
+//   columns: lane l (1 <= l < F/2) transforms column fx = l; lane 0 packs the
+//            real columns 0 and F/2 into one complex column.
+// The half spectra stay in shared memory [channel][fy or row][fx], in place.
+// Grid: x = channel group (fastest, so blocks running together fill adjacent
+// parts of the same output rows), y = column.
 template <int F, class Src, class Out>
-__global__ void __launch_bounds__(256) k_fft_r2c(Src src, int nch, int ldc, Out out) {
-    constexpr int H2 = FftSize<F>::H2, LOG = FftSize<F>::LOG;
+__global__ void __launch_bounds__(32 * FftSize<F>::R2C_WARPS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
+    using Z = FftSize<F>;
+    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH;
     extern __shared__ float2 sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* spec = sm;                               // [kCPB][F][H2]
-    float2* scr = sm + kCPB * F * H2 + warp * F;     // per-warp [F]
-    const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    const int sub = lane / HF, l = lane % HF;
+    const int ch = warp * Z::CPW + sub;            // channel within the block
+    const int tile = blockIdx.y, c0 = blockIdx.x * CH, c = c0 + ch;
     const auto view = src.bind(tile);
-    for (int job = warp; job < kCPB * F; job += 8) {  // rows
-        const int ch = job / F, r = job % F, c = c0 + ch;
-        for (int x = lane; x < F; x += 32)
-            scr[bitrev(x, LOG)] = make_float2(c < nch ? view(c, r, x) : 0.f, 0.f);
+    float2* R = sm + (size_t)ch * Z::BINS;          // [F][H2]
+    {
+        constexpr int PS = F + 1;
+        float* Pm = reinterpret_cast<float*>(R);    // [F][PS] real patch
+        const bool on = c < nch;
+        {
+            float t[2 * F];
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                t[2 * r] = on ? view(c, r, l) : 0.f;
+                t[2 * r + 1] = on ? view(c, r, l + HF) : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                Pm[r * PS + l] = t[2 * r];
+                Pm[r * PS + l + HF] = t[2 * r + 1];
+            }
+        }
         __syncwarp();
-        warp_fft<F, false>(scr);
-        for (int k = lane; k < H2; k += 32) spec[(ch * F + r) * H2 + k] = scr[k];
-        __syncwarp();
+        float2 a[F];
+#pragma unroll
+        for (int x = 0; x < F; ++x) a[brev_c(x, LOG)] = make_float2(Pm[l * PS + x], Pm[(l + HF) * PS + x]);
+        __syncwarp();  // the half spectra below overwrite the patch
+        fft_reg<F, false>(a);
+#pragma unroll
+        for (int k = 0; k <= HF; ++k) {
+            const float2 z = a[k], m = a[(F - k) & (F - 1)];
+            R[l * H2 + k] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
+            R[(l + HF) * H2 + k] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+        }
+    }
+    __syncwarp();
+    {
+        float2 a[F];
+        if (l == 0) {
+#pragma unroll
+            for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = make_float2(R[r * H2].x, R[r * H2 + HF].x);
+        } else {
+#pragma unroll
+            for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = R[r * H2 + l];
+        }
+        fft_reg<F, false>(a);
+        if (l == 0) {
+#pragma unroll
+            for (int fy = 0; fy < F; ++fy) {
+                const float2 z = a[fy], m = a[(F - fy) & (F - 1)];
+                R[fy * H2] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
+                R[fy * H2 + HF] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+            }
+        } else {
+#pragma unroll
+            for (int fy = 0; fy < F; ++fy) R[fy * H2 + l] = a[fy];
+        }
     }
     __syncthreads();
-    for (int job = warp; job < kCPB * H2; job += 8) {  // columns
-        const int ch = job / H2, k = job % H2;
-        for (int r = lane; r < F; r += 32) scr[bitrev(r, LOG)] = spec[(ch * F + r) * H2 + k];
-        __syncwarp();
-        warp_fft<F, false>(scr);
-        for (int r = lane; r < F; r += 32) spec[(ch * F + r) * H2 + k] = scr[r];
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
-        const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
-        if (c < ldc) out(bin, tile, c, c < nch ? spec[ch * F * H2 + bin] : make_float2(0.f, 0.f));
+    // every bin of 8 consecutive channels at a time
+    for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
+        const int bin = e % Z::BINS, g = e / Z::BINS;
+        if (c0 + 8 * g >= ldc) continue;
+        float2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = sm[(size_t)(8 * g + k) * Z::BINS + bin];
+        out.put8(bin, tile, c0 + 8 * g, v);
     }
 }
 
@@ -282,52 +380,112 @@ struct TabVolDst {
     }
 };
 
-// C2R 2-D transform of kCPB channels of one tile; the rows / columns
-// [off, off + B) of the real result, times `scale`, go to dst.
+// C2R 2-D transform of FftSize<F>::CH channels of one tile: rows and columns
+// [off, off + B) of the real result, times `scale`, go to dst. Each channel
+// belongs to F/2 lanes of one warp:
+//   columns: lane l (1 <= l < F/2) inverse-transforms column fx = l; lane 0
+//            packs columns 0 and F/2 (whose inverses are real) into one;
+//   rows:    lane i < B/2 inverse-transforms output rows off+i and
+//            off+i+B/2 packed as one complex row (each row's spectrum extended
+//            by conjugate symmetry), then the outputs go through shared memory
+//            so that dst sees consecutive j across lanes.
+// Grid: x = column, y = channel group.
 template <int F, class Dst>
-__global__ void __launch_bounds__(256) k_fft_c2r(const float2* __restrict__ in, int nch, int ldc,
-                                                 int ntile, int off, int B, float scale, Dst dst) {
-    constexpr int H2 = FftSize<F>::H2, LOG = FftSize<F>::LOG;
+__global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const float2* __restrict__ in, int nch,
+                                                                    int ldc, int ntile, int off, int B,
+                                                                    float scale, Dst dst) {
+    using Z = FftSize<F>;
+    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::C2R_CH;
     extern __shared__ float2 sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* spec = sm;
-    float2* scr = sm + kCPB * F * H2 + warp * F;
-    const int tile = blockIdx.x, c0 = blockIdx.y * kCPB;
+    const int sub = lane / HF, l = lane % HF;
+    const int ch = warp * Z::CPW + sub;
+    const int tile = blockIdx.x, c0 = blockIdx.y * CH, c = c0 + ch;
     const auto view = dst.bind(tile);
-    for (int e = threadIdx.x; e < FftSize<F>::BINS * kCPB; e += blockDim.x) {
-        const int ch = e % kCPB, bin = e / kCPB, c = c0 + ch;
-        spec[ch * F * H2 + bin] =
-            c < nch ? in[((int64_t)bin * ntile + tile) * ldc + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int job = warp; job < kCPB * H2; job += 8) {  // columns: fy -> y
-        const int ch = job / H2, k = job % H2;
-        for (int r = lane; r < F; r += 32) scr[bitrev(r, LOG)] = spec[(ch * F + r) * H2 + k];
-        __syncwarp();
-        warp_fft<F, true>(scr);
-        for (int r = lane; r < F; r += 32) spec[(ch * F + r) * H2 + k] = scr[r];
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int job = warp; job < kCPB * B; job += 8) {  // rows y in [off, off+B): fx -> x
-        const int ch = job / B, i = job % B, y = off + i, c = c0 + ch;
-        const float2* row = spec + (ch * F + y) * H2;
-        for (int x = lane; x < F; x += 32) {
-            float2 v;
-            if (x < H2) {
-                v = row[x];
-            } else {  // a real row has a conjugate-symmetric spectrum
-                v = row[F - x];
-                v.y = -v.y;
-            }
-            scr[bitrev(x, LOG)] = v;
+    // spectra of 4 consecutive channels per bin, into [channel][bin]
+    for (int e = threadIdx.x; e < Z::BINS * (CH / 4); e += blockDim.x) {
+        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + 4 * g;
+        float2 v[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                       make_float2(0.f, 0.f)};
+        if (cg < ldc) {
+            const float4* q = reinterpret_cast<const float4*>(in + ((int64_t)bin * ntile + tile) * ldc + cg);
+            const float4 w0 = q[0], w1 = q[1];
+            v[0] = make_float2(w0.x, w0.y);
+            v[1] = make_float2(w0.z, w0.w);
+            v[2] = make_float2(w1.x, w1.y);
+            v[3] = make_float2(w1.z, w1.w);
         }
-        __syncwarp();
-        warp_fft<F, true>(scr);
-        if (c < nch)
-            for (int j = lane; j < B; j += 32) view(c, i, j, scr[off + j].x * scale);
-        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sm[(size_t)(4 * g + k) * Z::BINS + bin] = v[k];
     }
+    __syncthreads();
+    float2* R = sm + (size_t)ch * Z::BINS;  // [F][H2]
+    {
+        float2 a[F];
+        if (l == 0) {
+#pragma unroll
+            for (int fy = 0; fy < F; ++fy) {
+                const float2 x0 = R[fy * H2], xh = R[fy * H2 + HF];
+                a[brev_c(fy, LOG)] = make_float2(x0.x - xh.y, x0.y + xh.x);
+            }
+        } else {
+#pragma unroll
+            for (int fy = 0; fy < F; ++fy) a[brev_c(fy, LOG)] = R[fy * H2 + l];
+        }
+        fft_reg<F, true>(a);
+        if (l == 0) {
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                R[r * H2] = make_float2(a[r].x, 0.f);
+                R[r * H2 + HF] = make_float2(a[r].y, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < F; ++r) R[r * H2 + l] = a[r];
+        }
+    }
+    __syncwarp();
+    const int hb = B >> 1, ob = B + 1;  // row pairs; staged row stride
+    float* O = reinterpret_cast<float*>(R);
+    {
+        float2 a[F];
+        if (l < hb) {
+            const float2* r1 = R + (off + l) * H2;
+            const float2* r2 = R + (off + l + hb) * H2;
+#pragma unroll
+            for (int k = 0; k < F; ++k) {
+                float2 t1, t2;
+                if (k <= HF) {
+                    t1 = r1[k];
+                    t2 = r2[k];
+                } else {
+                    t1 = r1[F - k];
+                    t2 = r2[F - k];
+                    t1.y = -t1.y;
+                    t2.y = -t2.y;
+                }
+                a[brev_c(k, LOG)] = make_float2(t1.x - t2.y, t1.y + t2.x);
+            }
+            fft_reg<F, true>(a);
+        }
+        __syncwarp();  // every lane has read its rows before R is reused for the outputs
+        if (l < hb) {
+#pragma unroll
+            for (int x = 0; x < F; ++x) {
+                const int j = x - off;
+                if (j >= 0 && j < B) {
+                    O[l * ob + j] = a[x].x * scale;
+                    O[(l + hb) * ob + j] = a[x].y * scale;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (c < nch)
+        for (int e = l; e < B * B; e += HF) {
+            const int i = e / B, j = e % B;
+            view(c, i, j, O[i * ob + j]);
+        }
 }
 
 // forward contraction: Yh[bin][t][s] = sum_c Wf[bin][s][c] Xh[bin][t][c].
@@ -508,17 +666,25 @@ __device__ float exact_bwd_voxel(int64_t idx, const float* __restrict__ rimg,
     const float* K = psf + (((int64_t)z * g.N + ty) * g.N + tx) * g.P * g.P;
     const int mi0 = max(0, c0 - ip), mi1 = min(g.P, g.H + c0 - ip);
     const int mj0 = max(0, c0 - jp), mj1 = min(g.P, g.W + c0 - jp);
+    // lanes along the window's columns; a window narrower than 32 columns
+    // takes 32 / width rows per step
+    const int ncl = max(0, mj1 - mj0);
+    const int rps = ncl >= 32 || ncl == 0 ? 1 : 32 / ncl;   // rows per step
+    const int dr = ncl >= 32 ? 0 : lane / max(ncl, 1), cc = ncl >= 32 ? lane : lane % max(ncl, 1);
+    const bool act = ncl >= 32 || lane < rps * ncl;
+    const float* rr = rimg ? rimg + (int64_t)(ip - c0) * g.W + (jp - c0) : nullptr;
     float acc = 0.f;
-    for (int mi = mi0; mi < mi1; ++mi) {
-        const float* kk = K + (int64_t)mi * g.P;
-        float row = 0.f;
-        if (rimg) {
-            const float* rr = rimg + (int64_t)(ip + mi - c0) * g.W + (jp - c0);
-            for (int mj = mj0 + lane; mj < mj1; mj += 32) row = fmaf(rr[mj], kk[mj], row);
-        } else {
-            for (int mj = mj0 + lane; mj < mj1; mj += 32) row += kk[mj];
+    if (act) {
+#pragma unroll 2
+        for (int mi = mi0 + dr; mi < mi1; mi += rps) {
+            const float* kk = K + (int64_t)mi * g.P;
+            if (rr) {
+                const float* rw = rr + (int64_t)mi * g.W;
+                for (int mj = mj0 + cc; mj < mj1; mj += 32) acc = fmaf(rw[mj], kk[mj], acc);
+            } else {
+                for (int mj = mj0 + cc; mj < mj1; mj += 32) acc += kk[mj];
+            }
         }
-        acc += row;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
@@ -697,8 +863,8 @@ inline int grid_for(int64_t n, int cap = 152 * 16) {
 }
 
 template <int F>
-size_t fft_smem() {
-    return sizeof(float2) * ((size_t)kCPB * F * FftSize<F>::H2 + 8 * F);
+size_t fft_smem(bool r2c) {
+    return sizeof(float2) * (size_t)(r2c ? FftSize<F>::R2C_CH : FftSize<F>::C2R_CH) * FftSize<F>::BINS;
 }
 
 bool g_tw_ready[64] = {};
@@ -719,11 +885,11 @@ cudaError_t upload_twiddles() {
 
 template <int F, class Src, class Out>
 cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, Out out, cudaStream_t st) {
-    const size_t smem = fft_smem<F>();
+    const size_t smem = fft_smem<F>(true);
     cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)ntile, (unsigned)((ldc + kCPB - 1) / kCPB));
-    k_fft_r2c<F, Src, Out><<<grid, 256, smem, st>>>(src, nch, ldc, out);
+    dim3 grid((unsigned)((ldc + FftSize<F>::R2C_CH - 1) / FftSize<F>::R2C_CH), (unsigned)ntile);
+    k_fft_r2c<F, Src, Out><<<grid, 32 * FftSize<F>::R2C_WARPS, smem, st>>>(src, nch, ldc, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -743,11 +909,11 @@ cudaError_t r2c_any(const FftPlan& p, Src src, int nch, int ldc, int ntile, floa
 template <int F, class Dst>
 cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
                     cudaStream_t st) {
-    const size_t smem = fft_smem<F>();
+    const size_t smem = fft_smem<F>(false);
     cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)ntile, (unsigned)((nch + kCPB - 1) / kCPB));
-    k_fft_c2r<F, Dst><<<grid, 256, smem, st>>>(in, nch, ldc, ntile, off, B, 1.0f / (F * F), dst);
+    dim3 grid((unsigned)ntile, (unsigned)((nch + FftSize<F>::C2R_CH - 1) / FftSize<F>::C2R_CH));
+    k_fft_c2r<F, Dst><<<grid, 32 * FftSize<F>::C2R_WARPS, smem, st>>>(in, nch, ldc, ntile, off, B, 1.0f / (F * F), dst);
     count_launch();
     return cudaGetLastError();
 }
