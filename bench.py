@@ -258,7 +258,9 @@ def fft_kernel_work(g, plan, prec):
                                     "kernel": "forward contraction"},
             "backward_contraction": {"bytes": ws + ys + xs, "flops": flops, "slot": 6,
                                      "kernel": "backward contraction"},
-            "volume_c2r": {"bytes": xs + vol, "slot": 9, "kernel": "backward volume transform"}}, \
+            "volume_c2r": {"bytes": xs + vol, "slot": 9, "kernel": "backward volume transform"},
+            # fused update: read v, H^T r, 1 / H^T 1, write v (4 B each per voxel), write the MIP
+            "update": {"bytes": 4.0 * vol + 4.0 * g.H * g.W, "slot": 3, "kernel": "fused update + MIP + flux"}}, \
         {"F": F, "bins": bins, "tiles": nt}
 
 

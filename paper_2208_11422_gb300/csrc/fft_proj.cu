@@ -784,7 +784,10 @@ __global__ void k_inv_cm(const float* __restrict__ x, int64_t n, float* __restri
 
 // RL update on channel-major volumes; thread per (phase t, lenslet), walking
 // the depths: v_new = max(0, v * x * inv) (NaN -> 0, 0 where H^T 1 = 0), the
-// z-maximum of v_new for its pixel, and the FP64 flux sum(v * x) where H^T 1 > 0.
+// z-maximum of v_new for its pixel, and the flux sum(v * x) where H^T 1 > 0
+// (compensated FP32 over the thread's depths, FP64 across threads). The loads
+// of 16 depths are issued together.
+constexpr int kUpdBatch = 16;
 __global__ void __launch_bounds__(256) k_update_cm(const float* __restrict__ vin, float* __restrict__ vout,
                                                    const float* __restrict__ x, const float* __restrict__ inv,
                                                    Geo g, float* __restrict__ mip,
@@ -804,47 +807,40 @@ __global__ void __launch_bounds__(256) k_update_cm(const float* __restrict__ vin
          e += (int64_t)gridDim.x * blockDim.x) {
         const int t = (int)(e / L2);
         const int64_t l = e % L2;
-        float mx = 0.f;
+        float mx = 0.f, fs = 0.f, fc = 0.f;
         const int64_t zs = (int64_t)g.S * L2;  // stride between depths
         const int64_t o0 = (int64_t)t * L2 + l;
+        auto step = [&](float ivq, float voq, float xq, int64_t o) {
+            float vn = 0.f;
+            if (ivq > 0.f) {
+                const float vx = voq * xq;
+                vn = vx * ivq;
+                kahan_add(fs, fc, vx);
+            }
+            vn = vn > 0.f ? vn : 0.f;
+            vout[o] = vn;
+            mx = fmaxf(mx, vn);
+        };
         int z = 0;
-        for (; z + 4 <= g.Nz; z += 4) {  // four depths' loads in flight
-            float iv[4], vo[4], xx[4];
+        for (; z + kUpdBatch <= g.Nz; z += kUpdBatch) {
+            float iv[kUpdBatch], vo[kUpdBatch], xx[kUpdBatch];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < kUpdBatch; ++q) {
                 const int64_t o = o0 + (z + q) * zs;
                 iv[q] = inv[o];
                 vo[q] = vin[o];
                 xx[q] = x[o];
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float vn = 0.f;
-                if (iv[q] > 0.f) {
-                    const float vx = vo[q] * xx[q];
-                    vn = vx * iv[q];
-                    flux += (double)vx;
-                }
-                vn = vn > 0.f ? vn : 0.f;
-                vout[o0 + (z + q) * zs] = vn;
-                mx = fmaxf(mx, vn);
-            }
+            for (int q = 0; q < kUpdBatch; ++q) step(iv[q], vo[q], xx[q], o0 + (z + q) * zs);
         }
         for (; z < g.Nz; ++z) {
             const int64_t o = o0 + z * zs;
-            const float iv = inv[o], vo = vin[o];
-            float vn = 0.f;
-            if (iv > 0.f) {
-                const float vx = vo * x[o];
-                vn = vx * iv;
-                flux += (double)vx;
-            }
-            vn = vn > 0.f ? vn : 0.f;
-            vout[o] = vn;
-            mx = fmaxf(mx, vn);
+            step(inv[o], vin[o], x[o], o);
         }
         const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
         mip[((int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N] = mx;
+        flux += (double)fs - (double)fc;
     }
     for (int o = 16; o > 0; o >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = flux;

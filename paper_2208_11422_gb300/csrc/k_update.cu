@@ -1,4 +1,4 @@
-// Fused RL update (multiplicative step, clamp, z-MIP, FP64 flux) and the
+// Fused RL update (multiplicative step, clamp, z-MIP, flux) and the
 // DCT-entropy metric of Section 2.2.
 #include "lfd_internal.h"
 
@@ -28,7 +28,9 @@ __device__ double block_sum(double x, double* red) {
 //   v_new = max(0, v_new) with NaN -> 0
 // and, on the fly, the z-maximum of v_new for pixel (Iy*N + ty, Ix*N + tx)
 // and this lenslet's share of the flux sum(H^T1 * v_new) = sum(v * x) taken
-// where H^T 1 > 0, accumulated in FP64.
+// where H^T 1 > 0: compensated FP32 over a thread's depths, FP64 across
+// threads (FP64 arithmetic per voxel would bound the kernel on the GB300's
+// FP64 rate).
 __global__ void __launch_bounds__(256) k_update(
     const float* __restrict__ vin, float* __restrict__ vout, __nv_bfloat16* __restrict__ hi,
     __nv_bfloat16* __restrict__ lo, const float* __restrict__ parts, int nsplit,
@@ -43,6 +45,7 @@ __global__ void __launch_bounds__(256) k_update(
     double flux = 0.0;
     for (int t = threadIdx.x; t < g.S; t += blockDim.x) {
         float mx = 0.f;
+        float fs = 0.f, fc = 0.f;  // this thread's depths: compensated FP32 sum
 #pragma unroll 4
         for (int z = 0; z < g.Nz; ++z) {
             const int c = z * g.S + t;
@@ -54,7 +57,7 @@ __global__ void __launch_bounds__(256) k_update(
             if (iv > 0.f) {
                 const float vx = vo * x;
                 vn = vx * iv;
-                flux += (double)vx;
+                kahan_add(fs, fc, vx);
             }
             vn = vn > 0.f ? vn : 0.f;  // clamp; a NaN compares false and becomes 0
             vout[grow + c] = vn;
@@ -67,6 +70,7 @@ __global__ void __launch_bounds__(256) k_update(
         }
         const int ty = t / g.N, tx = t % g.N;
         mip[((int64_t)Iy * g.N + ty) * g.W + (int64_t)Ix * g.N + tx] = mx;
+        flux += (double)fs - (double)fc;
     }
     const double f = block_sum(flux, red);
     if (threadIdx.x == 0) flux_part[l] = f;

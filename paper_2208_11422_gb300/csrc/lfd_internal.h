@@ -147,6 +147,15 @@ struct lfd_ctx {
 namespace lfd {
 
 extern std::atomic<uint64_t> g_launches;
+// compensated (Kahan) FP32 accumulation: s + c carries the sum of the added
+// terms with about twice FP32's precision (the flux partial of one thread)
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // --------------------------------------------------------- kernel launchers --
