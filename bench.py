@@ -244,6 +244,24 @@ NCU_TRAFFIC = {
 }
 
 
+def direct_tensor_roofline(g, prec, st_ms):
+    """Tensor-pipe fraction of the direct (implicit GEMM) projections: the
+    algorithmic flops 2*H*W*Nz*P^2 per projection, and the executed ones (the
+    dense tap union (k+2)^2/k^2, three products per term in split BF16),
+    against the sustained BF16 peak (the projections run inside a long step)."""
+    peaks, src = measured_peaks()
+    k = g.psf_lenslets
+    fl = algorithmic_flops_per_projection(g)
+    ex = fl * ((k + 2) / k) ** 2 * (3 if prec == "bf16x3" else 1)
+    ms = max(st_ms[0], st_ms[2])
+    peak = peaks["bf16_tflops_sustained"]
+    return {"kernel": "forward projection" if st_ms[0] >= st_ms[2] else "backprojection",
+            "algorithmic_TFLOPs": fl / (ms / 1e3) / 1e12, "executed_TFLOPs": ex / (ms / 1e3) / 1e12,
+            "peak": peak, "frac_algorithmic": fl / (ms / 1e3) / 1e12 / peak,
+            "frac_executed": ex / (ms / 1e3) / 1e12 / peak,
+            "peak_source": "bf16_tflops_sustained (%s)" % src}
+
+
 def fft_kernel_work(g, plan, prec):
     """Algorithmic bytes (and contraction flops) per launch of the FFT
     variant's four large kernels. Spectra are 8 bytes per complex value (BF16
@@ -417,6 +435,8 @@ def run_lfd(args, rank, world, local):
                 "value": it_s, "unit": "RL iterations/s", "iterations": n_it,
                 "forward_ms": st_ms[0], "backward_ms": st_ms[2],
                 "rel_l2_vs_headline_after_%d_iterations" % steps: rel}
+            if var == "direct" and pr in ("bf16", "bf16x3"):
+                paths[PATH_NAMES[(var, pr)]]["tensor_roofline"] = direct_tensor_roofline(g, pr, st_ms)
             del vo
             torch.cuda.empty_cache()
 
