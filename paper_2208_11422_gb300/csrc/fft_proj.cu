@@ -737,39 +737,39 @@ __global__ void k_low_list(const float* __restrict__ x, int64_t n, const unsigne
 }
 
 // ------------------------------------------------ layout and update kernels --
-// v[z][Iy*N+ty][Ix*N+tx] -> vcm[z*S + ty*N + tx][Iy][Ix]
-__global__ void k_poly_volume_cm(const float* __restrict__ v, Geo g, float* __restrict__ vcm) {
-    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.C * L2;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / L2);
-        const int64_t l = e % L2;
-        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
-        const int z = c / g.S, t = c % g.S;
-        vcm[e] = v[((int64_t)z * g.H + (int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N];
+// Stack-order planes <-> channel-major polyphase planes:
+//   img[z][Iy*N+ty][Ix*N+tx]  <->  cm[z*S + ty*N + tx][Iy][Ix]
+// (a volume has Nz planes, an image one). One block per (image row, plane):
+// the row goes through shared memory, so both the image row and the N
+// channel rows it feeds are read / written contiguously (the shared-memory
+// stride N is odd, so the accesses are free of bank conflicts).
+__global__ void k_to_cm(const float* __restrict__ img, Geo g, float* __restrict__ cm) {
+    extern __shared__ float row[];
+    const int y = blockIdx.x, z = blockIdx.y;
+    const int Iy = y / g.N, ty = y % g.N;
+    const float* src = img + ((int64_t)z * g.H + y) * g.W;
+    for (int x = threadIdx.x; x < g.W; x += blockDim.x) row[x] = src[x];
+    __syncthreads();
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    float* dst = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
+    for (int k = threadIdx.x; k < g.W; k += blockDim.x) {
+        const int tx = k / g.Lx, Ix = k % g.Lx;
+        dst[tx * L2 + Ix] = row[Ix * g.N + tx];
     }
 }
-__global__ void k_depoly_volume_cm(const float* __restrict__ vcm, Geo g, float* __restrict__ v) {
-    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.C * L2;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / L2);
-        const int64_t l = e % L2;
-        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
-        const int z = c / g.S, t = c % g.S;
-        v[((int64_t)z * g.H + (int64_t)Iy * g.N + t / g.N) * g.W + (int64_t)Ix * g.N + t % g.N] = vcm[e];
+__global__ void k_from_cm(const float* __restrict__ cm, Geo g, float* __restrict__ img) {
+    extern __shared__ float row[];
+    const int y = blockIdx.x, z = blockIdx.y;
+    const int Iy = y / g.N, ty = y % g.N;
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const float* src = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
+    for (int k = threadIdx.x; k < g.W; k += blockDim.x) {
+        const int tx = k / g.Lx, Ix = k % g.Lx;
+        row[Ix * g.N + tx] = src[tx * L2 + Ix];
     }
-}
-// y[Iy*N+sy][Ix*N+sx] -> ycm[sy*N + sx][Iy][Ix]
-__global__ void k_poly_image_cm(const float* __restrict__ y, Geo g, float* __restrict__ ycm) {
-    const int64_t L2 = (int64_t)g.Ly * g.Lx, total = (int64_t)g.S * L2;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e / L2);
-        const int64_t l = e % L2;
-        const int Iy = (int)(l / g.Lx), Ix = (int)(l % g.Lx);
-        ycm[e] = y[((int64_t)Iy * g.N + s / g.N) * g.W + (int64_t)Ix * g.N + s % g.N];
-    }
+    __syncthreads();
+    float* dst = img + ((int64_t)z * g.H + y) * g.W;
+    for (int x = threadIdx.x; x < g.W; x += blockDim.x) dst[x] = row[x];
 }
 __global__ void k_fill_cm(float* __restrict__ p, int64_t n, float val) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -1005,20 +1005,29 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
                      : run_c2r<32>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
-cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st) {
-    k_poly_volume_cm<<<grid_for((int64_t)g.C * g.Ly * g.Lx), 256, 0, st>>>(v, g, vcm);
+static cudaError_t cm_copy(bool to, const float* src, const Geo& g, int planes, float* dst, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)g.W;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(to ? k_to_cm : k_from_cm,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)g.H, (unsigned)planes);
+    if (to)
+        k_to_cm<<<grid, 256, smem, st>>>(src, g, dst);
+    else
+        k_from_cm<<<grid, 256, smem, st>>>(src, g, dst);
     count_launch();
     return cudaGetLastError();
+}
+cudaError_t launch_poly_volume_cm(const float* v, const Geo& g, float* vcm, cudaStream_t st) {
+    return cm_copy(true, v, g, g.Nz, vcm, st);
 }
 cudaError_t launch_depoly_volume_cm(const float* vcm, const Geo& g, float* v, cudaStream_t st) {
-    k_depoly_volume_cm<<<grid_for((int64_t)g.C * g.Ly * g.Lx), 256, 0, st>>>(vcm, g, v);
-    count_launch();
-    return cudaGetLastError();
+    return cm_copy(false, vcm, g, g.Nz, v, st);
 }
 cudaError_t launch_poly_image_cm(const float* y, const Geo& g, float* ycm, cudaStream_t st) {
-    k_poly_image_cm<<<grid_for((int64_t)g.S * g.Ly * g.Lx), 256, 0, st>>>(y, g, ycm);
-    count_launch();
-    return cudaGetLastError();
+    return cm_copy(true, y, g, 1, ycm, st);
 }
 cudaError_t launch_fill_cm(float* p, int64_t n, float val, cudaStream_t st) {
     k_fill_cm<<<grid_for(n), 256, 0, st>>>(p, n, val);

@@ -1,5 +1,7 @@
 // Fused RL update (multiplicative step, clamp, z-MIP, flux) and the
 // DCT-entropy metric of Section 2.2.
+#include <algorithm>
+
 #include "lfd_internal.h"
 
 namespace lfd {
@@ -99,39 +101,65 @@ __global__ void k_mip_stack(const float* __restrict__ v, int Nz, int64_t HW, flo
     }
 }
 
-// G[y][u] = sum_x f[y][x] * C_u(x; W) for u < XS (Eq. 1 along the rows, with
-// the basis of Eqs. 2-4 tabulated in cosW[u][x]); rowE2[y] = sum_x f[y][x]^2.
-__global__ void k_dct_rows(const float* __restrict__ f, const double* __restrict__ cosW, int W,
-                           int XS, double* __restrict__ G, double* __restrict__ rowE2) {
-    extern __shared__ float row[];
-    __shared__ double red[32];
-    const int y = blockIdx.x;
+// Row transform (Eq. 1 along the rows, basis of Eqs. 2-4 tabulated in
+// cosW[u][x]) G[y][u] = sum_x f[y][x] C_u(x; W), u < XS, and the row energy
+// rowE2[y] = sum_x f[y][x]^2 (FP64). A block holds ROWS rows in shared memory
+// (8, fewer for very wide images); warp w takes the basis rows u = w, w + 8,
+// ... and applies each to all the block's rows (one basis load per ROWS
+// products, ROWS independent sums per lane). The products and sums are double-float on the
+// FP32 units: the basis is an FP64 value split as hi + lo, each product
+// f * hi is kept exactly as p + e (FMA), and each running sum is a
+// compensated pair, rounded to FP64 at the end (about 44 significant bits,
+// without the slow FP64 pipe of this GPU).
+template <int ROWS>
+__global__ void __launch_bounds__(256) k_dct_rows(const float* __restrict__ f, const float2* __restrict__ cosW,
+                                                  int H, int W, int XS, double* __restrict__ G,
+                                                  double* __restrict__ rowE2) {
+    extern __shared__ float rows[];  // [ROWS][W]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int y0 = blockIdx.x * ROWS;
+    const int nr = min(ROWS, H - y0);
     {  // frame blockIdx.y
-        const int64_t H = gridDim.x;
         f += (int64_t)blockIdx.y * H * W;
         G += (int64_t)blockIdx.y * H * XS;
         rowE2 += (int64_t)blockIdx.y * H;
     }
-    double e2 = 0.0;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const float a = f[(int64_t)y * W + x];
-        row[x] = a;
-        e2 += (double)a * (double)a;
+    for (int r = w; r < ROWS; r += nw) {
+        double e2 = 0.0;
+        for (int x = lane; x < W; x += 32) {
+            const float a = r < nr ? f[(int64_t)(y0 + r) * W + x] : 0.f;
+            rows[r * W + x] = a;
+            e2 += (double)a * (double)a;
+        }
+        e2 = warp_sum(e2);
+        if (lane == 0 && r < nr) rowE2[y0 + r] = e2;
     }
-    const double tot = block_sum(e2, red);  // contains the barrier that publishes row[]
-    if (threadIdx.x == 0) rowE2[y] = tot;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
     for (int u = w; u < XS; u += nw) {
-        double s = 0.0;
-        const double* cb = cosW + (int64_t)u * W;
-        for (int x = lane; x < W; x += 32) s += (double)row[x] * cb[x];
-        s = warp_sum(s);
-        if (lane == 0) G[(int64_t)y * XS + u] = s;
+        const float2* cb = cosW + (int64_t)u * W;
+        float sh[ROWS], sl[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) sh[r] = sl[r] = 0.f;
+        for (int x = lane; x < W; x += 32) {
+            const float2 c = cb[x];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const float m = rows[r * W + x];
+                const float p = m * c.x;
+                const float e = fmaf(m, c.y, fmaf(m, c.x, -p));  // m*hi - p exactly, plus m*lo
+                const float t = sh[r] + p;                        // two-sum of sh + p
+                const float bp = t - sh[r];
+                sl[r] += ((sh[r] - (t - bp)) + (p - bp)) + e;
+                sh[r] = t;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const double s = warp_sum((double)sh[r] + (double)sl[r]);
+            if (lane == 0 && r < nr) G[(int64_t)(y0 + r) * XS + u] = s;
+        }
     }
 }
-
-// F(u, v) = sum_y C_v(y; H) * G[y][u] for (u, v) in the triangle
-// u*YS + v*XS < XS*YS (Eq. 6); one block per column u.
 __global__ void k_dct_cols(const double* __restrict__ G, const double* __restrict__ cosH, int H,
                            int XS, int YS, double* __restrict__ coef) {
     const int u = blockIdx.x;
@@ -219,17 +247,26 @@ cudaError_t launch_mip_stack(const float* v, int Nz, int64_t HW, float* mip, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH, int H, int W,
+cudaError_t launch_metric(const float* mip, const float2* cosW, const double* cosH, int H, int W,
                           int XS, int YS, int l2_over_region, double* G, double* rowE2,
                           double* coef, const double* flux_part, int nflux, double* out_entropy,
                           double* out_flux, cudaStream_t st, int nf, int out_stride) {
-    const size_t smem = (size_t)W * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_dct_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_dct_rows<<<dim3(H, nf), 256, smem, st>>>(mip, cosW, W, XS, G, rowE2);
+    // 8 rows per block, fewer where 8 rows of floats exceed 200 KB of shared memory
+    const size_t rowb = (size_t)W * sizeof(float);
+    const int rows = rowb * 8 <= 200 * 1024 ? 8 : rowb * 4 <= 200 * 1024 ? 4 : rowb * 2 <= 200 * 1024 ? 2 : 1;
+    const size_t smem = rows * rowb;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    auto launch = [&](auto kern) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<dim3((H + rows - 1) / rows, nf), 256, smem, st>>>(mip, cosW, H, W, XS, G, rowE2);
+        return cudaSuccess;
+    };
+    cudaError_t e = rows == 8 ? launch(k_dct_rows<8>) : rows == 4 ? launch(k_dct_rows<4>)
+                  : rows == 2 ? launch(k_dct_rows<2>) : launch(k_dct_rows<1>);
+    if (e != cudaSuccess) return e;
     k_dct_cols<<<dim3(XS, nf), 256, 0, st>>>(G, cosH, H, XS, YS, coef);
     k_entropy<<<nf, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
                                   out_entropy, out_flux, out_stride);

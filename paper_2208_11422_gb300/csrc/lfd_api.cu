@@ -62,6 +62,15 @@ bool make_geo(int P, int N, int Nz, int H, int W, Geo* g, std::string* why) {
     return true;
 }
 
+std::vector<float2> split_table(const std::vector<double>& t) {
+    std::vector<float2> r(t.size());
+    for (size_t i = 0; i < t.size(); ++i) {
+        const float hi = (float)t[i];
+        r[i] = make_float2(hi, (float)(t[i] - (double)hi));
+    }
+    return r;
+}
+
 std::vector<double> dct_table(int n, int Z) {
     // C_k(x; Z) = c(k, Z) cos((2x+1) pi k / (2Z)), c = sqrt(1/Z) for k = 0, sqrt(2/Z) otherwise
     std::vector<double> t((size_t)n * Z);
@@ -528,8 +537,9 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
 
     // metric tables (Eqs. 2-4), FP64 on the host
     {
-        std::vector<double> tw = dct_table(XS, g.W), th = dct_table(YS, g.H);
-        CREATE_CK(cudaMemcpyAsync(ctx->cosW, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        const std::vector<float2> tw = split_table(dct_table(XS, g.W));
+        const std::vector<double> th = dct_table(YS, g.H);
+        CREATE_CK(cudaMemcpyAsync(ctx->cosW, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
         CREATE_CK(cudaMemcpyAsync(ctx->cosH, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         CREATE_CK(cudaStreamSynchronize(st));
     }

@@ -54,6 +54,9 @@ constexpr float kLowSensitivity = 1e-3f;
 
 // orthonormal DCT-II basis rows C_k(x; Z), k < n, x < Z (Eqs. 2-4), FP64, [n][Z]
 std::vector<double> dct_table(int n, int Z);
+// the same values split as FP32 pairs (hi = fl(c), lo = fl(c - hi)), for the
+// row transform's double-float accumulation on the FP32 units
+std::vector<float2> split_table(const std::vector<double>& t);
 
 // ------------------------------------------------------------ device buffers --
 struct DevBuf {
@@ -98,7 +101,7 @@ struct lfd_ctx {
     float* ypoly = nullptr;      // [M_pad][Spad]
     // metric
     float* mip = nullptr;        // [H][W]
-    double* cosW = nullptr;      // [XS][W]
+    float2* cosW = nullptr;      // [XS][W] FP64 basis split as FP32 hi + lo
     double* cosH = nullptr;      // [YS][H]
     double* G = nullptr;         // [H][XS]
     double* rowE2 = nullptr;     // [H] sum of mip^2 per row
@@ -186,7 +189,7 @@ cudaError_t launch_mip(const float* vp32, const Geo& g, float* mip, cudaStream_t
 // DCT entropy of nf frames' MIPs (frame-major arrays: mip H*W, G H*XS, rowE2 H,
 // coef XS*YS, flux_part nflux per frame); frame f writes out_entropy[f*out_stride]
 // and out_flux[f*out_stride]
-cudaError_t launch_metric(const float* mip, const double* cosW, const double* cosH,
+cudaError_t launch_metric(const float* mip, const float2* cosW, const double* cosH,
                           int H, int W, int XS, int YS, int l2_over_region,
                           double* G, double* rowE2, double* coef,
                           const double* flux_part, int nflux, double* out_entropy,

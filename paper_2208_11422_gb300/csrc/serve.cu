@@ -120,7 +120,8 @@ struct Job {
     // device buffers, carved from the arena block
     float *ycm = nullptr, *vcm[2] = {nullptr, nullptr}, *xcm = nullptr, *invcm = nullptr;
     float *rcm = nullptr, *rimg = nullptr, *mip = nullptr;
-    double *cosW = nullptr, *cosH = nullptr, *G = nullptr, *rowE2 = nullptr, *coef = nullptr;
+    float2* cosW = nullptr;  // FP64 basis split as FP32 hi + lo
+    double *cosH = nullptr, *G = nullptr, *rowE2 = nullptr, *coef = nullptr;
     double* flux_part = nullptr;
     int* low = nullptr;
     int* n_low = nullptr;
@@ -151,7 +152,7 @@ int64_t job_layout(Job* j, char* base) {
     j->rcm = (float*)take(4 * g.S * L2);
     j->rimg = (float*)take(4 * img);
     j->mip = (float*)take(4 * img);
-    j->cosW = (double*)take(8 * (int64_t)j->XS * g.W);
+    j->cosW = (float2*)take(8 * (int64_t)j->XS * g.W);
     j->cosH = (double*)take(8 * (int64_t)j->YS * g.H);
     j->G = (double*)take(8 * (int64_t)g.H * j->XS);
     j->rowE2 = (double*)take(8 * (int64_t)g.H);
@@ -385,10 +386,12 @@ void enqueue_tick(lfd_server* s, PsfSet& ps) {
         }
         TICK_CK(launch_poly_image_cm(ysrc, g, j->ycm, st));
         double* tab = ps.h_tab + (int64_t)i * ps.tab_stride;
-        const std::vector<double> tw = dct_table(j->XS, g.W), th = dct_table(j->YS, g.H);
-        std::memcpy(tab, tw.data(), tw.size() * sizeof(double));
+        const std::vector<float2> tw = split_table(dct_table(j->XS, g.W));
+        const std::vector<double> th = dct_table(j->YS, g.H);
+        static_assert(sizeof(float2) == sizeof(double), "one table entry either way");
+        std::memcpy(tab, tw.data(), tw.size() * sizeof(float2));
         std::memcpy(tab + tw.size(), th.data(), th.size() * sizeof(double));
-        TICK_CK(cudaMemcpyAsync(j->cosW, tab, tw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        TICK_CK(cudaMemcpyAsync(j->cosW, tab, tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
         TICK_CK(cudaMemcpyAsync(j->cosH, tab + tw.size(), th.size() * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
         TICK_CK(launch_fill_cm(j->vcm[0], (int64_t)g.C * g.Ly * g.Lx, 1.0f, st));
