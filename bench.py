@@ -501,10 +501,7 @@ def run_lfd(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
         "data": "synthetic (seeded beads + filaments, Poisson noise)",
-        "config": {"workload": g.name, "H": g.H, "W": g.W,
-                   "Nnum": g.nnum, "Nz": g.nz, "P": g.P, "precision": prec, "variant": variant,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (volume %.2f GB)" % (g.nz * g.H * g.W * 4 / 1e9)},
+        "config": frame_config(g, prec, variant, world),
         "e2e": e2e, "e2e_volume_roundtrip": e2e_rt, "gpu_launches": launches, "clocks": clocks,
         "roofline": roof, "cpu_baseline": cpu, "paths": paths,
         "entropy": ent, "predicted_iteration": pred,
@@ -726,12 +723,23 @@ def run_serve(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def frame_config(g, prec, variant, world):
+    """The `config` object of the frame workload (both arms print the same)."""
+    return {"workload": g.name, "H": g.H, "W": g.W, "Nnum": g.nnum, "Nz": g.nz, "P": g.P,
+            "precision": prec, "variant": variant,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (volume %.2f GB)" % (g.nz * g.H * g.W * 4 / 1e9)}
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload
+    (one RL iteration on a crop per step, scaled to the frame)."""
     if rank != 0:
         return
     steps = args.steps if args.steps is not None else 1
     warm = args.warmup
+    for _ in range(warm):
+        cpu_baseline_sample(args.config)
     vals = []
     sample = cores = None
     for _ in range(steps):
@@ -749,7 +757,7 @@ def run_reference(args, rank, world):
         "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps, "warmup": warm,
         "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": g.name, "H": g.H, "W": g.W, "Nnum": g.nnum, "Nz": g.nz, "P": g.P},
+        "config": frame_config(g, args.precision or "bf16x3", args.variant, world),
         "cpu_baseline": {"value": value, "unit": "RL iterations/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "RL iterations/s", "h2d_bytes_per_step": 0,
