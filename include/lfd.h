@@ -246,6 +246,20 @@ lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps,
  * pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
 lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int* bins);
 
+/* Test hooks (no counterpart in the paper).
+ * lfd_debug_fail_allocs(n): the next n device allocations the library makes
+ * (contexts, staging buffers, PSF sets, the serving arena) fail with
+ * LFD_ENOMEM without calling the CUDA allocator; n <= 0 cancels. Host-side
+ * fault injection: a call that fails this way leaves its context as it was.
+ * lfd_selftest_bounded_wait(limit_ns, code): runs one kernel whose thread waits
+ * on a shared-memory mbarrier that nothing arrives at, with the bounded wait of
+ * the tensor-core kernels limited to limit_ns (1e6 .. 4e9); *code receives the
+ * error word the kernel stored. LFD_ETIMEDOUT: the wait gave up (the expected
+ * outcome); LFD_OK: it completed; LFD_EINVAL: limit out of range; LFD_ECUDA:
+ * a launch or copy failed. */
+void lfd_debug_fail_allocs(int n);
+lfd_status lfd_selftest_bounded_wait(int64_t limit_ns, int* code);
+
 /* Number of kernels the library has launched in this process (all contexts). */
 uint64_t lfd_launch_count(void);
 

@@ -5,6 +5,7 @@
 namespace lfd {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_fail_allocs{0};
 
 namespace {
 

@@ -98,6 +98,11 @@ bool is_device_ptr(const void* p) {
 template <class T>
 lfd_status dalloc(lfd_ctx* ctx, T** p, int64_t count, bool zero) {
     const size_t bytes = (size_t)count * sizeof(T);
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        ctx->err = "device allocation of " + std::to_string(bytes) + " bytes failed (injected)";
+        return LFD_ENOMEM;
+    }
     cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -159,6 +159,16 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// host-side fault injection (lfd_debug_fail_allocs): the next n device
+// allocations of the library report failure without calling cudaMalloc
+extern std::atomic<int> g_fail_allocs;
+inline bool injected_alloc_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // --------------------------------------------------------- kernel launchers --

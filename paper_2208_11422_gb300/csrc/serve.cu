@@ -56,6 +56,7 @@ class Arena {
     int64_t cap = 0, used = 0, peak = 0;
 
     cudaError_t init(int64_t bytes) {
+        if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc((void**)&base, (size_t)bytes);
         if (e != cudaSuccess) {
             base = nullptr;
@@ -208,6 +209,10 @@ struct PsfSet {
     template <class T>
     cudaError_t dev(T** p, int64_t count) {
         const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        if (injected_alloc_failure()) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
         cudaError_t e = cudaMalloc((void**)p, bytes);
         if (e != cudaSuccess) {
             *p = nullptr;

@@ -38,14 +38,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false when the block is aborting or the limit passed
+// bounded wait; false when the block is aborting or the limit passed (then
+// the abort flag is raised and `code` stored in *err)
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
-                          int code) {
+                          int code, unsigned long long limit_ns = kTimeoutNs) {
     if (mbar_try_wait(b, parity)) return true;
     const unsigned long long t0 = gtime();
     while (!mbar_try_wait(b, parity)) {
         if (*abort_flag) return false;
-        if (gtime() - t0 > kTimeoutNs) {
+        if (gtime() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicExch(err, code);
             return false;

@@ -120,6 +120,8 @@ _SIGS = {
     "lfd_get_fft_plan": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
     "lfd_launch_count": (ctypes.c_uint64, []),
+    "lfd_debug_fail_allocs": (None, [_I]),
+    "lfd_selftest_bounded_wait": (_I, [ctypes.c_int64, ctypes.POINTER(_I)]),
     "lfd_server_default_options": (None, [ctypes.POINTER(lfd_server_options)]),
     "lfd_server_create": (_I, [ctypes.POINTER(lfd_server_options), ctypes.POINTER(_VP)]),
     "lfd_server_add_psf": (_I, [_VP, _VP, _I, _I, _I, _I, _I, ctypes.POINTER(_I)]),
@@ -317,6 +319,17 @@ def lfd_get_fft_plan(ctx) -> dict:
     _check(load().lfd_get_fft_plan(ctx, ctypes.byref(F), ctypes.byref(B), ctypes.byref(nt),
                                    ctypes.byref(bins)), ctx)
     return {"F": F.value, "B": B.value, "tiles": nt.value, "bins": bins.value}
+
+
+def lfd_debug_fail_allocs(n: int):
+    load().lfd_debug_fail_allocs(n)
+
+
+def lfd_selftest_bounded_wait(limit_ns: int):
+    """(status, error word) of the bounded-wait self-test kernel."""
+    code = _I(0)
+    st = load().lfd_selftest_bounded_wait(limit_ns, ctypes.byref(code))
+    return st, code.value
 
 
 def lfd_launch_count() -> int:

@@ -165,3 +165,11 @@ def test_server_calls_reject_null_handles(lib):
     assert lib.lfd_cancel(None, 1) == lfd.LFD_EINVAL
     assert lib.lfd_server_add_psf(None, None, 3, 1, 1, 3, 3, None) == lfd.LFD_EINVAL
     lib.lfd_server_destroy(None)
+
+
+def test_bounded_wait_selftest_rejects_limits_before_cuda(lib):
+    code = ctypes.c_int(5)
+    assert lib.lfd_selftest_bounded_wait(10, ctypes.byref(code)) == lfd.LFD_EINVAL
+    assert lib.lfd_selftest_bounded_wait(5_000_000_000, ctypes.byref(code)) == lfd.LFD_EINVAL
+    assert lib.lfd_selftest_bounded_wait(20_000_000, None) == lfd.LFD_EINVAL
+    lib.lfd_debug_fail_allocs(0)
