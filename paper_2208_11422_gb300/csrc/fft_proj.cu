@@ -196,6 +196,30 @@ struct OutPlanes {
         }
     }
 };
+// The transformed volume / ratio for the tensor-core contraction, in groups of
+// 8 channels: plane[q][g][col][bin][8] (g = channel / 8). One transform block
+// writes, per plane, all bins of its 8 channels of one column as one
+// contiguous run; the contraction's TMA box (8 channels x 1 bin x 16 columns
+// x 8 groups) lands in shared memory as [group][column][8 channels], the
+// canonical K-major layout without swizzle (8 x 16-byte core matrices).
+struct OutPlanesG {
+    __nv_bfloat16* p[4];
+    int ncolp, bins;  // columns per group, bins per column
+    __device__ void put8(int bin, int col, int c0, const float2 (&v)[8]) const {
+        const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8;
+        __align__(16) __nv_bfloat16 h[4][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const __nv_bfloat16 rh = __float2bfloat16_rn(v[k].x), ih = __float2bfloat16_rn(v[k].y);
+            h[0][k] = rh;
+            h[1][k] = __float2bfloat16_rn(v[k].x - __bfloat162float(rh));
+            h[2][k] = ih;
+            h[3][k] = __float2bfloat16_rn(v[k].y - __bfloat162float(ih));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
+    }
+};
 
 // R2C 2-D transform of the F x F patches of FftSize<F>::R2C_CH channels of
 // one tile; bin = fy*(F/2+1) + fx, out.put8 for every channel below ldc (zeros
@@ -894,11 +918,20 @@ cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, Out out, cudaStream_t 
 template <class Src>
 cudaError_t r2c_any(const FftPlan& p, Src src, int nch, int ldc, int ntile, float2* c64,
                     __nv_bfloat16* const* planes, int plane_tiles, cudaStream_t st) {
-    if (planes) {
+    if (planes) {  // the PSF spectra: [bins][S][Cw] (plane_tiles = S rows per bin)
         OutPlanes o{{planes[0], planes[1], planes[2], planes[3]}, plane_tiles, ldc};
         return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
     }
     OutC64 o{c64, ntile, ldc};
+    return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
+}
+
+// the columns' spectra for the tensor-core contraction: grouped planes
+// (ldc a multiple of 8)
+template <class Src>
+cudaError_t r2c_grouped(const FftPlan& p, Src src, int nch, int ldc, int ntile,
+                        __nv_bfloat16* const* planes, int ncolp, cudaStream_t st) {
+    OutPlanesG o{{planes[0], planes[1], planes[2], planes[3]}, ncolp, p.bins};
     return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
 }
 
@@ -974,7 +1007,7 @@ cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     const int ncol = nf * p.ntile;
     ImgSrc src{vcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x, p.ntile, (int64_t)g.C * L2};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, ncol, nullptr, b.Xp, b.ncolp, st)
+    cudaError_t e = b.cg ? r2c_grouped(p, src, g.C, p.Cw, ncol, b.Xp, b.ncolp, st)
                          : r2c_any(p, src, g.C, p.Cf, ncol, b.Xh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
@@ -992,7 +1025,7 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     const int ncol = nf * p.ntile;
     ImgSrc src{rcm, g.Ly, g.Lx, p.h, p.B, p.tiles_x, p.ntile, (int64_t)g.S * L2};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, ncol, nullptr, b.Yp, b.ncolp, st)
+    cudaError_t e = b.cg ? r2c_grouped(p, src, g.S, p.Sw, ncol, b.Yp, b.ncolp, st)
                          : r2c_any(p, src, g.S, p.Sf, ncol, b.Yh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
@@ -1070,7 +1103,7 @@ cudaError_t launch_low_list(const float* x, int64_t n, float frac, unsigned* mx,
 cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
                             const int* colf, int col0, int ncol, float eps, cudaStream_t st) {
     TabSrc src{fr, colf, col0, p.h, p.B, true};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.C, p.Cw, ncol, nullptr, b.Xp, b.ncolp, st)
+    cudaError_t e = b.cg ? r2c_grouped(p, src, g.C, p.Cw, ncol, b.Xp, b.ncolp, st)
                          : r2c_any(p, src, g.C, p.Cf, ncol, b.Xh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     e = b.cg ? cgemm_forward(b.cg, ncol, st) : contract_fwd_all(p, g, b.Wf, b.Xh, b.Yh, ncol, st);
@@ -1083,7 +1116,7 @@ cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b,
 cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
                              const int* colf, int col0, int ncol, cudaStream_t st) {
     TabSrc src{fr, colf, col0, p.h, p.B, false};
-    cudaError_t e = b.cg ? r2c_any(p, src, g.S, p.Sw, ncol, nullptr, b.Yp, b.ncolp, st)
+    cudaError_t e = b.cg ? r2c_grouped(p, src, g.S, p.Sw, ncol, b.Yp, b.ncolp, st)
                          : r2c_any(p, src, g.S, p.Sf, ncol, b.Yh, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     e = b.cg ? cgemm_adjoint(b.cg, ncol, st) : contract_adj_all(p, g, b.Wf, b.Yh, b.Xh, ncol, st);

@@ -15,9 +15,10 @@ struct FftPlan {
 };
 
 // Spectra buffers. FP32 contraction: Wf, Xh, Yh (complex64). Tensor-core
-// contraction (cg != null): BF16 planes Wp[4] [bins][S][Cw], Xp[4] [bins][16][Cw],
-// Yp[4] [bins][16][Sw] (real hi, real lo, imag hi, imag lo) as inputs, and
-// Yh / Xh as the contractions' complex64 outputs.
+// contraction (cg != null): BF16 planes (real hi, real lo, imag hi, imag lo)
+// Wp[4] [bins][S][Cw] (PSF), Xp[4] [Cw/8][ncolp][bins][8] (volume columns) and
+// Yp[4] [Sw/8][ncolp][bins][8] (ratio columns) as inputs, and Yh / Xh as the
+// contractions' complex64 outputs.
 struct FftBuffers {
     float2* Wf = nullptr;
     float2* Xh = nullptr;

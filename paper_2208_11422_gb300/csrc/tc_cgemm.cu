@@ -129,7 +129,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         } else {
                             tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
-                        tma_3d(sB + i * kPlaneB, B[i], kb * 64, cg * 16, bin, &full[stage]);
+                        // 8 channels x 1 bin x 16 columns x 8 groups: [group][column][8]
+                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, cg * 16, kb * 8, &full[stage]);
                     }
                     ++issued;
                     if (++stage == kStages) {
@@ -177,7 +178,9 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                             for (int i = 0; i < 4; ++i) {
                                 ad[i] = ADJ ? sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024)
                                             : sdesc(sA + i * kPlaneA + ks * 32, 16, 1024);
-                                bd[i] = sdesc(sB + i * kPlaneB + ks * 32, 16, 1024);
+                                // K = 16 per MMA: groups 2ks, 2ks+1 (256 B apart); the
+                                // two 8-column halves 128 B apart
+                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 512, 256, 128);
                             }
 #pragma unroll
                             for (int p = 0; p < 3; ++p) {
@@ -284,6 +287,21 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// grouped column planes [groups][ncolp][bins][8]: the box 8 channels x 1 bin x
+// 16 columns x 8 groups lands densely (no swizzle) as [group][column][8], the
+// K-major core-matrix layout the B descriptor below describes
+bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {8, bins, ncolp, groups};
+    const cuuint64_t str[3] = {16, 16 * bins, 16 * bins * ncolp};
+    const cuuint32_t box[4] = {8, 1, 16, 8};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, str, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct CgState {
     CUtensorMap fa[4], fb[4], aa[4], ab[4];
     CgArgs fwd, adj;
@@ -304,8 +322,8 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     for (int i = 0; i < 4; ++i) {
         bool ok = map3(&s->fa[i], b.W[i], b.Cw, b.S, b.bins, 64, 128) &&
                   map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64) &&
-                  map3(&s->fb[i], b.X[i], b.Cw, b.ncolp, b.bins, 64, 16) &&
-                  map3(&s->ab[i], b.Y[i], b.Sw, b.ncolp, b.bins, 64, 16);
+                  map4_grouped(&s->fb[i], b.X[i], b.Cw / 8, b.bins, b.ncolp) &&
+                  map4_grouped(&s->ab[i], b.Y[i], b.Sw / 8, b.bins, b.ncolp);
         if (!ok) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the spectra planes";
             return cudaErrorInvalidValue;

@@ -9,13 +9,13 @@ namespace lfd {
 // Operands are BF16 planes: [0] real hi, [1] real lo, [2] imag hi, [3] imag lo.
 struct CgemmBuffers {
     int bins, ntile;          // frequency bins; tiles per frame
-    int ncolp;                // rows per bin of the X / Y planes (columns padded to 16)
+    int ncolp;                // columns of the X / Y planes (padded to 16)
     int S, C;                 // phases, channels
     int Sw, Cw;               // plane row lengths (multiples of 8)
     int Sf, Cf;               // FP32 complex output row lengths
     const __nv_bfloat16* W[4];  // [bins][S][Cw] PSF spectra
-    const __nv_bfloat16* X[4];  // [bins][ncolp][Cw] volume spectra (forward input)
-    const __nv_bfloat16* Y[4];  // [bins][ncolp][Sw] ratio spectra (adjoint input)
+    const __nv_bfloat16* X[4];  // [Cw/8][ncolp][bins][8] volume spectra (forward input)
+    const __nv_bfloat16* Y[4];  // [Sw/8][ncolp][bins][8] ratio spectra (adjoint input)
     float2* Yout;             // [bins][ncol][Sf] forward output
     float2* Xout;             // [bins][ncol][Cf] adjoint output
 };
