@@ -256,9 +256,15 @@ lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int*
  * the tensor-core kernels limited to limit_ns (1e6 .. 4e9); *code receives the
  * error word the kernel stored. LFD_ETIMEDOUT: the wait gave up (the expected
  * outcome); LFD_OK: it completed; LFD_EINVAL: limit out of range; LFD_ECUDA:
- * a launch or copy failed. */
+ * a launch or copy failed.
+ * lfd_selftest_freelist(seed, steps): host only; runs `steps` random
+ * allocations and releases on the first-fit free list of the serving arena and
+ * checks it against a byte map: no overlap, 256-byte alignment, failure only
+ * when no free run is large enough, exact accounting, full coalescing at the
+ * end. LFD_OK, LFD_EINTERNAL on a violation, LFD_EINVAL for steps < 1. */
 void lfd_debug_fail_allocs(int n);
 lfd_status lfd_selftest_bounded_wait(int64_t limit_ns, int* code);
+lfd_status lfd_selftest_freelist(int seed, int steps);
 
 /* Number of kernels the library has launched in this process (all contexts). */
 uint64_t lfd_launch_count(void);

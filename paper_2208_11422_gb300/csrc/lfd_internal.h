@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -158,6 +159,26 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     c = (t - s) - y;
     s = t;
 }
+
+// First-fit offset allocator with coalescing (the serving arena's bookkeeping)
+int64_t align256(int64_t b);
+class FreeList {
+  public:
+    int64_t used = 0, peak = 0;
+    void reset(int64_t cap) {
+        free_.clear();
+        taken_.clear();
+        used = peak = 0;
+        if (cap > 0) free_[0] = cap;
+    }
+    int64_t alloc(int64_t bytes);  // offset (256-byte aligned size), or -1
+    bool release(int64_t off);     // false for an offset not handed out
+    size_t free_blocks() const { return free_.size(); }
+
+  private:
+    std::map<int64_t, int64_t> free_;   // offset -> bytes
+    std::map<int64_t, int64_t> taken_;  // offset -> bytes
+};
 
 // host-side fault injection (lfd_debug_fail_allocs): the next n device
 // allocations of the library report failure without calling cudaMalloc

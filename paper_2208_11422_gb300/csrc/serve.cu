@@ -43,17 +43,61 @@
 #include "tc_cgemm.h"
 
 namespace lfd {
+
+int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
-int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+}  // namespace
 
-// First-fit allocator over one device allocation (bookkeeping on the host).
+// First-fit bookkeeping of offsets in [0, cap) with coalescing on release
+// (host only; the server's device arena is one allocation managed by it).
+int64_t FreeList::alloc(int64_t bytes) {
+    bytes = align256(bytes);
+    if (bytes <= 0) return -1;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second < bytes) continue;
+        const int64_t off = it->first, rest = it->second - bytes;
+        free_.erase(it);
+        if (rest > 0) free_[off + bytes] = rest;
+        taken_[off] = bytes;
+        used += bytes;
+        peak = std::max(peak, used);
+        return off;
+    }
+    return -1;
+}
+bool FreeList::release(int64_t off) {
+    auto t = taken_.find(off);
+    if (t == taken_.end()) return false;
+    int64_t size = t->second;
+    taken_.erase(t);
+    used -= size;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && next->first == off + size) {
+        size += next->second;
+        next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += size;
+            return true;
+        }
+    }
+    free_[off] = size;
+    return true;
+}
+
+namespace {
+
 class Arena {
   public:
     char* base = nullptr;
-    int64_t cap = 0, used = 0, peak = 0;
+    int64_t cap = 0;
+    FreeList fl;
 
     cudaError_t init(int64_t bytes) {
         if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
@@ -63,50 +107,14 @@ class Arena {
             return e;
         }
         cap = bytes;
-        free_[0] = bytes;
+        fl.reset(bytes);
         return cudaSuccess;
     }
-    int64_t alloc(int64_t bytes) {
-        bytes = align256(bytes);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            const int64_t off = it->first, rest = it->second - bytes;
-            free_.erase(it);
-            if (rest > 0) free_[off + bytes] = rest;
-            taken_[off] = bytes;
-            used += bytes;
-            peak = std::max(peak, used);
-            return off;
-        }
-        return -1;
-    }
-    void release(int64_t off) {
-        auto t = taken_.find(off);
-        if (t == taken_.end()) return;
-        int64_t size = t->second;
-        taken_.erase(t);
-        used -= size;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && next->first == off + size) {
-            size += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += size;
-                return;
-            }
-        }
-        free_[off] = size;
-    }
+    int64_t alloc(int64_t bytes) { return fl.alloc(bytes); }
+    void release(int64_t off) { fl.release(off); }
     ~Arena() {
         if (base) cudaFree(base);
     }
-
-  private:
-    std::map<int64_t, int64_t> free_;   // offset -> bytes
-    std::map<int64_t, int64_t> taken_;  // offset -> bytes
 };
 
 enum class JobState { Queued, New, Iter, Finishing, Done };
@@ -787,7 +795,7 @@ lfd_status lfd_server_stats_get(const lfd_server* cs, lfd_server_stats* out) {
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
     out->arena_bytes = s->arena.cap;
-    out->arena_peak_bytes = s->arena.peak;
+    out->arena_peak_bytes = s->arena.fl.peak;
     out->queued = (int)s->queue.size();
     int inflight = 0;
     for (auto& ps : s->sets)

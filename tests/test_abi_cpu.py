@@ -173,3 +173,10 @@ def test_bounded_wait_selftest_rejects_limits_before_cuda(lib):
     assert lib.lfd_selftest_bounded_wait(5_000_000_000, ctypes.byref(code)) == lfd.LFD_EINVAL
     assert lib.lfd_selftest_bounded_wait(20_000_000, None) == lfd.LFD_EINVAL
     lib.lfd_debug_fail_allocs(0)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_serving_arena_free_list(lib, seed):
+    """The serving arena's first-fit free list against a byte-map model."""
+    assert lib.lfd_selftest_freelist(seed, 400) == lfd.LFD_OK
+    assert lib.lfd_selftest_freelist(seed, 0) == lfd.LFD_EINVAL
