@@ -979,7 +979,9 @@ bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, bool split_
         const double rate = split_bf16 ? 1.7e15 / 3.0 : 6.0e13;
         // transforms: one F x F patch per tile, frame and channel
         const double xform = (double)q.ntile * frames * (g.C + g.S) * 2.0 * F * F * 8.0;
-        const double t = std::max(spectra / 6.0e12, flops / rate) + xform / 4.0e12;
+        // the tensor-core contraction streams the spectra once per 64 columns
+        const double passes = split_bf16 ? (double)((q.ntile * frames + 63) / 64) : 1.0;
+        const double t = std::max(spectra * passes / 6.0e12, flops / rate) + xform / 4.0e12;
         if (t < best_t) {
             best_t = t;
             best = q;

@@ -10,16 +10,17 @@
 //   adjoint  re += Wr Yr + Wi Yi,   im += Wr Yi - Wi Yr
 // each of them in three passes hi*hi + hi*lo + lo*hi (negation through the
 // instruction descriptor). One block owns 128 output rows (phases s for the
-// forward, channels c for the adjoint) by 16 columns (frame x tile) of one bin;
-// units are ordered bin-major so the blocks working on one bin share its
-// spectra in L2. Its K loop
-// streams 64-wide blocks of all eight planes through a 3-stage TMA ring. The
-// accumulators (real and imaginary, 16 columns each) alternate between two
-// TMEM buffers so the drain of one chunk overlaps the next; chains are cut
-// every 64 k-blocks (1536 MMA steps) and added into the FP32 output at L2
-// (the same rounding control as the direct projections). The spectra (all of
-// Wf, 8 bytes per complex value) are read once per projection: the kernel is
-// bound by HBM bandwidth.
+// forward, channels c for the adjoint) by a chunk of 16, 32 or 64 columns
+// (frame x tile) of one bin, so a spectra tile is loaded once for up to 64
+// columns; units are ordered bin-major so the blocks working on one bin share
+// its spectra in L2. Its K loop streams 64-wide blocks of all eight planes
+// through a TMA ring (3 stages for 16 columns, 2 for wider chunks). The
+// accumulators (real and imaginary, one chunk of columns each) alternate
+// between two TMEM buffers so the drain of one chunk overlaps the next; chains
+// are cut every 64 k-blocks (1536 MMA steps) and added into the FP32 output at
+// L2 (the same rounding control as the direct projections). The spectra (all
+// of Wf, 8 bytes per complex value) are read once per projection while the
+// columns fit one chunk: the kernel is bound by HBM bandwidth.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -35,18 +36,28 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kStages = 3;
 constexpr int kPlaneA = 128 * 64 * 2;  // 16 KB
-constexpr int kPlaneB = 16 * 64 * 2;   // 2 KB
-constexpr int kStageBytes = 4 * kPlaneA + 4 * kPlaneB;
 constexpr int kThreads = 192;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 MMA steps
+
+// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4).
+template <int NG>
+struct Cg {
+    static constexpr int N = 16 * NG;                        // MMA N
+    static constexpr int kPlaneB = N * 64 * 2;               // 2, 4 or 8 KB
+    static constexpr int kStageBytes = 4 * kPlaneA + 4 * kPlaneB;
+    static constexpr int kStages = NG == 1 ? 3 : 2;
+    static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+    static constexpr uint32_t kTmemCols = 64 * NG;           // 2 buffers x (real, imag) x N
+};
+static_assert(Cg<1>::kSmemBytes <= 232448 && Cg<2>::kSmemBytes <= 232448 &&
+                  Cg<4>::kSmemBytes <= 232448,
+              "stage ring exceeds the shared memory of a block");
 
 struct CgArgs {
     int nbins;
     int ncol;          // output columns (frames x tiles) of this launch
-    int ncg;           // column groups of 16
+    int nchunk;        // column chunks of 16 x NG
     int mtiles;        // row tiles of 128 per bin
     int nkb;           // k-blocks of 64 per unit
     int nrows;         // valid rows (S or C)
@@ -55,13 +66,16 @@ struct CgArgs {
     int* err;
 };
 
-template <bool ADJ>
+template <bool ADJ, int NG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
            const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
            const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
            const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
            const CgArgs a) {
+    constexpr int kStages = Cg<NG>::kStages, kStageBytes = Cg<NG>::kStageBytes;
+    constexpr int kPlaneB = Cg<NG>::kPlaneB, N = Cg<NG>::N;
+    constexpr uint32_t kTmemCols = Cg<NG>::kTmemCols;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -76,7 +90,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_units = a.nbins * a.ncg * a.mtiles;
+    const int n_units = a.nbins * a.nchunk * a.mtiles;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -95,7 +109,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(64));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -112,8 +126,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
             uint32_t phase = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int bin = u / (a.ncg * a.mtiles), rem = u % (a.ncg * a.mtiles);
-                const int cg = rem / a.mtiles, mt = rem % a.mtiles;
+                const int bin = u / (a.nchunk * a.mtiles), rem = u % (a.nchunk * a.mtiles);
+                const int q = rem / a.mtiles, mt = rem % a.mtiles;
                 for (int kb = 0; kb < a.nkb && ok; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
                         ok = false;
@@ -129,8 +143,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         } else {
                             tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
-                        // 8 channels x 1 bin x 16 columns x 8 groups: [group][column][8]
-                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, cg * 16, kb * 8, &full[stage]);
+                        // 8 channels x 1 bin x N columns x 8 groups: [group][column][8]
+                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, q * N, kb * 8, &full[stage]);
                     }
                     ++issued;
                     if (++stage == kStages) {
@@ -146,8 +160,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer --
-            const uint32_t id_p = idesc_bf16(128, 16, false, ADJ, false);
-            const uint32_t id_n = idesc_bf16(128, 16, false, ADJ, true);
+            const uint32_t id_p = idesc_bf16(128, N, false, ADJ, false);
+            const uint32_t id_n = idesc_bf16(128, N, false, ADJ, true);
             int stage = 0, consumed = 0, ci = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -161,7 +175,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dR = tmem + buf * 32, dI = dR + 16;
+                    const uint32_t dR = tmem + buf * 2 * N, dI = dR + N;
                     bool first = true;
                     for (int kb = c0; kb < c1 && ok; ++kb) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) {
@@ -178,9 +192,9 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                             for (int i = 0; i < 4; ++i) {
                                 ad[i] = ADJ ? sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024)
                                             : sdesc(sA + i * kPlaneA + ks * 32, 16, 1024);
-                                // K = 16 per MMA: groups 2ks, 2ks+1 (256 B apart); the
-                                // two 8-column halves 128 B apart
-                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 512, 256, 128);
+                                // K = 16 per MMA: groups 2ks, 2ks+1 (N x 16 B apart); the
+                                // 8-column core matrices 128 B apart
+                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 2 * N * 16, N * 16, 128);
                             }
 #pragma unroll
                             for (int p = 0; p < 3; ++p) {
@@ -221,8 +235,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
         int ci = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const int bin = u / (a.ncg * a.mtiles), rem = u % (a.ncg * a.mtiles);
-            const int cg = rem / a.mtiles, mt = rem % a.mtiles;
+            const int bin = u / (a.nchunk * a.mtiles), rem = u % (a.nchunk * a.mtiles);
+            const int q = rem / a.mtiles, mt = rem % a.mtiles;
             const int grow = mt * 128 + row;
             for (int c0 = 0; c0 < a.nkb; c0 += kChunkKb, ++ci) {
                 const int buf = ci & 1;
@@ -231,20 +245,25 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                     break;
                 }
                 tc_fence_after();
-                uint32_t re[16], im[16];
-                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16) + buf * 32;
-                tmem_ld16(tb, re);
-                tmem_ld16(tb + 16, im);
-                tmem_wait_ld();
-                if (grow < a.nrows) {
-                    float2* o = a.out + ((int64_t)bin * a.ncol + cg * 16) * a.ld + grow;
+                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16) + buf * 2 * N;
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        if (cg * 16 + t < a.ncol) {
-                            float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.ld);
-                            const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
-                            if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
-                            else red_add_v2(dst, vr, vi);
+                for (int g = 0; g < NG; ++g) {
+                    const int col0 = q * N + g * 16;
+                    if (col0 >= a.ncol) break;
+                    uint32_t re[16], im[16];
+                    tmem_ld16(tb + g * 16, re);
+                    tmem_ld16(tb + N + g * 16, im);
+                    tmem_wait_ld();
+                    if (grow < a.nrows) {
+                        float2* o = a.out + ((int64_t)bin * a.ncol + col0) * a.ld + grow;
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            if (col0 + t < a.ncol) {
+                                float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.ld);
+                                const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
+                                if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
+                                else red_add_v2(dst, vr, vi);
+                            }
                         }
                     }
                 }
@@ -258,7 +277,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -288,26 +308,69 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
 }
 
 // grouped column planes [groups][ncolp][bins][8]: the box 8 channels x 1 bin x
-// 16 columns x 8 groups lands densely (no swizzle) as [group][column][8], the
-// K-major core-matrix layout the B descriptor below describes
-bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp) {
+// ncb columns x 8 groups lands densely (no swizzle) as [group][column][8], the
+// K-major core-matrix layout the B descriptor of the kernel describes
+bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp,
+                  uint32_t ncb) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[4] = {8, bins, ncolp, groups};
     const cuuint64_t str[3] = {16, 16 * bins, 16 * bins * ncolp};
-    const cuuint32_t box[4] = {8, 1, 16, 8};
+    const cuuint32_t box[4] = {8, 1, ncb, 8};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, str, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// column chunks of 16 x kNg[j] columns; a chunk is never wider than the planes
+constexpr int kNg[3] = {1, 2, 4};
+
 struct CgState {
-    CUtensorMap fa[4], fb[4], aa[4], ab[4];
+    CUtensorMap fa[4], aa[4];
+    CUtensorMap fb[3][4], ab[3][4];  // per chunk width
     CgArgs fwd, adj;
-    int sm_count = 0, ncolp = 16;
+    int sm_count = 0, ncolp = 16, nwidths = 1;
     int* err = nullptr;
 };
+
+template <bool ADJ, int NG>
+cudaError_t launch_width(const CUtensorMap* A, const CUtensorMap* B, CgArgs a, int sm_count,
+                         cudaStream_t st) {
+    a.nchunk = (a.ncol + Cg<NG>::N - 1) / Cg<NG>::N;
+    const int grid = std::min(a.nbins * a.nchunk * a.mtiles, sm_count);
+    k_tc_cgemm<ADJ, NG><<<grid, kThreads, Cg<NG>::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
+                                                                    B[2], B[3], a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <bool ADJ>
+cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
+    if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
+    CgArgs a = ADJ ? s->adj : s->fwd;
+    a.ncol = ncol;
+    // the narrowest chunk that covers all columns, else the widest available
+    const int ncg = (ncol + 15) / 16;
+    int j = 0;
+    while (j + 1 < s->nwidths && kNg[j] < ncg) ++j;
+    const CUtensorMap* A = ADJ ? s->aa : s->fa;
+    const CUtensorMap* B = ADJ ? s->ab[j] : s->fb[j];
+    switch (kNg[j]) {
+        case 1: return launch_width<ADJ, 1>(A, B, a, s->sm_count, st);
+        case 2: return launch_width<ADJ, 2>(A, B, a, s->sm_count, st);
+        default: return launch_width<ADJ, 4>(A, B, a, s->sm_count, st);
+    }
+}
+
+template <int NG>
+cudaError_t set_smem() {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm<false, NG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cg<NG>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_cgemm<true, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cg<NG>::kSmemBytes);
+}
 
 }  // namespace
 
@@ -319,11 +382,14 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     cudaError_t e = cudaMalloc(&s->err, sizeof(int));
     if (e != cudaSuccess) return e;
     if ((e = cudaMemset(s->err, 0, sizeof(int))) != cudaSuccess) return e;
+    s->nwidths = 1;
+    while (s->nwidths < 3 && 16 * kNg[s->nwidths] <= b.ncolp) ++s->nwidths;
     for (int i = 0; i < 4; ++i) {
         bool ok = map3(&s->fa[i], b.W[i], b.Cw, b.S, b.bins, 64, 128) &&
-                  map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64) &&
-                  map4_grouped(&s->fb[i], b.X[i], b.Cw / 8, b.bins, b.ncolp) &&
-                  map4_grouped(&s->ab[i], b.Y[i], b.Sw / 8, b.bins, b.ncolp);
+                  map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64);
+        for (int j = 0; j < s->nwidths && ok; ++j)
+            ok = map4_grouped(&s->fb[j][i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16 * kNg[j]) &&
+                 map4_grouped(&s->ab[j][i], b.Y[i], b.Sw / 8, b.bins, b.ncolp, 16 * kNg[j]);
         if (!ok) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the spectra planes";
             return cudaErrorInvalidValue;
@@ -332,7 +398,7 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     CgArgs& f = s->fwd;
     f.nbins = b.bins;
     f.ncol = 16;
-    f.ncg = 1;
+    f.nchunk = 1;
     f.mtiles = (b.S + 127) / 128;
     f.nkb = (b.Cw + 63) / 64;
     f.nrows = b.S;
@@ -348,35 +414,17 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.out = b.Xout;
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
-    e = cudaFuncSetAttribute(k_tc_cgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_cgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if ((e = set_smem<1>()) != cudaSuccess) return e;
+    if ((e = set_smem<2>()) != cudaSuccess) return e;
+    return set_smem<4>();
 }
 
 cudaError_t cgemm_forward(void* state, int ncol, cudaStream_t st) {
-    CgState* s = static_cast<CgState*>(state);
-    if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
-    CgArgs a = s->fwd;
-    a.ncol = ncol;
-    a.ncg = (ncol + 15) / 16;
-    const int grid = std::min(a.nbins * a.ncg * a.mtiles, s->sm_count);
-    k_tc_cgemm<false><<<grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fa[2], s->fa[3],
-                                                          s->fb[0], s->fb[1], s->fb[2], s->fb[3], a);
-    count_launch();
-    return cudaGetLastError();
+    return launch<false>(static_cast<CgState*>(state), ncol, st);
 }
 
 cudaError_t cgemm_adjoint(void* state, int ncol, cudaStream_t st) {
-    CgState* s = static_cast<CgState*>(state);
-    if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
-    CgArgs a = s->adj;
-    a.ncol = ncol;
-    a.ncg = (ncol + 15) / 16;
-    const int grid = std::min(a.nbins * a.ncg * a.mtiles, s->sm_count);
-    k_tc_cgemm<true><<<grid, kThreads, kSmemBytes, st>>>(s->aa[0], s->aa[1], s->aa[2], s->aa[3],
-                                                         s->ab[0], s->ab[1], s->ab[2], s->ab[3], a);
-    count_launch();
-    return cudaGetLastError();
+    return launch<true>(static_cast<CgState*>(state), ncol, st);
 }
 
 int cgemm_error(void* state) {

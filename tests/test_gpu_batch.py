@@ -98,6 +98,30 @@ def test_batch_slots_compact_as_frames_stop(prec, use_graph):
         lfd.lfd_destroy(ctx)
 
 
+# one tile per frame at this size: 20 frames take the 32-column contraction
+# chunks, 70 frames two 64-column chunks (the second one ragged)
+@pytest.mark.parametrize("nf", [20, 70])
+def test_batch_wide_column_chunks_equal_single_frames(nf):
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    n = 4
+    g, psf, ys = make_frames(nf)
+    dev = torch.device("cuda:0")
+    ctx = ctx_for(psf, g, "bf16x3", nf)
+    try:
+        assert lfd.lfd_get_fft_plan(ctx)["tiles"] == 1
+        v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+        done, pred, ent, _ = lfd.lfd_rl_iterate_batch(ctx, nf, torch.from_numpy(ys).to(dev), v, n, False)
+        vb = v.cpu().numpy()
+        for f in sorted({0, 15, nf // 2, 63 % nf, nf - 1}):
+            v1 = torch.ones((g.nz, g.H, g.W), device=dev)
+            _, _, e1, _ = lfd.lfd_rl_iterate(ctx, torch.from_numpy(ys[f]).to(dev), v1, n, False)
+            assert rel_l2(vb[f], v1.cpu().numpy()) <= 1e-6, f
+            np.testing.assert_allclose(ent[f], e1, rtol=1e-9)
+    finally:
+        lfd.lfd_destroy(ctx)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_batch_frame0_matches_oracle(prec):
     import torch

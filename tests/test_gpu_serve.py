@@ -52,15 +52,17 @@ def make_server(lfd, prec, sets, **kw):
     return srv, ids
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
-def test_results_in_the_mix_equal_results_alone(prec):
+# (precision, frames per set, columns per contraction): 16 columns with at most
+# 3 frames per set, or 64 columns with all of a set's frames at once (the
+# contraction then takes 32-column chunks)
+@pytest.mark.parametrize("prec,mf,mc", [("bf16x3", 3, 16), ("fp32", 3, 16), ("bf16x3", 8, 64)])
+def test_results_in_the_mix_equal_results_alone(prec, mf, mc):
     import torch
     from paper_2208_11422_gb300 import lfd
     sets = psf_sets()
     n = 12
     ys = [frame_data(sets, k, *f) for k, f in enumerate(FRAMES)]
-    # at most 3 frames per set iterate together, 16 tiles per contraction
-    srv, ids = make_server(lfd, prec, sets, max_frames_per_set=3, max_cols=16, max_iter=n)
+    srv, ids = make_server(lfd, prec, sets, max_frames_per_set=mf, max_cols=mc, max_iter=n)
     outs, reqs = [], []
     try:
         for k, (si, ly, lx, _) in enumerate(FRAMES):
