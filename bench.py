@@ -221,7 +221,7 @@ def cpu_baseline_sample(cfg: int, psf=None):
 
 
 # ---------------------------------------------------------------- GPU arm --
-PATH_NAMES = {("fft", "fp32"): "fft_fp32", ("fft", "bf16x3"): "fft_bf16x3",
+PATH_NAMES = {("fft", "fp32"): "fft_fp32", ("fft", "bf16x3"): "fft_bf16x3", ("fft", "bf16"): "fft_bf16",
               ("direct", "bf16x3"): "direct_bf16x3", ("direct", "bf16"): "direct_bf16",
               ("direct", "fp32"): "direct_fp32"}
 
@@ -265,12 +265,15 @@ def direct_tensor_roofline(g, prec, st_ms):
 def fft_kernel_work(g, plan, prec):
     """Algorithmic bytes (and contraction flops) per launch of the FFT
     variant's four large kernels. Spectra are 8 bytes per complex value (BF16
-    hi/lo planes of real and imaginary part, or complex64)."""
+    hi/lo planes of real and imaginary part, or complex64); BF16 PSF spectra
+    are 4 bytes (hi planes only). Executed flops count every tensor-core
+    product (three per term in split BF16, two with BF16 PSF spectra)."""
     F, bins, nt, _, S, C = fft_plan_numbers(g, plan)
     L2 = (g.H // g.nnum) * (g.W // g.nnum)
     vol = 4.0 * C * L2
-    xs, ys, ws = 8.0 * bins * nt * C, 8.0 * bins * nt * S, 8.0 * bins * S * C
-    flops = 8.0 * bins * S * nt * C * (3 if prec == "bf16x3" else 1)
+    xs, ys = 8.0 * bins * nt * C, 8.0 * bins * nt * S
+    ws = (4.0 if prec == "bf16" else 8.0) * bins * S * C
+    flops = 8.0 * bins * S * nt * C * {"bf16x3": 3, "bf16": 2}.get(prec, 1)
     return {"volume_r2c": {"bytes": vol + xs, "slot": 8, "kernel": "forward volume transform"},
             "forward_contraction": {"bytes": ws + xs + ys, "flops": flops, "slot": 5,
                                     "kernel": "forward contraction"},
@@ -439,26 +442,39 @@ def run_lfd(args, rank, world, local):
 
     # the other formulations and precisions on the same GPU and data, with the
     # relative L2 distance of their v^steps from this path's
+    # (the FFT variant with FP32 contractions runs first: every path's v^steps
+    # is also compared with it, the metric's FP32 reference)
     paths = {}
+    head_vs_fp32 = None
     if not args.skip_fp32_ref:
-        for var, pr in (("fft", "bf16x3"), ("fft", "fp32"), ("direct", "bf16x3"), ("direct", "bf16"),
-                        ("direct", "fp32")):
+        v_fp32 = None
+        for var, pr in (("fft", "fp32"), ("fft", "bf16x3"), ("fft", "bf16"), ("direct", "bf16x3"),
+                        ("direct", "bf16"), ("direct", "fp32")):
             if (var, pr) == (variant, prec):
                 continue
             n_it = 1 if (var, pr) == ("direct", "fp32") else steps
             it_s, st_ms, vo = time_path(lfd, torch, dev, psf_d, g, y_d, var, pr, n_it,
                                         0 if n_it == 1 else 2, stream)
-            rel = None
+            rel = rel32 = None
             if n_it == steps:
                 rel = float(torch.linalg.vector_norm(vo - v_head) / torch.linalg.vector_norm(v_head))
+                if (var, pr) == ("fft", "fp32"):
+                    v_fp32 = vo
+                    head_vs_fp32 = rel * float(torch.linalg.vector_norm(v_head) / torch.linalg.vector_norm(vo))
+                elif v_fp32 is not None:
+                    rel32 = float(torch.linalg.vector_norm(vo - v_fp32) / torch.linalg.vector_norm(v_fp32))
             paths[PATH_NAMES[(var, pr)]] = {
                 "value": it_s, "unit": "RL iterations/s", "iterations": n_it,
                 "forward_ms": st_ms[0], "backward_ms": st_ms[2],
-                "rel_l2_vs_headline_after_%d_iterations" % steps: rel}
+                "rel_l2_vs_headline_after_%d_iterations" % steps: rel,
+                "rel_l2_vs_fft_fp32_after_%d_iterations" % steps: rel32}
             if var == "direct" and pr in ("bf16", "bf16x3"):
                 paths[PATH_NAMES[(var, pr)]]["tensor_roofline"] = direct_tensor_roofline(g, pr, st_ms)
-            del vo
+            if vo is not v_fp32:
+                del vo
             torch.cuda.empty_cache()
+        del v_fp32
+        torch.cuda.empty_cache()
 
     peaks, peak_src = measured_peaks()
     smax = peaks.get("sm_max_mhz", 2070.0)
@@ -504,6 +520,7 @@ def run_lfd(args, rank, world, local):
         "config": frame_config(g, prec, variant, world),
         "e2e": e2e, "e2e_volume_roundtrip": e2e_rt, "gpu_launches": launches, "clocks": clocks,
         "roofline": roof, "cpu_baseline": cpu, "paths": paths,
+        "rel_l2_vs_fft_fp32_after_%d_iterations" % steps: head_vs_fp32,
         "entropy": ent, "predicted_iteration": pred,
     }
     if rank == 0:

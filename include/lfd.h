@@ -67,7 +67,11 @@ typedef enum {
 typedef enum {
     LFD_FP32 = 0,   /* FP32 inputs and FP32 FMA accumulation on the CUDA cores   */
     LFD_TF32 = 1,   /* reserved                                                  */
-    LFD_BF16 = 2,   /* BF16 inputs on tcgen05 tensor cores, FP32 accumulation    */
+    LFD_BF16 = 2,   /* BF16 on tcgen05 tensor cores, FP32 accumulation. LFD_DIRECT:
+                       PSF and data rounded to BF16, one product per term.
+                       LFD_FFT: the PSF spectra rounded once to BF16 (4 bytes
+                       per complex value), the transformed data split hi + lo,
+                       two products per term                                     */
     LFD_BF16X3 = 3  /* split BF16: x = hi + lo, three products hi*hi + hi*lo +
                        lo*hi per term, FP32 accumulation (tensor cores)          */
 } lfd_precision;
@@ -97,7 +101,8 @@ typedef enum {
                         cores (FP32)                                                */
     LFD_FFT = 1      /* overlap-save FFT on the lenslet grid with cached PSF spectra,
                         FP32 transforms; complex contractions in FP32 on the CUDA
-                        cores (LFD_FP32) or in split BF16 on tcgen05 (LFD_BF16X3) */
+                        cores (LFD_FP32), or on tcgen05 in split BF16 (LFD_BF16X3)
+                        or with BF16 PSF spectra (LFD_BF16)                      */
 } lfd_variant;
 
 /* Fills *opt with the defaults listed above. */
@@ -303,7 +308,7 @@ lfd_status lfd_stage_times(const lfd_ctx* ctx, float* ms, int n);
 typedef struct lfd_server lfd_server;
 
 typedef struct {
-    lfd_options opt;          /* precision (LFD_BF16X3 default, or LFD_FP32), eps,
+    lfd_options opt;          /* precision (LFD_BF16X3 default, LFD_BF16 or LFD_FP32), eps,
                                  optics, XS / YS, l2_over_region, fft_size; variant
                                  is LFD_FFT; max_frames and use_graph are ignored  */
     int64_t arena_bytes;      /* device memory for frames in flight; 0 (default):

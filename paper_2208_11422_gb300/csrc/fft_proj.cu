@@ -173,6 +173,7 @@ struct OutC64 {
             if (k < n4) q[k] = make_float4(v[2 * k].x, v[2 * k].y, v[2 * k + 1].x, v[2 * k + 1].y);
     }
 };
+// (the lo planes p[1], p[3] may be null: BF16 PSF spectra keep only the hi planes)
 struct OutPlanes {
     __nv_bfloat16* p[4];
     int ntile, ld;
@@ -189,10 +190,12 @@ struct OutPlanes {
         }
         if (ld - c0 >= 8) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
+            for (int q = 0; q < 4; ++q)
+                if (p[q]) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(p[q] + o) = *reinterpret_cast<const uint2*>(h[q]);
+            for (int q = 0; q < 4; ++q)
+                if (p[q]) *reinterpret_cast<uint2*>(p[q] + o) = *reinterpret_cast<const uint2*>(h[q]);
         }
     }
 };
@@ -950,7 +953,7 @@ cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int 
 }  // namespace
 
 // ------------------------------------------------------------------ plan --
-bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, bool split_bf16) {
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, int tc_products) {
     FftPlan best{};
     double best_t = 1e300;
     for (int F : {32, 64}) {
@@ -971,16 +974,17 @@ bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, bool split_
         q.Sf = (g.S + 3) & ~3;
         q.Cw = (g.C + 7) & ~7;
         q.Sw = (g.S + 7) & ~7;
-        const double spectra = (double)q.bins * g.S * q.Cf * 8.0;
+        // complex64, split BF16 (4 planes) or BF16 (2 planes)
+        const double spectra = (double)q.bins * g.S * q.Cf * (tc_products == 2 ? 4.0 : 8.0);
         if (spectra > 96e9) continue;  // keep the cached spectra well inside HBM
-        // complex multiply-adds at 8 flops: FP32 FMA on the CUDA cores, or three
-        // BF16 tensor-core products per term (split BF16)
+        // complex multiply-adds at 8 flops: FP32 FMA on the CUDA cores, or two
+        // or three BF16 tensor-core products per term
         const double flops = (double)q.bins * g.S * q.ntile * frames * g.C * 8.0;
-        const double rate = split_bf16 ? 1.7e15 / 3.0 : 6.0e13;
+        const double rate = tc_products ? 1.7e15 / tc_products : 6.0e13;
         // transforms: one F x F patch per tile, frame and channel
         const double xform = (double)q.ntile * frames * (g.C + g.S) * 2.0 * F * F * 8.0;
         // the tensor-core contraction streams the spectra once per 64 columns
-        const double passes = split_bf16 ? (double)((q.ntile * frames + 63) / 64) : 1.0;
+        const double passes = tc_products ? (double)((q.ntile * frames + 63) / 64) : 1.0;
         const double t = std::max(spectra * passes / 6.0e12, flops / rate) + xform / 4.0e12;
         if (t < best_t) {
             best_t = t;

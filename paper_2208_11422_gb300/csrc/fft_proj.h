@@ -44,10 +44,10 @@ struct FrameCols {
 };
 
 // picks F (or uses force_F if non-zero) by a bandwidth / arithmetic cost model
-// for `frames` frames, with the contraction on the CUDA cores (FP32) or the
-// tensor cores (split_bf16); false if no plan fits (> 64 tiles, spectra too
-// large, or more than 256 phases)
-bool fft_plan_for(const Geo& g, FftPlan* p, int force_F = 0, int frames = 1, bool split_bf16 = false);
+// for `frames` frames, with the contraction on the CUDA cores (tc_products 0,
+// FP32) or the tensor cores (2: BF16 PSF spectra, 3: split BF16); false if no
+// plan fits (> 64 tiles, spectra too large, or more than 256 phases)
+bool fft_plan_for(const Geo& g, FftPlan* p, int force_F = 0, int frames = 1, int tc_products = 0);
 
 // half spectra of the packed PSF taps (W32 [T*T][Spad][Cpad]) into b.Wf or b.Wp
 cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const FftBuffers& b,

@@ -149,6 +149,11 @@ bool uses_tc(const lfd_ctx* ctx) {
            (ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3);
 }
 bool uses_lo(const lfd_ctx* ctx) { return ctx->opt.precision == LFD_BF16X3; }
+// FFT-variant contraction: tensor-core products per term (3 split BF16, 2 BF16
+// PSF spectra), 0 for FP32 on the CUDA cores
+int fft_products(const lfd_ctx* ctx) {
+    return ctx->opt.precision == LFD_BF16X3 ? 3 : ctx->opt.precision == LFD_BF16 ? 2 : 0;
+}
 
 // forward projection of Vp32[buf] (and its BF16 copies) into ctx->Fwd
 lfd_status run_forward(lfd_ctx* ctx, int buf, cudaStream_t st) {
@@ -314,8 +319,6 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         return LFD_EINVAL;
     if (!(opt.eps >= 0.f)) return LFD_EINVAL;
     if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
-    if (opt.variant == LFD_FFT && opt.precision != LFD_FP32 && opt.precision != LFD_BF16X3)
-        return LFD_EINVAL;
     if (opt.max_frames < 1 || opt.max_frames > 4096) return LFD_EINVAL;
     if (opt.fft_size != 0 && opt.fft_size != 32 && opt.fft_size != 64) return LFD_EINVAL;
     if (opt.max_frames > 1 && opt.variant != LFD_FFT) return LFD_EUNSUPPORTED;
@@ -372,8 +375,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     const bool fft = ctx->opt.variant == LFD_FFT;
     FftPlan fplan{};
     if (fft) {
-        if (!fft_plan_for(g, &fplan, ctx->opt.fft_size, ctx->opt.max_frames,
-                          ctx->opt.precision == LFD_BF16X3)) {
+        if (!fft_plan_for(g, &fplan, ctx->opt.fft_size, ctx->opt.max_frames, fft_products(ctx))) {
             ctx->err = "no FFT tiling fits this geometry (at most 64 tiles, Nnum <= 15)";
             return bail(LFD_EUNSUPPORTED);
         }
@@ -389,9 +391,10 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     const int mf = ctx->mf = fft ? ctx->opt.max_frames : 1;
     if (fft) {
         const int ncol = mf * fplan.ntile, ncolp = (ncol + 15) / 16 * 16;
-        if (ctx->opt.precision == LFD_BF16X3) {
+        if (fft_products(ctx)) {
             for (int i = 0; i < 4; ++i) {
-                CREATE_TRY(dalloc(ctx, &ctx->Wp[i], (int64_t)fplan.bins * g.S * fplan.Cw, false));
+                if (fft_products(ctx) == 3 || i % 2 == 0)  // BF16 spectra: hi planes only
+                    CREATE_TRY(dalloc(ctx, &ctx->Wp[i], (int64_t)fplan.bins * g.S * fplan.Cw, false));
                 CREATE_TRY(dalloc(ctx, &ctx->Xp[i], (int64_t)fplan.bins * ncolp * fplan.Cw, true));
                 CREATE_TRY(dalloc(ctx, &ctx->Yp[i], (int64_t)fplan.bins * ncolp * fplan.Sw, true));
             }
@@ -466,11 +469,11 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
 
     if (fft) {
         // PSF spectra, then H^T 1 by the FFT backprojection of ones
-        if (ctx->opt.precision == LFD_BF16X3) {
+        if (fft_products(ctx)) {
             int major = 0;
             CREATE_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device));
             if (major != 10) {
-                ctx->err = "the split-BF16 FFT contraction needs an sm_10x (Blackwell) device";
+                ctx->err = "the tensor-core FFT contraction needs an sm_10x (Blackwell) device";
                 return bail(LFD_EUNSUPPORTED);
             }
             CgemmBuffers cb{};

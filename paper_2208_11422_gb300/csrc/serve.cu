@@ -525,18 +525,20 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
     }
     auto ps = std::make_unique<PsfSet>();
     ps->gmax = g;
-    if (!fft_plan_for(g, &ps->plan, o.fft_size, std::max(1, s->opt.max_frames_per_set / 8),
-                      o.precision == LFD_BF16X3)) {
+    // tensor-core contraction: split BF16 (three products per term) or BF16
+    // PSF spectra (two); FP32 runs on the CUDA cores
+    const int products = o.precision == LFD_BF16X3 ? 3 : o.precision == LFD_BF16 ? 2 : 0;
+    if (!fft_plan_for(g, &ps->plan, o.fft_size, std::max(1, s->opt.max_frames_per_set / 8), products)) {
         s->err = "no FFT tiling fits this PSF / sensor shape";
         return LFD_EUNSUPPORTED;
     }
     const FftPlan& p = ps->plan;
-    const bool split = o.precision == LFD_BF16X3;
+    const bool split = products != 0;  // tensor-core planes and contraction
     if (split) {
         int major = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, s->device);
         if (major != 10) {
-            s->err = "the split-BF16 FFT contraction needs an sm_10x (Blackwell) device";
+            s->err = "the tensor-core FFT contraction needs an sm_10x (Blackwell) device";
             return LFD_EUNSUPPORTED;
         }
     }
@@ -564,7 +566,8 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
     b.ncolp = ncolp;
     if (split) {
         for (int i = 0; i < 4; ++i) {
-            ADD_CK(ps->dev(&b.Wp[i], (int64_t)p.bins * g.S * p.Cw));
+            if (products == 3 || i % 2 == 0)  // BF16 spectra: hi planes only
+                ADD_CK(ps->dev(&b.Wp[i], (int64_t)p.bins * g.S * p.Cw));
             ADD_CK(ps->dev(&b.Xp[i], (int64_t)p.bins * ncolp * p.Cw));
             ADD_CK(ps->dev(&b.Yp[i], (int64_t)p.bins * ncolp * p.Sw));
         }
@@ -643,7 +646,8 @@ lfd_status lfd_server_create(const lfd_server_options* opt_in, lfd_server** out)
     *out = nullptr;
     lfd_server_options o;
     if (opt_in) o = *opt_in; else lfd_server_default_options(&o);
-    if (o.opt.precision != LFD_FP32 && o.opt.precision != LFD_BF16X3) return LFD_EINVAL;
+    if (o.opt.precision != LFD_FP32 && o.opt.precision != LFD_BF16 && o.opt.precision != LFD_BF16X3)
+        return LFD_EINVAL;
     if (!(o.opt.eps >= 0.f)) return LFD_EINVAL;
     if (o.opt.fft_size != 0 && o.opt.fft_size != 32 && o.opt.fft_size != 64) return LFD_EINVAL;
     if (o.max_frames_per_set < 1 || o.max_frames_per_set > 1024) return LFD_EINVAL;

@@ -9,7 +9,10 @@
 //   forward  re += Wr Xr - Wi Xi,   im += Wr Xi + Wi Xr
 //   adjoint  re += Wr Yr + Wi Yi,   im += Wr Yi - Wi Yr
 // each of them in three passes hi*hi + hi*lo + lo*hi (negation through the
-// instruction descriptor). One block owns 128 output rows (phases s for the
+// instruction descriptor). With BF16 PSF spectra (no lo planes of Wf) the
+// passes are hi*hi + hi*lo: the PSF spectra are rounded once, the transformed
+// data still carry hi + lo, and the spectra stream is 4 bytes per complex
+// value instead of 8. One block owns 128 output rows (phases s for the
 // forward, channels c for the adjoint) by a chunk of 16, 32 or 64 columns
 // (frame x tile) of one bin, so a spectra tile is loaded once for up to 64
 // columns; units are ordered bin-major so the blocks working on one bin share
@@ -19,8 +22,8 @@
 // between two TMEM buffers so the drain of one chunk overlaps the next; chains
 // are cut every 64 k-blocks (1536 MMA steps) and added into the FP32 output at
 // L2 (the same rounding control as the direct projections). The spectra (all
-// of Wf, 8 bytes per complex value) are read once per projection while the
-// columns fit one chunk: the kernel is bound by HBM bandwidth.
+// of Wf) are read once per projection while the columns fit one chunk: the
+// kernel is bound by HBM bandwidth.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -40,19 +43,21 @@ constexpr int kPlaneA = 128 * 64 * 2;  // 16 KB
 constexpr int kThreads = 192;
 constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 MMA steps
 
-// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4).
-template <int NG>
+// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4). SW: the PSF
+// spectra as four planes (split BF16, three products per term); otherwise as
+// their two hi planes (BF16 spectra, two products per term: W x_hi + W x_lo).
+template <int NG, bool SW>
 struct Cg {
     static constexpr int N = 16 * NG;                        // MMA N
+    static constexpr int NA = SW ? 4 : 2;                    // PSF planes per stage
+    static constexpr int NP = SW ? 3 : 2;                    // products per term
     static constexpr int kPlaneB = N * 64 * 2;               // 2, 4 or 8 KB
-    static constexpr int kStageBytes = 4 * kPlaneA + 4 * kPlaneB;
-    static constexpr int kStages = NG == 1 ? 3 : 2;
+    static constexpr int kStageBytes = NA * kPlaneA + 4 * kPlaneB;
+    static constexpr int kStages = (232448 - 1280) / kStageBytes < 6 ? (232448 - 1280) / kStageBytes : 6;
     static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
     static constexpr uint32_t kTmemCols = 64 * NG;           // 2 buffers x (real, imag) x N
+    static_assert(kStages >= 2 && kSmemBytes <= 232448, "stage ring exceeds the shared memory of a block");
 };
-static_assert(Cg<1>::kSmemBytes <= 232448 && Cg<2>::kSmemBytes <= 232448 &&
-                  Cg<4>::kSmemBytes <= 232448,
-              "stage ring exceeds the shared memory of a block");
 
 struct CgArgs {
     int nbins;
@@ -66,16 +71,17 @@ struct CgArgs {
     int* err;
 };
 
-template <bool ADJ, int NG>
+template <bool ADJ, int NG, bool SW>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
            const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
            const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
            const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
            const CgArgs a) {
-    constexpr int kStages = Cg<NG>::kStages, kStageBytes = Cg<NG>::kStageBytes;
-    constexpr int kPlaneB = Cg<NG>::kPlaneB, N = Cg<NG>::N;
-    constexpr uint32_t kTmemCols = Cg<NG>::kTmemCols;
+    using G = Cg<NG, SW>;
+    constexpr int kStages = G::kStages, kStageBytes = G::kStageBytes;
+    constexpr int kPlaneB = G::kPlaneB, N = G::N, NA = G::NA;
+    constexpr uint32_t kTmemCols = G::kTmemCols;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -134,18 +140,19 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         break;
                     }
                     mbar_expect_tx(&full[stage], kStageBytes);
-                    const uint32_t sA = sbase + stage * kStageBytes, sB = sA + 4 * kPlaneA;
+                    const uint32_t sA = sbase + stage * kStageBytes, sB = sA + NA * kPlaneA;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < NA; ++i) {
                         if (ADJ) {  // MN-major: two 64-channel atoms of 64 phases
                             tma_3d(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage]);
                             tma_3d(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage]);
                         } else {
                             tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
-                        // 8 channels x 1 bin x N columns x 8 groups: [group][column][8]
-                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, q * N, kb * 8, &full[stage]);
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)  // 8 channels x 1 bin x N columns x 8 groups: [group][column][8]
+                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, q * N, kb * 8, &full[stage]);
                     ++issued;
                     if (++stage == kStages) {
                         stage = 0;
@@ -183,34 +190,37 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + 4 * kPlaneA;
+                        const uint32_t sA = sbase + stage * kStageBytes, sB = sA + NA * kPlaneA;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
-                            // planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo
-                            uint64_t ad[4], bd[4];
+                            // B planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo; A planes
+                            // the same (SW), or 0 real hi, 1 imag hi
+                            uint64_t ad[NA], bd[4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) {
+                            for (int i = 0; i < NA; ++i)
                                 ad[i] = ADJ ? sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024)
                                             : sdesc(sA + i * kPlaneA + ks * 32, 16, 1024);
-                                // K = 16 per MMA: groups 2ks, 2ks+1 (N x 16 B apart); the
-                                // 8-column core matrices 128 B apart
-                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 2 * N * 16, N * 16, 128);
-                            }
 #pragma unroll
-                            for (int p = 0; p < 3; ++p) {
-                                const int ia = p == 2 ? 1 : 0;  // hi, hi, lo
-                                const int ib = p == 1 ? 1 : 0;  // hi, lo, hi
+                            for (int i = 0; i < 4; ++i)  // K = 16 per MMA: groups 2ks, 2ks+1 (N x 16 B
+                                                         // apart); 8-column core matrices 128 B apart
+                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 2 * N * 16, N * 16, 128);
+#pragma unroll
+                            for (int p = 0; p < G::NP; ++p) {
+                                // SW: (hi, hi), (hi, lo), (lo, hi); else (hi, hi), (hi, lo)
+                                const int ia = (SW && p == 2) ? 1 : 0;
+                                const int ib = p == 1 ? 1 : 0;
+                                const uint64_t wr = ad[ia], wi = ad[SW ? 2 + ia : 1];
                                 const uint32_t acc0 = (first && ks == 0 && p == 0) ? 0u : 1u;
                                 if (!ADJ) {
-                                    umma_bf16(dR, ad[ia], bd[ib], id_p, acc0);          // + Wr Xr
-                                    umma_bf16(dR, ad[2 + ia], bd[2 + ib], id_n, 1u);    // - Wi Xi
-                                    umma_bf16(dI, ad[ia], bd[2 + ib], id_p, acc0);      // + Wr Xi
-                                    umma_bf16(dI, ad[2 + ia], bd[ib], id_p, 1u);        // + Wi Xr
+                                    umma_bf16(dR, wr, bd[ib], id_p, acc0);          // + Wr Xr
+                                    umma_bf16(dR, wi, bd[2 + ib], id_n, 1u);        // - Wi Xi
+                                    umma_bf16(dI, wr, bd[2 + ib], id_p, acc0);      // + Wr Xi
+                                    umma_bf16(dI, wi, bd[ib], id_p, 1u);            // + Wi Xr
                                 } else {
-                                    umma_bf16(dR, ad[ia], bd[ib], id_p, acc0);          // + Wr Yr
-                                    umma_bf16(dR, ad[2 + ia], bd[2 + ib], id_p, 1u);    // + Wi Yi
-                                    umma_bf16(dI, ad[ia], bd[2 + ib], id_p, acc0);      // + Wr Yi
-                                    umma_bf16(dI, ad[2 + ia], bd[ib], id_n, 1u);        // - Wi Yr
+                                    umma_bf16(dR, wr, bd[ib], id_p, acc0);          // + Wr Yr
+                                    umma_bf16(dR, wi, bd[2 + ib], id_p, 1u);        // + Wi Yi
+                                    umma_bf16(dI, wr, bd[2 + ib], id_p, acc0);      // + Wr Yi
+                                    umma_bf16(dI, wi, bd[ib], id_n, 1u);            // - Wi Yr
                                 }
                             }
                         }
@@ -327,20 +337,22 @@ bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bin
 constexpr int kNg[3] = {1, 2, 4};
 
 struct CgState {
-    CUtensorMap fa[4], aa[4];
+    CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (two of them without SW)
     CUtensorMap fb[3][4], ab[3][4];  // per chunk width
     CgArgs fwd, adj;
     int sm_count = 0, ncolp = 16, nwidths = 1;
+    bool sw = true;
     int* err = nullptr;
 };
 
-template <bool ADJ, int NG>
+template <bool ADJ, int NG, bool SW>
 cudaError_t launch_width(const CUtensorMap* A, const CUtensorMap* B, CgArgs a, int sm_count,
                          cudaStream_t st) {
-    a.nchunk = (a.ncol + Cg<NG>::N - 1) / Cg<NG>::N;
+    using G = Cg<NG, SW>;
+    a.nchunk = (a.ncol + G::N - 1) / G::N;
     const int grid = std::min(a.nbins * a.nchunk * a.mtiles, sm_count);
-    k_tc_cgemm<ADJ, NG><<<grid, kThreads, Cg<NG>::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
-                                                                    B[2], B[3], a);
+    k_tc_cgemm<ADJ, NG, SW><<<grid, kThreads, G::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
+                                                                   B[2], B[3], a);
     count_launch();
     return cudaGetLastError();
 }
@@ -356,20 +368,28 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     while (j + 1 < s->nwidths && kNg[j] < ncg) ++j;
     const CUtensorMap* A = ADJ ? s->aa : s->fa;
     const CUtensorMap* B = ADJ ? s->ab[j] : s->fb[j];
+    if (s->sw) {
+        switch (kNg[j]) {
+            case 1: return launch_width<ADJ, 1, true>(A, B, a, s->sm_count, st);
+            case 2: return launch_width<ADJ, 2, true>(A, B, a, s->sm_count, st);
+            default: return launch_width<ADJ, 4, true>(A, B, a, s->sm_count, st);
+        }
+    }
     switch (kNg[j]) {
-        case 1: return launch_width<ADJ, 1>(A, B, a, s->sm_count, st);
-        case 2: return launch_width<ADJ, 2>(A, B, a, s->sm_count, st);
-        default: return launch_width<ADJ, 4>(A, B, a, s->sm_count, st);
+        case 1: return launch_width<ADJ, 1, false>(A, B, a, s->sm_count, st);
+        case 2: return launch_width<ADJ, 2, false>(A, B, a, s->sm_count, st);
+        default: return launch_width<ADJ, 4, false>(A, B, a, s->sm_count, st);
     }
 }
 
-template <int NG>
+template <int NG, bool SW>
 cudaError_t set_smem() {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm<false, NG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cg<NG>::kSmemBytes);
+    constexpr int bytes = Cg<NG, SW>::kSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm<false, NG, SW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_cgemm<true, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Cg<NG>::kSmemBytes);
+    return cudaFuncSetAttribute(k_tc_cgemm<true, NG, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
 }
 
 }  // namespace
@@ -384,9 +404,12 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     if ((e = cudaMemset(s->err, 0, sizeof(int))) != cudaSuccess) return e;
     s->nwidths = 1;
     while (s->nwidths < 3 && 16 * kNg[s->nwidths] <= b.ncolp) ++s->nwidths;
+    s->sw = b.W[1] && b.W[3];
     for (int i = 0; i < 4; ++i) {
-        bool ok = map3(&s->fa[i], b.W[i], b.Cw, b.S, b.bins, 64, 128) &&
-                  map3(&s->aa[i], b.W[i], b.Cw, b.S, b.bins, 64, 64);
+        // without the lo planes the kernel's PSF planes are 0 (real hi), 2 (imag hi)
+        const __nv_bfloat16* w = s->sw ? b.W[i] : b.W[(i & 1) * 2];
+        bool ok = w && map3(&s->fa[i], w, b.Cw, b.S, b.bins, 64, 128) &&
+                  map3(&s->aa[i], w, b.Cw, b.S, b.bins, 64, 64);
         for (int j = 0; j < s->nwidths && ok; ++j)
             ok = map4_grouped(&s->fb[j][i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16 * kNg[j]) &&
                  map4_grouped(&s->ab[j][i], b.Y[i], b.Sw / 8, b.bins, b.ncolp, 16 * kNg[j]);
@@ -414,9 +437,14 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.out = b.Xout;
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
-    if ((e = set_smem<1>()) != cudaSuccess) return e;
-    if ((e = set_smem<2>()) != cudaSuccess) return e;
-    return set_smem<4>();
+    if (s->sw) {
+        if ((e = set_smem<1, true>()) != cudaSuccess) return e;
+        if ((e = set_smem<2, true>()) != cudaSuccess) return e;
+        return set_smem<4, true>();
+    }
+    if ((e = set_smem<1, false>()) != cudaSuccess) return e;
+    if ((e = set_smem<2, false>()) != cudaSuccess) return e;
+    return set_smem<4, false>();
 }
 
 cudaError_t cgemm_forward(void* state, int ncol, cudaStream_t st) {

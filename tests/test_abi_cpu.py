@@ -152,7 +152,8 @@ def test_server_rejects_bad_options_before_cuda(lib):
         srv = ctypes.c_void_p()
         assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL, kw
         assert not srv.value
-    o = lfd.lfd_server_default_options(precision="bf16")   # split BF16 or FP32 only
+    o = lfd.lfd_server_default_options()
+    o.opt.precision = lfd.LFD_TF32   # reserved: split BF16, BF16 or FP32 only
     srv = ctypes.c_void_p()
     assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL
 

@@ -100,14 +100,14 @@ def test_batch_slots_compact_as_frames_stop(prec, use_graph):
 
 # one tile per frame at this size: 20 frames take the 32-column contraction
 # chunks, 70 frames two 64-column chunks (the second one ragged)
-@pytest.mark.parametrize("nf", [20, 70])
-def test_batch_wide_column_chunks_equal_single_frames(nf):
+@pytest.mark.parametrize("nf,prec", [(20, "bf16x3"), (70, "bf16x3"), (70, "bf16")])
+def test_batch_wide_column_chunks_equal_single_frames(nf, prec):
     import torch
     from paper_2208_11422_gb300 import lfd
     n = 4
     g, psf, ys = make_frames(nf)
     dev = torch.device("cuda:0")
-    ctx = ctx_for(psf, g, "bf16x3", nf)
+    ctx = ctx_for(psf, g, prec, nf)
     try:
         assert lfd.lfd_get_fft_plan(ctx)["tiles"] == 1
         v = torch.ones((nf, g.nz, g.H, g.W), device=dev)

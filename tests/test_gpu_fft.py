@@ -2,7 +2,14 @@
 oracle through the C ABI. FP32 contractions: relative L2 <= 1e-5 per
 projection and <= 1e-4 after RL iterations. Split-BF16 tensor-core
 contractions: <= 1e-4 per projection and <= 5e-4 after RL iterations. The
-predicted iteration must equal the oracle's."""
+predicted iteration must equal the oracle's.
+
+BF16 PSF spectra (LFD_BF16): every spectrum value is rounded once to BF16,
+relative error at most 2^-9 per real component; the transforms and the
+data's hi + lo split add ~1e-6. A projection is a sum of those products, so
+its relative L2 error is bounded by 2^-9 ~ 2e-3 unless the sums cancel; the
+RL bound 1e-2 is the one of the direct path's BF16 mode. The errors are
+printed (reported per workload)."""
 import os
 
 import numpy as np
@@ -18,9 +25,10 @@ from gpu_util import Ctx, lib, rel_l2
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-TOL_PROJ = {"fp32": 1e-5, "bf16x3": 1e-4}
-TOL_RL = {"fp32": 1e-4, "bf16x3": 5e-4}
-PRECS = ["fp32", "bf16x3"]
+TOL_PROJ = {"fp32": 1e-5, "bf16x3": 1e-4, "bf16": 2e-3}
+TOL_RL = {"fp32": 1e-4, "bf16x3": 5e-4, "bf16": 1e-2}
+PRECS = ["fp32", "bf16x3", "bf16"]
+ENT_RTOL = {"fp32": 1e-5, "bf16x3": 1e-3, "bf16": 1e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,9 +76,12 @@ def test_fft_rl_config0(prec):
     with Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision=prec) as c:
         v, done, pred, ent, flux = c.rl(y, g.iterations)
         vs, done_s, pred_s, _, _ = c.rl(y, g.iterations, stop=True)
-    assert rel_l2(v, ref.v) <= TOL_RL[prec]
+    e = rel_l2(v, ref.v)
+    print("config 0 fft %s: rel-L2 %.2e, predicted %d (oracle %d)" % (prec, e, pred, ref.predicted))
+    assert e <= TOL_RL[prec]
+    assert v.min() >= 0.0
     assert pred == ref.predicted
-    np.testing.assert_allclose(ent, ref.entropy, rtol=1e-5 if prec == "fp32" else 1e-3)
+    np.testing.assert_allclose(ent, ref.entropy, rtol=ENT_RTOL[prec])
     np.testing.assert_allclose(flux, ref.flux, rtol=1e-5 if prec == "fp32" else 1e-4)
     assert done_s == pred_s == ref.predicted
 
@@ -93,7 +104,7 @@ def test_fft_rl_config1_against_stored_oracle_run(prec):
     # z-maximum turns it into a small upward bias of the MIP background, which
     # moves the entropy by up to ~1e-4 relative (measured 8e-5). The volume and
     # the predicted iteration stay within their tolerances.
-    np.testing.assert_allclose(ent, d["entropy"], rtol=2e-4 if prec == "fp32" else 1e-3)
+    np.testing.assert_allclose(ent, d["entropy"], rtol=2e-4 if prec == "fp32" else ENT_RTOL[prec])
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -115,12 +126,20 @@ def test_fft_full_size_sampled_projections(prec):
     assert ef <= TOL_PROJ[prec] and eb <= TOL_PROJ[prec]
 
 
-def test_fft_rejects_plain_bf16():
-    from paper_2208_11422_gb300 import lfd
-    g = synth.CONFIGS[0]
-    psf = synth.make_psf(0)
-    with pytest.raises(lfd.LfdError):
-        Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision="bf16")
+def test_fft_bf16_spectra_error_is_bf16_rounding_of_the_psf_spectra():
+    """The BF16 mode's error comes from the PSF spectra alone: it is well above
+    split BF16's and below the 2^-9 rounding bound."""
+    N, Ly, Lx, Nz, k = 5, 40, 40, 5, 5
+    H, W, P = Ly * N, Lx * N, k * N
+    psf = synth.random_psf(21, N, Nz, P, density=0.8)
+    v = synth.random_volume(22, Nz, H, W)
+    ref = oracle.forward(psf, N, v)
+    err = {}
+    for prec in ("bf16x3", "bf16"):
+        with Ctx(psf, N, H, W, variant="fft", precision=prec) as c:
+            err[prec] = rel_l2(c.forward(v), ref)
+    print("forward rel-L2: split BF16 %.2e, BF16 spectra %.2e" % (err["bf16x3"], err["bf16"]))
+    assert err["bf16x3"] * 10 < err["bf16"] <= 2.0 ** -9
 
 
 def test_fft_low_sensitivity_voxels_are_exact():

@@ -55,7 +55,8 @@ def make_server(lfd, prec, sets, **kw):
 # (precision, frames per set, columns per contraction): 16 columns with at most
 # 3 frames per set, or 64 columns with all of a set's frames at once (the
 # contraction then takes 32-column chunks)
-@pytest.mark.parametrize("prec,mf,mc", [("bf16x3", 3, 16), ("fp32", 3, 16), ("bf16x3", 8, 64)])
+@pytest.mark.parametrize("prec,mf,mc", [("bf16x3", 3, 16), ("fp32", 3, 16), ("bf16x3", 8, 64),
+                                        ("bf16", 8, 64)])
 def test_results_in_the_mix_equal_results_alone(prec, mf, mc):
     import torch
     from paper_2208_11422_gb300 import lfd
