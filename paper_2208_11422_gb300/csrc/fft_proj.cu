@@ -94,20 +94,28 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[N]) {
 }
 
 // A source or destination is bound to one column (one tile of one frame)
-// before a block's transforms: bind(col) returns a view whose operator()
-// takes (channel, row, column) within the tile's patch.
+// before a block's transforms: bind(col) returns a view of the tile's patch.
+// Sources give rows of a channel's patch (row(c, r), then at(row, x) for the
+// columns with col_ok(x)); destinations give output rows (row(c, i), then
+// put(row, j, value)), so per-row address arithmetic is done once per row.
 
 // patch view of a channel-major image [nch][Ly][Lx]: patch row r, column x is
 // lenslet (y0 + r, x0 + x), zero outside the grid; base == null reads an
 // all-ones image (used for H^T 1)
+struct SrcRow {
+    const float* p;  // patch column 0 of the row (valid only if ok)
+    bool ok;
+};
 struct ImgView {
     const float* base;
     int Ly, Lx, y0, x0;
-    __device__ float operator()(int c, int r, int x) const {
-        const int Iy = y0 + r, Ix = x0 + x;
-        if (Iy < 0 || Iy >= Ly || Ix < 0 || Ix >= Lx) return 0.f;
-        return base ? base[((int64_t)c * Ly + Iy) * Lx + Ix] : 1.f;
+    __device__ bool col_ok(int x) const { return (unsigned)(x0 + x) < (unsigned)Lx; }
+    __device__ SrcRow row(int c, int r) const {
+        const int Iy = y0 + r;
+        const bool ok = (unsigned)Iy < (unsigned)Ly;
+        return SrcRow{base ? base + ((int64_t)c * Ly + (ok ? Iy : 0)) * Lx + x0 : nullptr, ok};
     }
+    __device__ float at(const SrcRow& w, int x) const { return base ? w.p[x] : 1.f; }
 };
 
 // channel-major images, uniform frames; patch of tile (ty, tx) starts at
@@ -145,9 +153,11 @@ struct TapView {
     const float* W;  // at phase s
     int T;
     int64_t tap_stride;
-    __device__ float operator()(int c, int r, int x) const {
-        return (r < T && x < T) ? W[(int64_t)(r * T + x) * tap_stride + c] : 0.f;
+    __device__ bool col_ok(int x) const { return x < T; }
+    __device__ SrcRow row(int c, int r) const {
+        return SrcRow{W + (int64_t)(r < T ? r : 0) * T * tap_stride + c, r < T};
     }
+    __device__ float at(const SrcRow& w, int x) const { return w.p[(int64_t)x * tap_stride]; }
 };
 struct TapSrc {
     const float* W;
@@ -162,6 +172,24 @@ struct TapSrc {
 // put8 writes channels c0 .. c0+7 of one bin and column that lie below the
 // row length ld (c0 and ld are multiples of 4, so 4 or 8 of them) with
 // 16-byte stores (8-byte for a group of 4 in the planes).
+// BF16 planes of 8 complex values, two channels per 32-bit word (channel 2k
+// in the low half): h[0] real hi, h[1] real lo, h[2] imag hi, h[3] imag lo,
+// with hi = RN(x) and lo = RN(x - hi)
+__device__ __forceinline__ void split8(const float2 (&v)[8], uint32_t (&h)[4][4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 a = v[2 * k], b = v[2 * k + 1];
+        const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+        const float2 rb = __bfloat1622float2(rh), ib = __bfloat1622float2(ih);
+        const __nv_bfloat162 rl = __floats2bfloat162_rn(a.x - rb.x, b.x - rb.y);
+        const __nv_bfloat162 il = __floats2bfloat162_rn(a.y - ib.x, b.y - ib.y);
+        h[0][k] = *reinterpret_cast<const uint32_t*>(&rh);
+        h[1][k] = *reinterpret_cast<const uint32_t*>(&rl);
+        h[2][k] = *reinterpret_cast<const uint32_t*>(&ih);
+        h[3][k] = *reinterpret_cast<const uint32_t*>(&il);
+    }
+}
+
 struct OutC64 {
     float2* p;
     int ntile, ld;
@@ -179,23 +207,16 @@ struct OutPlanes {
     int ntile, ld;
     __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
         const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
-        __align__(16) __nv_bfloat16 h[4][8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const __nv_bfloat16 rh = __float2bfloat16_rn(v[k].x), ih = __float2bfloat16_rn(v[k].y);
-            h[0][k] = rh;
-            h[1][k] = __float2bfloat16_rn(v[k].x - __bfloat162float(rh));
-            h[2][k] = ih;
-            h[3][k] = __float2bfloat16_rn(v[k].y - __bfloat162float(ih));
-        }
+        uint32_t h[4][4];
+        split8(v, h);
         if (ld - c0 >= 8) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (p[q]) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
+                if (p[q]) *reinterpret_cast<uint4*>(p[q] + o) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (p[q]) *reinterpret_cast<uint2*>(p[q] + o) = *reinterpret_cast<const uint2*>(h[q]);
+                if (p[q]) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
         }
     }
 };
@@ -210,17 +231,11 @@ struct OutPlanesG {
     int ncolp, bins;  // columns per group, bins per column
     __device__ void put8(int bin, int col, int c0, const float2 (&v)[8]) const {
         const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8;
-        __align__(16) __nv_bfloat16 h[4][8];
+        uint32_t h[4][4];
+        split8(v, h);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const __nv_bfloat16 rh = __float2bfloat16_rn(v[k].x), ih = __float2bfloat16_rn(v[k].y);
-            h[0][k] = rh;
-            h[1][k] = __float2bfloat16_rn(v[k].x - __bfloat162float(rh));
-            h[2][k] = ih;
-            h[3][k] = __float2bfloat16_rn(v[k].y - __bfloat162float(ih));
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(p[q] + o) = *reinterpret_cast<const uint4*>(h[q]);
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(p[q] + o) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
     }
 };
 
@@ -231,9 +246,11 @@ struct OutPlanesG {
 //            along x, so the global loads are coalesced, all issued before
 //            the first store;
 //   rows:    lane l transforms rows l and l + F/2 packed as one complex row
-//            (z = p_l + i p_{l+F/2}) and separates the two half spectra;
-//   columns: lane l (1 <= l < F/2) transforms column fx = l; lane 0 packs the
-//            real columns 0 and F/2 into one complex column.
+//            (z = p_l + i p_{l+F/2}) and separates the two half spectra; the
+//            real bins fx = 0 and F/2 of a row go to slot 0 as one complex
+//            value (bin 0 real part, bin F/2 real part);
+//   columns: lane l transforms column slot l, for lane 0 the packed real
+//            columns 0 and F/2, which it separates afterwards.
 // The half spectra stay in shared memory [channel][fy or row][fx], in place.
 // Grid: x = channel group (fastest, so blocks running together fill adjacent
 // parts of the same output rows), y = column.
@@ -252,12 +269,14 @@ __global__ void __launch_bounds__(32 * FftSize<F>::R2C_WARPS, 1) k_fft_r2c(Src s
         constexpr int PS = F + 1;
         float* Pm = reinterpret_cast<float*>(R);    // [F][PS] real patch
         const bool on = c < nch;
+        const bool ok0 = on && view.col_ok(l), ok1 = on && view.col_ok(l + HF);
         {
             float t[2 * F];
 #pragma unroll
             for (int r = 0; r < F; ++r) {
-                t[2 * r] = on ? view(c, r, l) : 0.f;
-                t[2 * r + 1] = on ? view(c, r, l + HF) : 0.f;
+                const SrcRow w = view.row(on ? c : 0, r);
+                t[2 * r] = (ok0 && w.ok) ? view.at(w, l) : 0.f;
+                t[2 * r + 1] = (ok1 && w.ok) ? view.at(w, l + HF) : 0.f;
             }
 #pragma unroll
             for (int r = 0; r < F; ++r) {
@@ -271,9 +290,11 @@ __global__ void __launch_bounds__(32 * FftSize<F>::R2C_WARPS, 1) k_fft_r2c(Src s
         for (int x = 0; x < F; ++x) a[brev_c(x, LOG)] = make_float2(Pm[l * PS + x], Pm[(l + HF) * PS + x]);
         __syncwarp();  // the half spectra below overwrite the patch
         fft_reg<F, false>(a);
+        R[l * H2] = make_float2(a[0].x, a[HF].x);
+        R[(l + HF) * H2] = make_float2(a[0].y, a[HF].y);
 #pragma unroll
-        for (int k = 0; k <= HF; ++k) {
-            const float2 z = a[k], m = a[(F - k) & (F - 1)];
+        for (int k = 1; k < HF; ++k) {
+            const float2 z = a[k], m = a[F - k];
             R[l * H2 + k] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
             R[(l + HF) * H2 + k] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
         }
@@ -281,15 +302,10 @@ __global__ void __launch_bounds__(32 * FftSize<F>::R2C_WARPS, 1) k_fft_r2c(Src s
     __syncwarp();
     {
         float2 a[F];
-        if (l == 0) {
 #pragma unroll
-            for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = make_float2(R[r * H2].x, R[r * H2 + HF].x);
-        } else {
-#pragma unroll
-            for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = R[r * H2 + l];
-        }
+        for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = R[r * H2 + l];
         fft_reg<F, false>(a);
-        if (l == 0) {
+        if (l == 0) {  // slot HF is free: the rows left it unused
 #pragma unroll
             for (int fy = 0; fy < F; ++fy) {
                 const float2 z = a[fy], m = a[(F - fy) & (F - 1)];
@@ -323,13 +339,25 @@ struct HvView {
     float* rimg;       // [H][W] ratio in image layout or null
     float eps;
     int N, W, Ly, Lx, y0, x0;
-    __device__ void operator()(int s, int i, int j, float hv) const {
-        const int Iy = y0 + i, Ix = x0 + j;
-        if (Iy >= Ly || Ix >= Lx) return;
-        const int64_t pix = ((int64_t)Iy * N + s / N) * W + (int64_t)Ix * N + s % N;
+    struct Chan {
+        int64_t pix, o;  // image index (column stride N) and channel-major index of output (y0, x0)
+    };
+    struct Row {
+        int64_t pix, o;
+        bool ok;
+    };
+    __device__ Chan chan(int s) const {
+        return Chan{((int64_t)y0 * N + s / N) * W + (int64_t)x0 * N + s % N, ((int64_t)s * Ly + y0) * Lx + x0};
+    }
+    __device__ bool col_ok(int j) const { return x0 + j < Lx; }
+    __device__ Row row(const Chan& ch, int i) const {
+        return Row{ch.pix + (int64_t)i * N * W, ch.o + (int64_t)i * Lx, y0 + i < Ly};
+    }
+    __device__ void put(const Row& w, int j, float hv) const {
+        const int64_t pix = w.pix + (int64_t)j * N;
         if (img) img[pix] = hv;
         if (rcm) {
-            const int64_t o = ((int64_t)s * Ly + Iy) * Lx + Ix;
+            const int64_t o = w.o + j;
             const float den = hv + eps;
             const float r = den > 0.f ? ycm[o] / den : 0.f;
             rcm[o] = r;
@@ -373,14 +401,25 @@ struct VolView {
     float* cm;     // [C][Ly][Lx] or null
     float* stack;  // [Nz][H][W] or null
     int N, S, H, W, Ly, Lx, y0, x0;
-    __device__ void operator()(int c, int i, int j, float x) const {
-        const int Iy = y0 + i, Ix = x0 + j;
-        if (Iy >= Ly || Ix >= Lx) return;
-        if (cm) cm[((int64_t)c * Ly + Iy) * Lx + Ix] = x;
-        if (stack) {
-            const int z = c / S, t = c % S;
-            stack[((int64_t)z * H + (int64_t)Iy * N + t / N) * W + (int64_t)Ix * N + t % N] = x;
-        }
+    struct Chan {
+        int64_t cm, st;  // channel-major index and stack index (column stride N) of output (y0, x0)
+    };
+    struct Row {
+        int64_t cm, st;
+        bool ok;
+    };
+    __device__ Chan chan(int c) const {
+        const int z = c / S, t = c % S;
+        return Chan{((int64_t)c * Ly + y0) * Lx + x0,
+                    ((int64_t)z * H + (int64_t)y0 * N + t / N) * W + (int64_t)x0 * N + t % N};
+    }
+    __device__ bool col_ok(int j) const { return x0 + j < Lx; }
+    __device__ Row row(const Chan& ch, int i) const {
+        return Row{ch.cm + (int64_t)i * Lx, ch.st + (int64_t)i * N * W, y0 + i < Ly};
+    }
+    __device__ void put(const Row& w, int j, float x) const {
+        if (cm) cm[w.cm + j] = x;
+        if (stack) stack[w.st + (int64_t)j * N] = x;
     }
 };
 struct VolDst {
@@ -411,11 +450,14 @@ struct TabVolDst {
 // [off, off + B) of the real result, times `scale`, go to dst. Each channel
 // belongs to F/2 lanes of one warp:
 //   columns: lane l (1 <= l < F/2) inverse-transforms column fx = l; lane 0
-//            packs columns 0 and F/2 (whose inverses are real) into one;
+//            packs columns 0 and F/2 (whose inverses are real) into one and
+//            leaves both results in slot 0 (real part: column 0, imaginary
+//            part: column F/2);
 //   rows:    lane i < B/2 inverse-transforms output rows off+i and
 //            off+i+B/2 packed as one complex row (each row's spectrum extended
 //            by conjugate symmetry), then the outputs go through shared memory
-//            so that dst sees consecutive j across lanes.
+//            so that dst sees consecutive j across lanes, one output row at a
+//            time.
 // Grid: x = column, y = channel group.
 template <int F, class Dst>
 __global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const float2* __restrict__ in, int nch,
@@ -460,16 +502,8 @@ __global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const fl
             for (int fy = 0; fy < F; ++fy) a[brev_c(fy, LOG)] = R[fy * H2 + l];
         }
         fft_reg<F, true>(a);
-        if (l == 0) {
 #pragma unroll
-            for (int r = 0; r < F; ++r) {
-                R[r * H2] = make_float2(a[r].x, 0.f);
-                R[r * H2 + HF] = make_float2(a[r].y, 0.f);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < F; ++r) R[r * H2 + l] = a[r];
-        }
+        for (int r = 0; r < F; ++r) R[r * H2 + l] = a[r];
     }
     __syncwarp();
     const int hb = B >> 1, ob = B + 1;  // row pairs; staged row stride
@@ -479,10 +513,14 @@ __global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const fl
         if (l < hb) {
             const float2* r1 = R + (off + l) * H2;
             const float2* r2 = R + (off + l + hb) * H2;
+            const float2 p1 = r1[0], p2 = r2[0];  // (bin 0, bin F/2) of each row, both real
+            a[0] = make_float2(p1.x, p2.x);
+            a[brev_c(HF, LOG)] = make_float2(p1.y, p2.y);
 #pragma unroll
-            for (int k = 0; k < F; ++k) {
+            for (int k = 1; k < F; ++k) {
+                if (k == HF) continue;
                 float2 t1, t2;
-                if (k <= HF) {
+                if (k < HF) {
                     t1 = r1[k];
                     t2 = r2[k];
                 } else {
@@ -508,11 +546,17 @@ __global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const fl
         }
     }
     __syncwarp();
-    if (c < nch)
-        for (int e = l; e < B * B; e += HF) {
-            const int i = e / B, j = e % B;
-            view(c, i, j, O[i * ob + j]);
+    if (c < nch) {
+        // lanes take output columns j = l and l + F/2 (B < F) of one row at a time
+        const auto chn = view.chan(c);
+        const bool ok0 = l < B && view.col_ok(l), ok1 = l + HF < B && view.col_ok(l + HF);
+        for (int i = 0; i < B; ++i) {
+            const auto w = view.row(chn, i);
+            if (!w.ok) break;  // the rows below are outside the grid as well
+            if (ok0) view.put(w, l, O[i * ob + l]);
+            if (ok1) view.put(w, l + HF, O[i * ob + l + HF]);
         }
+    }
 }
 
 // forward contraction: Yh[bin][t][s] = sum_c Wf[bin][s][c] Xh[bin][t][c].
