@@ -238,9 +238,13 @@ def fft_plan_numbers(g, plan):
 # removed when that kernel changes.
 NCU_TRAFFIC = {
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward contraction"):
-        ((4.030e9 + 0.0624e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        ((4.031e9 + 0.0628e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
-        ((3.502e9 + 0.2381e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        ((3.502e9 + 0.2382e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+    ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
+        ((0.0789e9 + 0.1840e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+    ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
+        ((0.2467e9 + 0.0483e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
 
 
@@ -558,7 +562,7 @@ def run_batch(args, rank, world, local):
     y_d = torch.from_numpy(np.stack(ys)).to(dev)
     stream = torch.cuda.current_stream()
     results = {}
-    for prec in ("bf16x3", "fp32"):
+    for prec in ("bf16x3", "bf16", "fp32"):
         opt = lfd.lfd_default_options(precision=prec, variant="fft", max_frames=nf)
         best, tune_ms = lfd.lfd_autotune(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
         opt.fft_size = best
@@ -586,6 +590,9 @@ def run_batch(args, rank, world, local):
         lfd.lfd_destroy(ctx)
         del v
         torch.cuda.empty_cache()
+    for prec in ("bf16x3", "bf16"):   # frames whose stopping iteration equals the FP32 run's
+        results[prec]["stops_equal_to_fp32"] = sum(
+            int(d == e) for d, e in zip(results[prec]["iters_done"], results["fp32"]["iters_done"]))
     head = results["bf16x3"]
     out = {
         "metric": "RL frames/s, %d-frame time-lapse 615x615 px x 31 depths, PSF 165 px, each frame "
