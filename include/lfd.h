@@ -251,6 +251,16 @@ lfd_status lfd_get_geometry(const lfd_ctx* ctx, int* XS, int* YS, int* taps,
  * pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
 lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int* bins);
 
+/* Low-sensitivity voxels of an LFD_FFT context (H^T 1 below 1e-3 of its
+ * largest value), which every backprojection sums exactly over their PSF
+ * windows instead of taking the transforms' value: how many there are
+ * (n_low), how many are summed in runs along a sensor row or column (in_runs,
+ * in `runs` blocks of at most 68 voxels) and how many one warp each
+ * (single = n_low - in_runs). All 0 for an LFD_DIRECT context. Any output
+ * pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
+lfd_status lfd_get_exact_plan(const lfd_ctx* ctx, int64_t* n_low, int64_t* in_runs, int64_t* runs,
+                              int64_t* single);
+
 /* Test hooks (no counterpart in the paper).
  * lfd_debug_fail_allocs(n): the next n device allocations the library makes
  * (contexts, staging buffers, PSF sets, the serving arena) fail with

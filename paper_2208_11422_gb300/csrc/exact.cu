@@ -1,0 +1,417 @@
+// Exact backprojection of the FFT variant's low-sensitivity voxels: the
+// backprojection of Section 2.1 written out as window sums,
+//   (H^T r)[z][ip][jp] = sum_{mi, mj} r[ip - c + mi][jp - c + mj] K[mi][mj],
+// K the PSF tile of the voxel's depth and phase (ty, tx), c = (P - 1) / 2,
+// the window clipped to the sensor (zero outside).
+//
+// At the sensor's borders these voxels come in runs: a lenslet row (Iy fixed)
+// or column (Ix fixed) of one channel (z, ty, tx). A row run shares K and,
+// PSF row by PSF row, one image row. One block owns a run: for each PSF row mi
+// it stages the image-row segment the run's windows touch in shared memory
+// (zeros outside the sensor), every lane holds K[mi][lane + 32 s] in
+// registers, and voxel v adds
+//   sum_s rs[(jp_v - jp_first) + lane + 32 s] * K[mi][lane + 32 s],
+// one shared-memory load and one FMA per product, the next image row and PSF
+// row already in flight. Runs are cut into pieces of at most 24 voxels,
+// sorted by cost and dealt to a grid of one wave (block b takes pieces b,
+// b + grid, ...), so no SM is left with a long tail. A column run is a row run
+// of the transposed problem (transposed ratio image, transposed PSF tile).
+// Voxels in short runs are summed by one warp each (k_exact_bwd).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "exact.h"
+#include "fft_proj.h"
+
+namespace lfd {
+
+namespace {
+
+constexpr int kThreads = 128, kWarps = kThreads / 32;
+constexpr int kVpw = 6;                  // voxel slots per warp
+constexpr int kMaxRun = kWarps * kVpw;   // 24 voxels per piece (longer runs are split)
+constexpr int kMinRun = 8;               // shorter runs go to the one-warp-per-voxel kernel
+constexpr int kNsMax = 16;               // PSF rows up to 512 taps (ns = ceil(P / 32) <= 16)
+constexpr int kFill = 8;                 // staged row floats per thread
+constexpr int kMaxSpan = kThreads * kFill;
+
+struct ExactRun {
+    int64_t ktile;  // float offset of the run's PSF tile (psf, or psfT for a column run)
+    int orient;     // 0: along a lenslet row (positions Ix), 1: along a column (positions Iy)
+    int fixed;      // Iy (row run) or Ix (column run)
+    int pf, pp;     // phase along the fixed axis and along the run: (ty, tx) or (tx, ty)
+    int first, count;
+};
+
+// NS = ceil(P / 32) chunks of a PSF row per lane
+template <int NS>
+__device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ pos,
+                            const int64_t* __restrict__ out, const float* __restrict__ rimg,
+                            const float* __restrict__ rimgT, const float* __restrict__ psf,
+                            const float* __restrict__ psfT, const Geo& g, float* __restrict__ xcm,
+                            float* rs) {
+    const bool tr = R.orient != 0;
+    const int Hh = tr ? g.W : g.H, Ww = tr ? g.H : g.W;
+    const float* img = (tr ? rimgT : rimg) + (int64_t)f * g.H * g.W;
+    const float* K = (tr ? psfT : psf) + R.ktile;
+    const int P = g.P, c0 = (P - 1) / 2;
+    const int ip = R.fixed * g.N + R.pf;
+    const int mi0 = max(0, c0 - ip), mi1 = min(P, Hh + c0 - ip);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int jp_first = pos[R.first] * g.N + R.pp;
+    const int j0 = jp_first - c0;
+    const int span = (pos[R.first + R.count - 1] - pos[R.first]) * g.N + 32 * NS;
+    int off[kVpw];
+#pragma unroll
+    for (int k = 0; k < kVpw; ++k) {
+        const int v = warp + kWarps * k;
+        off[k] = v < R.count ? (pos[R.first + v] - pos[R.first]) * g.N : 0;
+    }
+    float acc[kVpw];
+#pragma unroll
+    for (int k = 0; k < kVpw; ++k) acc[k] = 0.f;
+
+    float nxt[kFill], knx[NS];
+    auto fetch = [&](int mi) {  // image row and PSF row mi into registers
+        const float* row = img + (int64_t)(ip - c0 + mi) * Ww;
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int e = threadIdx.x + u * kThreads, col = j0 + e;
+            nxt[u] = (e < span && col >= 0 && col < Ww) ? row[col] : 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int mj = lane + 32 * s;
+            knx[s] = mj < P ? K[(int64_t)mi * P + mj] : 0.f;
+        }
+    };
+    if (mi0 < mi1) fetch(mi0);
+    for (int mi = mi0; mi < mi1; ++mi) {
+        __syncthreads();  // the previous row's products are done
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int e = threadIdx.x + u * kThreads;
+            if (e < span) rs[e] = nxt[u];
+        }
+        float kr[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) kr[s] = knx[s];
+        __syncthreads();
+        if (mi + 1 < mi1) fetch(mi + 1);
+#pragma unroll
+        for (int k = 0; k < kVpw; ++k) {
+            if (warp + kWarps * k < R.count) {
+                const float* q = rs + off[k] + lane;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) acc[k] = fmaf(q[32 * s], kr[s], acc[k]);
+            }
+        }
+    }
+    float* x = xcm + (int64_t)f * g.C * g.Ly * g.Lx;
+#pragma unroll
+    for (int k = 0; k < kVpw; ++k) {
+        const int v = warp + kWarps * k;
+        float a = acc[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (v < R.count && lane == 0) x[out[R.first + v]] = a;
+    }
+}
+
+// pieces sorted by cost; block b of the grid takes pieces b, b + gridDim.x, ...
+template <int NS>
+__global__ void __launch_bounds__(kThreads) k_exact_runs(const ExactRun* __restrict__ runs, int nruns,
+                                                         const int* __restrict__ pos,
+                                                         const int64_t* __restrict__ out,
+                                                         const float* __restrict__ rimg,
+                                                         const float* __restrict__ rimgT,
+                                                         const float* __restrict__ psf,
+                                                         const float* __restrict__ psfT, Geo g,
+                                                         float* __restrict__ xcm) {
+    extern __shared__ float rs[];
+    for (int b = blockIdx.x; b < nruns; b += gridDim.x) {
+        const ExactRun R = runs[b];
+        exact_piece<NS>(R, blockIdx.y, pos, out, rimg, rimgT, psf, psfT, g, xcm, rs);
+        __syncthreads();  // rs is reused by the next piece
+    }
+}
+
+using RunsKernel = void (*)(const ExactRun*, int, const int*, const int64_t*, const float*, const float*,
+                            const float*, const float*, Geo, float*);
+
+template <int NS>
+RunsKernel runs_kernel_n(int ns) {
+    if constexpr (NS > kNsMax) {
+        return nullptr;
+    } else {
+        return ns == NS ? k_exact_runs<NS> : runs_kernel_n<NS + 1>(ns);
+    }
+}
+
+// dst[f][x][y] = src[f][y][x] for [nf][H][W] images, 32 x 32 tiles
+__global__ void k_transpose_images(const float* __restrict__ src, int H, int W, float* __restrict__ dst) {
+    __shared__ float t[32][33];
+    const int64_t fo = (int64_t)blockIdx.z * H * W;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int y = y0 + i, x = x0 + threadIdx.x;
+        if (y < H && x < W) t[i][threadIdx.x] = src[fo + (int64_t)y * W + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int x = x0 + i, y = y0 + threadIdx.x;
+        if (x < W && y < H) dst[fo + (int64_t)x * H + y] = t[threadIdx.x][i];
+    }
+}
+
+// psfT[j] = transpose of the P x P PSF tile of channel chan[j]
+__global__ void k_transpose_tiles(const float* __restrict__ psf, const int* __restrict__ chan, int P,
+                                  float* __restrict__ psfT) {
+    __shared__ float t[32][33];
+    const float* src = psf + (int64_t)chan[blockIdx.z] * P * P;
+    float* dst = psfT + (int64_t)blockIdx.z * P * P;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int y = y0 + i, x = x0 + threadIdx.x;
+        if (y < P && x < P) t[i][threadIdx.x] = src[(int64_t)y * P + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int x = x0 + i, y = y0 + threadIdx.x;
+        if (x < P && y < P) dst[(int64_t)x * P + y] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t plan_alloc(void** p, size_t bytes, int64_t* total) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) *total += (int64_t)bytes;
+    return e;
+}
+
+}  // namespace
+
+struct ExactPlan {
+    Geo g{};
+    int max_frames = 0;
+    const float* psf = nullptr;
+    ExactRun* runs = nullptr;
+    int nruns = 0;
+    int* pos = nullptr;
+    int64_t* out = nullptr;
+    int64_t in_runs = 0;
+    int64_t* single = nullptr;  // voxels summed one warp each
+    int64_t nsingle = 0;
+    float* psfT = nullptr;
+    float* rimgT = nullptr;
+    int span_max = 0;
+    RunsKernel kern = nullptr;
+    int slots = 0;  // resident blocks of kern on the device
+};
+
+cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const float* psf, int max_frames,
+                              cudaStream_t st, ExactPlan** out, int64_t* bytes, std::string* why) {
+    *out = nullptr;
+    ExactPlan* p = new (std::nothrow) ExactPlan();
+    if (!p) return cudaErrorMemoryAllocation;
+    p->g = g;
+    p->max_frames = max_frames;
+    p->psf = psf;
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    const int ns = (g.P + 31) / 32;
+    // run lengths along rows (c, Iy) and columns (c, Ix); each voxel joins the
+    // longer of its two runs
+    std::unordered_map<int64_t, int> nrow, ncol;
+    std::vector<int> cs(n), iys(n), ixs(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t idx = low[i];
+        cs[i] = (int)(idx / L2);
+        iys[i] = (int)((idx % L2) / g.Lx);
+        ixs[i] = (int)(idx % g.Lx);
+        ++nrow[(int64_t)cs[i] * g.Ly + iys[i]];
+        ++ncol[(int64_t)cs[i] * g.Lx + ixs[i]];
+    }
+    struct Item {
+        int orient, c, fixed, pos;
+        int64_t idx;
+    };
+    std::vector<Item> items;
+    items.reserve(n);
+    std::vector<int64_t> single;
+    const bool runs_ok = ns <= kNsMax;
+    for (int64_t i = 0; i < n; ++i) {
+        const int lr = nrow[(int64_t)cs[i] * g.Ly + iys[i]], lc = ncol[(int64_t)cs[i] * g.Lx + ixs[i]];
+        if (!runs_ok || std::max(lr, lc) < kMinRun) {
+            single.push_back(low[i]);
+            continue;
+        }
+        if (lr >= lc) items.push_back({0, cs[i], iys[i], ixs[i], low[i]});
+        else items.push_back({1, cs[i], ixs[i], iys[i], low[i]});
+    }
+    std::sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+        if (a.orient != b.orient) return a.orient < b.orient;
+        if (a.c != b.c) return a.c < b.c;
+        if (a.fixed != b.fixed) return a.fixed < b.fixed;
+        return a.pos < b.pos;
+    });
+    std::vector<ExactRun> runs;
+    std::vector<int> pos;
+    std::vector<int64_t> outs;
+    std::vector<int> tchan;                     // channels whose tile is transposed
+    std::unordered_map<int, int> tslot;
+    for (size_t a = 0; a < items.size();) {
+        size_t b = a;
+        while (b < items.size() && items[b].orient == items[a].orient && items[b].c == items[a].c &&
+               items[b].fixed == items[a].fixed)
+            ++b;
+        if (b - a < (size_t)kMinRun) {          // the voxels' other runs took the rest
+            for (size_t i = a; i < b; ++i) single.push_back(items[i].idx);
+            a = b;
+            continue;
+        }
+        const Item& h = items[a];
+        const int t = h.c % g.S, ty = t / g.N, tx = t % g.N;
+        int64_t ktile = (int64_t)h.c * g.P * g.P;
+        if (h.orient) {
+            auto it = tslot.find(h.c);
+            if (it == tslot.end()) {
+                it = tslot.emplace(h.c, (int)tchan.size()).first;
+                tchan.push_back(h.c);
+            }
+            ktile = (int64_t)it->second * g.P * g.P;
+        }
+        // pieces of at most kMaxRun voxels whose staged row segment fits
+        for (size_t s = a; s < b;) {
+            size_t e = s + 1;
+            while (e < b && (int)(e + 1 - s) <= kMaxRun &&
+                   (items[e].pos - items[s].pos) * g.N + 32 * ns <= kMaxSpan)
+                ++e;
+            ExactRun r{};
+            r.ktile = ktile;
+            r.orient = h.orient;
+            r.fixed = h.fixed;
+            r.pf = h.orient ? tx : ty;
+            r.pp = h.orient ? ty : tx;
+            r.first = (int)pos.size();
+            r.count = (int)(e - s);
+            for (size_t i = s; i < e; ++i) {
+                pos.push_back(items[i].pos);
+                outs.push_back(items[i].idx);
+            }
+            p->span_max = std::max(p->span_max, (items[e - 1].pos - items[s].pos) * g.N + 32 * ns);
+            runs.push_back(r);
+            s = e;
+        }
+        a = b;
+    }
+    std::sort(single.begin(), single.end());
+    // costliest pieces first (voxels x PSF rows inside the sensor), so that the
+    // grid's block-stride deal ends evenly
+    auto cost = [&](const ExactRun& r) {
+        const int ip = r.fixed * g.N + r.pf, c0 = (g.P - 1) / 2, Hh = r.orient ? g.W : g.H;
+        return (int64_t)r.count * std::max(0, std::min(g.P, Hh + c0 - ip) - std::max(0, c0 - ip));
+    };
+    std::stable_sort(runs.begin(), runs.end(),
+                     [&](const ExactRun& a, const ExactRun& b) { return cost(a) > cost(b); });
+    p->nruns = (int)runs.size();
+    p->in_runs = (int64_t)pos.size();
+    p->nsingle = (int64_t)single.size();
+    int64_t total = 0;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](const char* what) {
+        if (why) *why = std::string("exact correction plan: ") + what + ": " + cudaGetErrorString(e);
+        *bytes += total;
+        *out = p;  // the caller destroys it
+        return e;
+    };
+    if (p->nruns) {
+        if ((e = plan_alloc((void**)&p->runs, sizeof(ExactRun) * runs.size(), &total)) != cudaSuccess ||
+            (e = plan_alloc((void**)&p->pos, sizeof(int) * pos.size(), &total)) != cudaSuccess ||
+            (e = plan_alloc((void**)&p->out, sizeof(int64_t) * outs.size(), &total)) != cudaSuccess)
+            return fail("allocation");
+        if ((e = cudaMemcpyAsync(p->runs, runs.data(), sizeof(ExactRun) * runs.size(), cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(p->pos, pos.data(), sizeof(int) * pos.size(), cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(p->out, outs.data(), sizeof(int64_t) * outs.size(), cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess)
+            return fail("upload");
+        p->kern = runs_kernel_n<1>(ns);
+        int per_sm = 0, dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, kThreads,
+                                                               sizeof(float) * p->span_max)) != cudaSuccess)
+            return fail("occupancy query");
+        p->slots = std::max(1, per_sm * sms);
+    }
+    if (!tchan.empty()) {
+        int* dchan = nullptr;
+        if ((e = plan_alloc((void**)&p->psfT, sizeof(float) * tchan.size() * g.P * g.P, &total)) != cudaSuccess ||
+            (e = plan_alloc((void**)&p->rimgT, sizeof(float) * max_frames * (size_t)g.H * g.W, &total)) !=
+                cudaSuccess)
+            return fail("allocation");
+        if ((e = cudaMalloc((void**)&dchan, sizeof(int) * tchan.size())) != cudaSuccess) return fail("allocation");
+        e = cudaMemcpyAsync(dchan, tchan.data(), sizeof(int) * tchan.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            const dim3 grid((g.P + 31) / 32, (g.P + 31) / 32, (unsigned)tchan.size());
+            k_transpose_tiles<<<grid, dim3(32, 8), 0, st>>>(psf, dchan, g.P, p->psfT);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dchan);
+        if (e != cudaSuccess) return fail("PSF tile transpose");
+    }
+    if (p->nsingle) {
+        if ((e = plan_alloc((void**)&p->single, sizeof(int64_t) * single.size(), &total)) != cudaSuccess)
+            return fail("allocation");
+        if ((e = cudaMemcpyAsync(p->single, single.data(), sizeof(int64_t) * single.size(),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return fail("upload");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail("upload");
+    *bytes += total;
+    *out = p;
+    return cudaSuccess;
+}
+
+cudaError_t exact_bwd(ExactPlan* p, int nf, const float* rimg, float* xcm, cudaStream_t st) {
+    if (!p || nf <= 0) return cudaSuccess;
+    if (nf > p->max_frames) return cudaErrorInvalidValue;
+    const Geo& g = p->g;
+    if (p->rimgT) {
+        const dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, (unsigned)nf);
+        k_transpose_images<<<grid, dim3(32, 8), 0, st>>>(rimg, g.H, g.W, p->rimgT);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (p->nruns) {
+        const int gx = std::min(p->nruns, std::max(1, p->slots / nf));
+        p->kern<<<dim3((unsigned)gx, (unsigned)nf), kThreads, sizeof(float) * p->span_max, st>>>(
+            p->runs, p->nruns, p->pos, p->out, rimg, p->rimgT, p->psf, p->psfT, g, xcm);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_exact_bwd(p->single, p->nsingle, nf, rimg, p->psf, g, xcm, st);
+}
+
+void exact_plan_counts(const ExactPlan* p, int64_t* in_runs, int64_t* runs, int64_t* single) {
+    if (in_runs) *in_runs = p ? p->in_runs : 0;
+    if (runs) *runs = p ? p->nruns : 0;
+    if (single) *single = p ? p->nsingle : 0;
+}
+
+void exact_plan_destroy(ExactPlan* p) {
+    if (!p) return;
+    void* ptrs[] = {p->runs, p->pos, p->out, p->single, p->psfT, p->rimgT};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+}  // namespace lfd

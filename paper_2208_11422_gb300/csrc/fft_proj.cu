@@ -746,7 +746,7 @@ __device__ float exact_bwd_voxel(int64_t idx, const float* __restrict__ rimg,
     const float* rr = rimg ? rimg + (int64_t)(ip - c0) * g.W + (jp - c0) : nullptr;
     float acc = 0.f;
     if (act) {
-#pragma unroll 2
+#pragma unroll 4
         for (int mi = mi0 + dr; mi < mi1; mi += rps) {
             const float* kk = K + (int64_t)mi * g.P;
             if (rr) {

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lfd_internal.h"
+#include "exact.h"
 #include "fft_proj.h"
 #include "tc_cgemm.h"
 #include "tc_gemm.h"
@@ -204,11 +205,13 @@ void free_all(lfd_ctx* ctx) {
                     ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
                     ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
                     ctx->Wf, ctx->Xh, ctx->Yh, ctx->Vcm[0], ctx->Vcm[1], ctx->Rcm, ctx->Xcm,
-                    ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg, ctx->low_list,
+                    ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg,
                     ctx->Wp[0], ctx->Wp[1], ctx->Wp[2], ctx->Wp[3], ctx->Xp[0], ctx->Xp[1],
                     ctx->Xp[2], ctx->Xp[3], ctx->Yp[0], ctx->Yp[1], ctx->Yp[2], ctx->Yp[3]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    exact_plan_destroy(ctx->exact);
+    ctx->exact = nullptr;
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
     if (ctx->host_pinned_slots) cudaFreeHost(ctx->host_pinned_slots);
@@ -520,13 +523,16 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
                 if (!(h[i] >= thr)) low.push_back(i);
             ctx->n_low = (int64_t)low.size();
             if (ctx->n_low > 0) {
-                CREATE_TRY(dalloc(ctx, &ctx->low_list, ctx->n_low, false));
-                CREATE_CK(cudaMemcpyAsync(ctx->low_list, low.data(), ctx->n_low * sizeof(int64_t),
-                                          cudaMemcpyHostToDevice, st));
+                std::string why2;
+                const cudaError_t pe = exact_plan_create(low.data(), ctx->n_low, g, ctx->psf_dev, mf, st,
+                                                         &ctx->exact, &ctx->device_bytes, &why2);
+                if (pe != cudaSuccess) {
+                    ctx->err = why2;
+                    return bail(pe == cudaErrorMemoryAllocation ? LFD_ENOMEM : LFD_ECUDA);
+                }
                 CREATE_TRY(ensure_stage(ctx, false));
                 CREATE_CK(launch_fill(ctx->stage_img, (int64_t)g.H * g.W, 1.0f, st));
-                CREATE_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, 1, ctx->stage_img, ctx->psf_dev, g,
-                                           ctx->Xcm, st));
+                CREATE_CK(exact_bwd(ctx->exact, 1, ctx->stage_img, ctx->Xcm, st));
             }
         }
         CREATE_CK(launch_inv_cm(ctx->Xcm, (int64_t)g.C * L2, ctx->invcm, st));
@@ -589,6 +595,14 @@ lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int*
     if (B) *B = fp ? fp->B : 0;
     if (tiles) *tiles = fp ? fp->ntile : 0;
     if (bins) *bins = fp ? fp->bins : 0;
+    return LFD_OK;
+}
+
+lfd_status lfd_get_exact_plan(const lfd_ctx* ctx, int64_t* n_low, int64_t* in_runs, int64_t* runs,
+                              int64_t* single) {
+    if (!ctx) return LFD_EINVAL;
+    if (n_low) *n_low = ctx->exact ? ctx->n_low : 0;
+    exact_plan_counts(ctx->exact, in_runs, runs, single);
     return LFD_OK;
 }
 
@@ -655,7 +669,7 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_image_cm(rd, g, ctx->Rcm, st));
         LFD_CK(fft_backward(fp, g, fbufs(ctx), 1, ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
-        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, 1, rd, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(exact_bwd(ctx->exact, 1, rd, ctx->Xcm, st));
         LFD_CK(launch_depoly_volume_cm(ctx->Xcm, g, vd, st));
     } else {
         LFD_CK(launch_poly_image(rd, g, ctx->Rp32, g.m_base, ctx->Rpb[0], ctx->Rpb[1], st));
@@ -706,7 +720,7 @@ lfd_status iter_body(lfd_ctx* ctx, int nf, int cur, cudaStream_t st, cudaEvent_t
         LFD_CK(mark(3));
         LFD_CK(fft_backward(*fp, g, fb, nf, ctx->Rcm, ctx->Xcm, nullptr, st, e9 ? e9 + 4 : nullptr));
         LFD_CK(mark(6));
-        LFD_CK(launch_exact_bwd(ctx->low_list, ctx->n_low, nf, ctx->rimg, ctx->psf_dev, g, ctx->Xcm, st));
+        LFD_CK(exact_bwd(ctx->exact, nf, ctx->rimg, ctx->Xcm, st));
         LFD_CK(mark(7));
         LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, nf, ctx->mip,
                                 ctx->flux_part, st));

@@ -75,6 +75,8 @@ struct StageTimes {
     int64_t count = 0;
 };
 
+struct ExactPlan;  // exact.h
+
 }  // namespace lfd
 
 struct lfd_ctx {
@@ -144,7 +146,7 @@ struct lfd_ctx {
     int nflux = 0;               // flux partials written per update
     float* psf_dev = nullptr;    // original PSF [Nz][N][N][P][P] (FFT variant)
     float* rimg = nullptr;       // ratio image [H][W] (FFT variant)
-    int64_t* low_list = nullptr; // voxels backprojected exactly (FFT variant)
+    lfd::ExactPlan* exact = nullptr;  // voxels backprojected exactly (FFT variant)
     int64_t n_low = 0;
 };
 

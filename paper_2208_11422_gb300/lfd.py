@@ -119,6 +119,7 @@ _SIGS = {
                               ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)]),
     "lfd_get_fft_plan": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
+    "lfd_get_exact_plan": (_I, [_VP] + [ctypes.POINTER(ctypes.c_int64)] * 4),
     "lfd_launch_count": (ctypes.c_uint64, []),
     "lfd_debug_fail_allocs": (None, [_I]),
     "lfd_selftest_bounded_wait": (_I, [ctypes.c_int64, ctypes.POINTER(_I)]),
@@ -320,6 +321,12 @@ def lfd_get_fft_plan(ctx) -> dict:
     _check(load().lfd_get_fft_plan(ctx, ctypes.byref(F), ctypes.byref(B), ctypes.byref(nt),
                                    ctypes.byref(bins)), ctx)
     return {"F": F.value, "B": B.value, "tiles": nt.value, "bins": bins.value}
+
+
+def lfd_get_exact_plan(ctx) -> dict:
+    v = [ctypes.c_int64(0) for _ in range(4)]
+    _check(load().lfd_get_exact_plan(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return dict(zip(("n_low", "in_runs", "runs", "single"), (x.value for x in v)))
 
 
 def lfd_debug_fail_allocs(n: int):

@@ -76,6 +76,7 @@ def test_null_context_calls(lib):
     assert lib.lfd_forward(None, None, None, None) == lfd.LFD_EINVAL
     assert lib.lfd_backward(None, None, None, None) == lfd.LFD_EINVAL
     assert lib.lfd_rl_iterate(None, None, None, 1, 0, None, None, None, None, None) == lfd.LFD_EINVAL
+    assert lib.lfd_get_exact_plan(None, None, None, None, None) == lfd.LFD_EINVAL
     lib.lfd_destroy(None)
     assert lfd.lfd_status_string(lfd.LFD_EINVAL) == "LFD_EINVAL"
 

@@ -159,6 +159,29 @@ def test_fft_low_sensitivity_voxels_are_exact():
     np.testing.assert_allclose(got, ref, rtol=1e-4)
 
 
+def test_fft_exact_correction_of_a_ratio_image():
+    """The exact sums for a non-constant image, at low-sensitivity voxels of the
+    2025 px frame summed along a sensor row, along a column (transposed image
+    and PSF tile) and one warp per voxel (short runs near the corners)."""
+    g = synth.CONFIGS[2]
+    psf = synth.make_psf(2)
+    r = synth.random_image(11, g.H, g.W, 0.5, 1.5)
+    vox = np.array([[49, 0, 1225], [46, 0, 798], [50, 0, 376], [50, 0, 1485],        # row runs
+                    [46, 184, 0], [47, 1746, 0], [47, 1400, 2024], [50, 1828, 0],   # column runs
+                    [0, 1969, 2010], [0, 2015, 14], [0, 1965, 2010], [1, 1983, 14]], np.int32)
+    from paper_2208_11422_gb300 import lfd
+    with Ctx(psf, g.nnum, g.H, g.W, variant="fft") as c:
+        ht = c.backward(r)
+        plan = lfd.lfd_get_exact_plan(c.ctx)
+    print("exact plan:", plan)
+    assert plan["in_runs"] + plan["single"] == plan["n_low"] > 40000
+    assert plan["in_runs"] > 0.8 * plan["n_low"]
+    ref = oracle.backward_at(psf, g.nnum, r, vox)
+    got = ht[vox[:, 0], vox[:, 1], vox[:, 2]]
+    print("H^T r at low-sensitivity voxels:", list(zip(ref, got)))
+    np.testing.assert_allclose(got, ref, rtol=1e-4)
+
+
 def test_fft_rl_full_size_agrees_with_split_bf16():
     """Five RL iterations on the 2025 px workload: the FFT variant and the split
     BF16 tensor-core path (both validated per projection against the oracle)
