@@ -6,17 +6,19 @@
 //
 // At the sensor's borders these voxels come in runs: a lenslet row (Iy fixed)
 // or column (Ix fixed) of one channel (z, ty, tx). A row run shares K and,
-// PSF row by PSF row, one image row. One block owns a run: for each PSF row mi
-// it stages the image-row segment the run's windows touch in shared memory
-// (zeros outside the sensor), every lane holds K[mi][lane + 32 s] in
-// registers, and voxel v adds
+// PSF row by PSF row, one image row. A block (or a warp) owns a piece of a
+// run: for each PSF row mi it stages the image-row segment the piece's
+// windows touch in shared memory (zeros outside the sensor), every lane holds
+// K[mi][lane + 32 s] in registers, and voxel v adds
 //   sum_s rs[(jp_v - jp_first) + lane + 32 s] * K[mi][lane + 32 s],
 // one shared-memory load and one FMA per product, the next image row and PSF
-// row already in flight. Runs are cut into pieces of at most 24 voxels,
-// sorted by cost and dealt to a grid of one wave (block b takes pieces b,
-// b + grid, ...), so no SM is left with a long tail. A column run is a row run
-// of the transposed problem (transposed ratio image, transposed PSF tile).
-// Voxels in short runs are summed by one warp each (k_exact_bwd).
+// row already in flight. Runs of 8 or more voxels are cut into pieces of at
+// most 24 voxels on four warps; shorter runs and lone voxels are pieces of one
+// warp. Pieces are sorted by cost and dealt to a grid of one wave (block b
+// takes pieces b, b + grid, ...), so no SM is left with a long tail. A column
+// run is a row run of the transposed problem (transposed ratio image,
+// transposed PSF tile). PSF rows wider than 512 taps take the
+// one-warp-per-voxel kernel (k_exact_bwd).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -30,13 +32,14 @@ namespace lfd {
 
 namespace {
 
-constexpr int kThreads = 128, kWarps = kThreads / 32;
-constexpr int kVpw = 6;                  // voxel slots per warp
-constexpr int kMaxRun = kWarps * kVpw;   // 24 voxels per piece (longer runs are split)
-constexpr int kMinRun = 8;               // shorter runs go to the one-warp-per-voxel kernel
+// long runs (>= kMinLong voxels): pieces of at most kLongWarps * kLongVpw
+// voxels on kLongWarps warps; short runs and single voxels: one warp each
+constexpr int kLongWarps = 4, kLongVpw = 6, kMaxPiece = kLongWarps * kLongVpw;  // 24 voxels
+constexpr int kMinLong = 8;
+constexpr int kShortVpw = kMinLong - 1;
 constexpr int kNsMax = 16;               // PSF rows up to 512 taps (ns = ceil(P / 32) <= 16)
-constexpr int kFill = 8;                 // staged row floats per thread
-constexpr int kMaxSpan = kThreads * kFill;
+constexpr int kLongFill = 8, kShortFill = 16;  // image-row floats per thread
+constexpr int kLongSpan = 32 * kLongWarps * kLongFill, kShortSpan = 32 * kShortFill;
 
 struct ExactRun {
     int64_t ktile;  // float offset of the run's PSF tile (psf, or psfT for a column run)
@@ -46,13 +49,23 @@ struct ExactRun {
     int first, count;
 };
 
-// NS = ceil(P / 32) chunks of a PSF row per lane
-template <int NS>
+template <int WARPS>
+__device__ __forceinline__ void piece_sync() {
+    if constexpr (WARPS == 1) __syncwarp();
+    else __syncthreads();
+}
+
+// One piece of a run with WARPS warps, VPW voxel slots per warp, NS =
+// ceil(P / 32) chunks of a PSF row per lane, and image-row segments of up to
+// 32 WARPS FILL floats. The next PSF row and image row are loaded into
+// registers while the current one is summed.
+template <int NS, int WARPS, int VPW, int FILL>
 __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ pos,
                             const int64_t* __restrict__ out, const float* __restrict__ rimg,
                             const float* __restrict__ rimgT, const float* __restrict__ psf,
                             const float* __restrict__ psfT, const Geo& g, float* __restrict__ xcm,
                             float* rs) {
+    constexpr int T = 32 * WARPS;
     const bool tr = R.orient != 0;
     const int Hh = tr ? g.W : g.H, Ww = tr ? g.H : g.W;
     const float* img = (tr ? rimgT : rimg) + (int64_t)f * g.H * g.W;
@@ -61,25 +74,24 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
     const int ip = R.fixed * g.N + R.pf;
     const int mi0 = max(0, c0 - ip), mi1 = min(P, Hh + c0 - ip);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int jp_first = pos[R.first] * g.N + R.pp;
-    const int j0 = jp_first - c0;
+    const int j0 = pos[R.first] * g.N + R.pp - c0;
     const int span = (pos[R.first + R.count - 1] - pos[R.first]) * g.N + 32 * NS;
-    int off[kVpw];
+    int off[VPW];
 #pragma unroll
-    for (int k = 0; k < kVpw; ++k) {
-        const int v = warp + kWarps * k;
+    for (int k = 0; k < VPW; ++k) {
+        const int v = warp + WARPS * k;
         off[k] = v < R.count ? (pos[R.first + v] - pos[R.first]) * g.N : 0;
     }
-    float acc[kVpw];
+    float acc[VPW];
 #pragma unroll
-    for (int k = 0; k < kVpw; ++k) acc[k] = 0.f;
+    for (int k = 0; k < VPW; ++k) acc[k] = 0.f;
 
-    float nxt[kFill], knx[NS];
+    float nxt[FILL], knx[NS];
     auto fetch = [&](int mi) {  // image row and PSF row mi into registers
         const float* row = img + (int64_t)(ip - c0 + mi) * Ww;
 #pragma unroll
-        for (int u = 0; u < kFill; ++u) {
-            const int e = threadIdx.x + u * kThreads, col = j0 + e;
+        for (int u = 0; u < FILL; ++u) {
+            const int e = threadIdx.x + u * T, col = j0 + e;
             nxt[u] = (e < span && col >= 0 && col < Ww) ? row[col] : 0.f;
         }
 #pragma unroll
@@ -90,20 +102,20 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
     };
     if (mi0 < mi1) fetch(mi0);
     for (int mi = mi0; mi < mi1; ++mi) {
-        __syncthreads();  // the previous row's products are done
+        piece_sync<WARPS>();  // the previous row's products are done
 #pragma unroll
-        for (int u = 0; u < kFill; ++u) {
-            const int e = threadIdx.x + u * kThreads;
+        for (int u = 0; u < FILL; ++u) {
+            const int e = threadIdx.x + u * T;
             if (e < span) rs[e] = nxt[u];
         }
         float kr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) kr[s] = knx[s];
-        __syncthreads();
+        piece_sync<WARPS>();
         if (mi + 1 < mi1) fetch(mi + 1);
 #pragma unroll
-        for (int k = 0; k < kVpw; ++k) {
-            if (warp + kWarps * k < R.count) {
+        for (int k = 0; k < VPW; ++k) {
+            if (warp + WARPS * k < R.count) {
                 const float* q = rs + off[k] + lane;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) acc[k] = fmaf(q[32 * s], kr[s], acc[k]);
@@ -112,8 +124,8 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
     }
     float* x = xcm + (int64_t)f * g.C * g.Ly * g.Lx;
 #pragma unroll
-    for (int k = 0; k < kVpw; ++k) {
-        const int v = warp + kWarps * k;
+    for (int k = 0; k < VPW; ++k) {
+        const int v = warp + WARPS * k;
         float a = acc[k];
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (v < R.count && lane == 0) x[out[R.first + v]] = a;
@@ -121,32 +133,32 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
 }
 
 // pieces sorted by cost; block b of the grid takes pieces b, b + gridDim.x, ...
-template <int NS>
-__global__ void __launch_bounds__(kThreads) k_exact_runs(const ExactRun* __restrict__ runs, int nruns,
-                                                         const int* __restrict__ pos,
-                                                         const int64_t* __restrict__ out,
-                                                         const float* __restrict__ rimg,
-                                                         const float* __restrict__ rimgT,
-                                                         const float* __restrict__ psf,
-                                                         const float* __restrict__ psfT, Geo g,
-                                                         float* __restrict__ xcm) {
+template <int NS, int WARPS, int VPW, int FILL>
+__global__ void __launch_bounds__(32 * WARPS) k_exact_runs(const ExactRun* __restrict__ runs, int nruns,
+                                                           const int* __restrict__ pos,
+                                                           const int64_t* __restrict__ out,
+                                                           const float* __restrict__ rimg,
+                                                           const float* __restrict__ rimgT,
+                                                           const float* __restrict__ psf,
+                                                           const float* __restrict__ psfT, Geo g,
+                                                           float* __restrict__ xcm) {
     extern __shared__ float rs[];
     for (int b = blockIdx.x; b < nruns; b += gridDim.x) {
         const ExactRun R = runs[b];
-        exact_piece<NS>(R, blockIdx.y, pos, out, rimg, rimgT, psf, psfT, g, xcm, rs);
-        __syncthreads();  // rs is reused by the next piece
+        exact_piece<NS, WARPS, VPW, FILL>(R, blockIdx.y, pos, out, rimg, rimgT, psf, psfT, g, xcm, rs);
+        piece_sync<WARPS>();  // rs is reused by the next piece
     }
 }
 
 using RunsKernel = void (*)(const ExactRun*, int, const int*, const int64_t*, const float*, const float*,
                             const float*, const float*, Geo, float*);
 
-template <int NS>
+template <int NS, int WARPS, int VPW, int FILL>
 RunsKernel runs_kernel_n(int ns) {
     if constexpr (NS > kNsMax) {
         return nullptr;
     } else {
-        return ns == NS ? k_exact_runs<NS> : runs_kernel_n<NS + 1>(ns);
+        return ns == NS ? k_exact_runs<NS, WARPS, VPW, FILL> : runs_kernel_n<NS + 1, WARPS, VPW, FILL>(ns);
     }
 }
 
@@ -197,19 +209,32 @@ struct ExactPlan {
     Geo g{};
     int max_frames = 0;
     const float* psf = nullptr;
-    ExactRun* runs = nullptr;
-    int nruns = 0;
+    ExactRun* runs = nullptr;   // the long pieces, then the short ones
+    int nlong = 0, nshort = 0;
     int* pos = nullptr;
     int64_t* out = nullptr;
     int64_t in_runs = 0;
-    int64_t* single = nullptr;  // voxels summed one warp each
+    int64_t* single = nullptr;  // voxels summed one warp each (PSF rows over 512 taps)
     int64_t nsingle = 0;
     float* psfT = nullptr;
     float* rimgT = nullptr;
-    int span_max = 0;
-    RunsKernel kern = nullptr;
-    int slots = 0;  // resident blocks of kern on the device
+    int span_long = 0, span_short = 0;  // largest staged image row of a piece
+    RunsKernel kern_long = nullptr, kern_short = nullptr;
+    int slots_long = 0, slots_short = 0;  // resident blocks on the device
 };
+
+namespace {
+cudaError_t slots_for(RunsKernel k, int threads, size_t smem, int* slots) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem)) != cudaSuccess)
+        return e;
+    *slots = std::max(1, per_sm * sms);
+    return cudaSuccess;
+}
+}  // namespace
 
 cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const float* psf, int max_frames,
                               cudaStream_t st, ExactPlan** out, int64_t* bytes, std::string* why) {
@@ -240,10 +265,10 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
     std::vector<Item> items;
     items.reserve(n);
     std::vector<int64_t> single;
-    const bool runs_ok = ns <= kNsMax;
+    const bool runs_ok = ns <= kNsMax;  // else every voxel takes the one-warp-per-voxel kernel
     for (int64_t i = 0; i < n; ++i) {
         const int lr = nrow[(int64_t)cs[i] * g.Ly + iys[i]], lc = ncol[(int64_t)cs[i] * g.Lx + ixs[i]];
-        if (!runs_ok || std::max(lr, lc) < kMinRun) {
+        if (!runs_ok) {
             single.push_back(low[i]);
             continue;
         }
@@ -256,7 +281,7 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         if (a.fixed != b.fixed) return a.fixed < b.fixed;
         return a.pos < b.pos;
     });
-    std::vector<ExactRun> runs;
+    std::vector<ExactRun> runs, shorts;
     std::vector<int> pos;
     std::vector<int64_t> outs;
     std::vector<int> tchan;                     // channels whose tile is transposed
@@ -266,11 +291,7 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         while (b < items.size() && items[b].orient == items[a].orient && items[b].c == items[a].c &&
                items[b].fixed == items[a].fixed)
             ++b;
-        if (b - a < (size_t)kMinRun) {          // the voxels' other runs took the rest
-            for (size_t i = a; i < b; ++i) single.push_back(items[i].idx);
-            a = b;
-            continue;
-        }
+        const bool is_long = b - a >= (size_t)kMinLong;
         const Item& h = items[a];
         const int t = h.c % g.S, ty = t / g.N, tx = t % g.N;
         int64_t ktile = (int64_t)h.c * g.P * g.P;
@@ -282,11 +303,13 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
             }
             ktile = (int64_t)it->second * g.P * g.P;
         }
-        // pieces of at most kMaxRun voxels whose staged row segment fits
+        // pieces of at most kMaxPiece (long) or kShortVpw (short) voxels
+        // whose staged row segment fits
+        const size_t cap = is_long ? kMaxPiece : kShortVpw;
+        const int span_cap = is_long ? kLongSpan : kShortSpan;
         for (size_t s = a; s < b;) {
             size_t e = s + 1;
-            while (e < b && (int)(e + 1 - s) <= kMaxRun &&
-                   (items[e].pos - items[s].pos) * g.N + 32 * ns <= kMaxSpan)
+            while (e < b && e + 1 - s <= cap && (items[e].pos - items[s].pos) * g.N + 32 * ns <= span_cap)
                 ++e;
             ExactRun r{};
             r.ktile = ktile;
@@ -300,8 +323,10 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
                 pos.push_back(items[i].pos);
                 outs.push_back(items[i].idx);
             }
-            p->span_max = std::max(p->span_max, (items[e - 1].pos - items[s].pos) * g.N + 32 * ns);
-            runs.push_back(r);
+            const int span = (items[e - 1].pos - items[s].pos) * g.N + 32 * ns;
+            int& sm = is_long ? p->span_long : p->span_short;
+            sm = std::max(sm, span);
+            (is_long ? runs : shorts).push_back(r);
             s = e;
         }
         a = b;
@@ -313,9 +338,12 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         const int ip = r.fixed * g.N + r.pf, c0 = (g.P - 1) / 2, Hh = r.orient ? g.W : g.H;
         return (int64_t)r.count * std::max(0, std::min(g.P, Hh + c0 - ip) - std::max(0, c0 - ip));
     };
-    std::stable_sort(runs.begin(), runs.end(),
-                     [&](const ExactRun& a, const ExactRun& b) { return cost(a) > cost(b); });
-    p->nruns = (int)runs.size();
+    auto by_cost = [&](const ExactRun& a, const ExactRun& b) { return cost(a) > cost(b); };
+    std::stable_sort(runs.begin(), runs.end(), by_cost);
+    std::stable_sort(shorts.begin(), shorts.end(), by_cost);
+    p->nlong = (int)runs.size();
+    p->nshort = (int)shorts.size();
+    runs.insert(runs.end(), shorts.begin(), shorts.end());
     p->in_runs = (int64_t)pos.size();
     p->nsingle = (int64_t)single.size();
     int64_t total = 0;
@@ -326,7 +354,7 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         *out = p;  // the caller destroys it
         return e;
     };
-    if (p->nruns) {
+    if (!runs.empty()) {
         if ((e = plan_alloc((void**)&p->runs, sizeof(ExactRun) * runs.size(), &total)) != cudaSuccess ||
             (e = plan_alloc((void**)&p->pos, sizeof(int) * pos.size(), &total)) != cudaSuccess ||
             (e = plan_alloc((void**)&p->out, sizeof(int64_t) * outs.size(), &total)) != cudaSuccess)
@@ -338,14 +366,13 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
             (e = cudaMemcpyAsync(p->out, outs.data(), sizeof(int64_t) * outs.size(), cudaMemcpyHostToDevice,
                                  st)) != cudaSuccess)
             return fail("upload");
-        p->kern = runs_kernel_n<1>(ns);
-        int per_sm = 0, dev = 0, sms = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, kThreads,
-                                                               sizeof(float) * p->span_max)) != cudaSuccess)
+        p->kern_long = runs_kernel_n<1, kLongWarps, kLongVpw, kLongFill>(ns);
+        p->kern_short = runs_kernel_n<1, 1, kShortVpw, kShortFill>(ns);
+        if ((p->nlong && (e = slots_for(p->kern_long, 32 * kLongWarps, sizeof(float) * p->span_long,
+                                        &p->slots_long)) != cudaSuccess) ||
+            (p->nshort && (e = slots_for(p->kern_short, 32, sizeof(float) * p->span_short,
+                                         &p->slots_short)) != cudaSuccess))
             return fail("occupancy query");
-        p->slots = std::max(1, per_sm * sms);
     }
     if (!tchan.empty()) {
         int* dchan = nullptr;
@@ -389,10 +416,18 @@ cudaError_t exact_bwd(ExactPlan* p, int nf, const float* rimg, float* xcm, cudaS
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (p->nruns) {
-        const int gx = std::min(p->nruns, std::max(1, p->slots / nf));
-        p->kern<<<dim3((unsigned)gx, (unsigned)nf), kThreads, sizeof(float) * p->span_max, st>>>(
-            p->runs, p->nruns, p->pos, p->out, rimg, p->rimgT, p->psf, p->psfT, g, xcm);
+    if (p->nlong) {
+        const int gx = std::min(p->nlong, std::max(1, p->slots_long / nf));
+        p->kern_long<<<dim3((unsigned)gx, (unsigned)nf), 32 * kLongWarps, sizeof(float) * p->span_long, st>>>(
+            p->runs, p->nlong, p->pos, p->out, rimg, p->rimgT, p->psf, p->psfT, g, xcm);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (p->nshort) {
+        const int gx = std::min(p->nshort, std::max(1, p->slots_short / nf));
+        p->kern_short<<<dim3((unsigned)gx, (unsigned)nf), 32, sizeof(float) * p->span_short, st>>>(
+            p->runs + p->nlong, p->nshort, p->pos, p->out, rimg, p->rimgT, p->psf, p->psfT, g, xcm);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -402,7 +437,7 @@ cudaError_t exact_bwd(ExactPlan* p, int nf, const float* rimg, float* xcm, cudaS
 
 void exact_plan_counts(const ExactPlan* p, int64_t* in_runs, int64_t* runs, int64_t* single) {
     if (in_runs) *in_runs = p ? p->in_runs : 0;
-    if (runs) *runs = p ? p->nruns : 0;
+    if (runs) *runs = p ? p->nlong + p->nshort : 0;
     if (single) *single = p ? p->nsingle : 0;
 }
 
