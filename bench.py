@@ -237,10 +237,6 @@ def fft_plan_numbers(g, plan):
 # precision, kernel); each entry names its summary under profiles/ and is
 # removed when that kernel changes.
 NCU_TRAFFIC = {
-    ("lf_large_2025px_51z_psf345", "bf16x3", "forward contraction"):
-        ((4.031e9 + 0.0628e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
-    ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
-        ((3.502e9 + 0.2382e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
         ((0.0789e9 + 0.1840e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
@@ -266,17 +262,20 @@ def direct_tensor_roofline(g, prec, st_ms):
             "peak_source": "bf16_tflops_sustained (%s)" % src}
 
 
-def fft_kernel_work(g, plan, prec):
+def fft_kernel_work(g, plan, prec, spectra=None):
     """Algorithmic bytes (and contraction flops) per launch of the FFT
-    variant's four large kernels. Spectra are 8 bytes per complex value (BF16
-    hi/lo planes of real and imaginary part, or complex64); BF16 PSF spectra
-    are 4 bytes (hi planes only). Executed flops count every tensor-core
-    product (three per term in split BF16, two with BF16 PSF spectra)."""
+    variant's four large kernels. Data spectra are 8 bytes per complex value
+    (BF16 hi/lo planes of real and imaginary part, or complex64); the PSF
+    spectra are the bytes of the planes the contraction streams
+    (lfd_get_spectra: 8 bytes per value in split BF16, less with adaptive lo
+    planes, 4 with BF16 spectra), else 8 bytes per complex64 value. Executed
+    flops count every tensor-core product (three per term in split BF16, two
+    with BF16 PSF spectra)."""
     F, bins, nt, _, S, C = fft_plan_numbers(g, plan)
     L2 = (g.H // g.nnum) * (g.W // g.nnum)
     vol = 4.0 * C * L2
     xs, ys = 8.0 * bins * nt * C, 8.0 * bins * nt * S
-    ws = (4.0 if prec == "bf16" else 8.0) * bins * S * C
+    ws = float(spectra["bytes"]) if spectra and spectra.get("bytes") else 8.0 * bins * S * C
     flops = 8.0 * bins * S * nt * C * {"bf16x3": 3, "bf16": 2}.get(prec, 1)
     return {"volume_r2c": {"bytes": vol + xs, "slot": 8, "kernel": "forward volume transform"},
             "forward_contraction": {"bytes": ws + xs + ys, "flops": flops, "slot": 5,
@@ -289,10 +288,10 @@ def fft_kernel_work(g, plan, prec):
         {"F": F, "bins": bins, "tiles": nt}
 
 
-def fft_roofline(g, plan, prec, stage, peaks, peak_src, fp32_peak, smax):
+def fft_roofline(g, plan, prec, stage, peaks, peak_src, fp32_peak, smax, spectra=None):
     """Roofline of the slowest of the FFT variant's kernels (by the stage
     times measured with CUDA events), and every kernel's fractions beside it."""
-    work, shape = fft_kernel_work(g, plan, prec)
+    work, shape = fft_kernel_work(g, plan, prec, spectra)
     kern = {}
     for name, w in work.items():
         ms = stage[w["slot"]]
@@ -367,6 +366,7 @@ def run_lfd(args, rank, world, local):
     ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W,
                          lfd.lfd_default_options(precision=prec, variant=variant))
     fft_plan = lfd.lfd_get_fft_plan(ctx)
+    spectra = lfd.lfd_get_spectra(ctx)
     # data: y = Poisson(scale * H v_true) + background; H v_true by this path's
     # forward projection (an input for timing, never an expected value)
     vt_d = torch.from_numpy(vt.astype(np.float32)).to(dev)
@@ -489,7 +489,8 @@ def run_lfd(args, rank, world, local):
                    "exact_low_sensitivity"]
     stage_ms = dict(zip(stage_names, stage))
     if variant == "fft":
-        roof = fft_roofline(g, fft_plan, prec, stage, peaks, peak_src, fp32_peak, smax)
+        roof = fft_roofline(g, fft_plan, prec, stage, peaks, peak_src, fp32_peak, smax, spectra)
+        roof["psf_spectra"] = spectra
     elif prec == "fp32":
         dom_ms = max(stage[0], stage[2])
         dom = "forward projection" if stage[0] >= stage[2] else "backprojection"

@@ -93,6 +93,12 @@ typedef struct {
     int fft_size;         /* LFD_FFT transform size per axis: 32 or 64; 0 (default)
                              picks by a bandwidth / arithmetic cost model (see
                              lfd_autotune for picking by measurement)               */
+    float spectra_lo_tau; /* LFD_FFT with LFD_BF16X3: the lo planes of the PSF
+                             spectra are kept only for the (frequency bin,
+                             64-channel block) tiles whose largest hi value
+                             reaches tau x the largest of all spectra; a dropped
+                             lo part is below 2^-9 tau of that largest value.
+                             0 keeps every lo plane; default 2^-10; [0, 1)       */
 } lfd_options;
 
 /* How the two projections are computed (same results up to rounding). */
@@ -260,6 +266,13 @@ lfd_status lfd_get_fft_plan(const lfd_ctx* ctx, int* F, int* B, int* tiles, int*
  * pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
 lfd_status lfd_get_exact_plan(const lfd_ctx* ctx, int64_t* n_low, int64_t* in_runs, int64_t* runs,
                               int64_t* single);
+
+/* PSF spectra of an LFD_FFT context on the tensor cores: device bytes of the
+ * planes the contractions stream, and of the (frequency bin, 64-channel block)
+ * tiles how many keep their lo planes (lo_tiles_kept) out of lo_tiles (all
+ * tiles with full split BF16, none with LFD_BF16). All 0 for other contexts.
+ * Any output pointer may be NULL. LFD_EINVAL only for ctx == NULL. */
+lfd_status lfd_get_spectra(const lfd_ctx* ctx, int64_t* bytes, int64_t* lo_tiles_kept, int64_t* lo_tiles);
 
 /* Test hooks (no counterpart in the paper).
  * lfd_debug_fail_allocs(n): the next n device allocations the library makes

@@ -1047,7 +1047,7 @@ cudaError_t fft_init(const FftPlan& p, const Geo& g, const float* W32, const Fft
     if (e != cudaSuccess) return e;
     TapSrc src{W32, g.T, g.Spad, g.Cpad};
     // "tiles" = phases s, channels = c: Wf[bin][s][c]
-    if (b.cg) return r2c_any(p, src, g.C, p.Cw, g.S, nullptr, b.Wp, g.S, st);
+    if (b.Wp[0]) return r2c_any(p, src, g.C, p.Cw, g.S, nullptr, b.Wp, g.S, st);
     return r2c_any(p, src, g.C, p.Cf, g.S, b.Wf, nullptr, 0, st);
 }
 

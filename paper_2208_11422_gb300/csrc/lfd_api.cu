@@ -212,6 +212,11 @@ void free_all(lfd_ctx* ctx) {
         if (p) cudaFree(p);
     exact_plan_destroy(ctx->exact);
     ctx->exact = nullptr;
+    if (ctx->lo) {
+        cgemm_free_lo(ctx->lo);
+        delete ctx->lo;
+        ctx->lo = nullptr;
+    }
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
     if (ctx->host_pinned_slots) cudaFreeHost(ctx->host_pinned_slots);
@@ -251,6 +256,7 @@ void lfd_default_options(lfd_options* opt) {
     opt->max_frames = 1;
     opt->use_graph = 1;
     opt->fft_size = 0;
+    opt->spectra_lo_tau = 0.0009765625f;  // 2^-10
 }
 
 lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q, double NA,
@@ -324,6 +330,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
     if (opt.max_frames < 1 || opt.max_frames > 4096) return LFD_EINVAL;
     if (opt.fft_size != 0 && opt.fft_size != 32 && opt.fft_size != 64) return LFD_EINVAL;
+    if (!(opt.spectra_lo_tau >= 0.f && opt.spectra_lo_tau < 1.f)) return LFD_EINVAL;
     if (opt.max_frames > 1 && opt.variant != LFD_FFT) return LFD_EUNSUPPORTED;
     int XS = opt.XS, YS = opt.YS;
     if (XS <= 0 || YS <= 0) {
@@ -472,6 +479,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
 
     if (fft) {
         // PSF spectra, then H^T 1 by the FFT backprojection of ones
+        CREATE_CK(fft_init(fplan, g, ctx->W32, fbufs(ctx), st));
         if (fft_products(ctx)) {
             int major = 0;
             CREATE_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device));
@@ -496,6 +504,23 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
             }
             cb.Yout = ctx->Yh;
             cb.Xout = ctx->Xh;
+            const int64_t plane_bytes = (int64_t)fplan.bins * g.S * fplan.Cw * (int64_t)sizeof(__nv_bfloat16);
+            ctx->spectra_bytes = plane_bytes * (fft_products(ctx) == 3 ? 4 : 2);
+            if (fft_products(ctx) == 3 && ctx->opt.spectra_lo_tau > 0.f) {
+                // adaptive lo planes: keep the tiles that matter, free the full lo planes
+                ctx->lo = new (std::nothrow) LoPlanes();
+                if (!ctx->lo) return bail(LFD_ENOMEM);
+                CREATE_CK(cgemm_compact_lo(cb, ctx->opt.spectra_lo_tau, st, ctx->lo, &ctx->device_bytes));
+                for (int i : {1, 3}) {
+                    cudaFree(ctx->Wp[i]);
+                    ctx->Wp[i] = nullptr;
+                    cb.W[i] = nullptr;
+                    ctx->device_bytes -= plane_bytes;
+                }
+                cb.lo = *ctx->lo;
+                ctx->spectra_bytes = plane_bytes * 2 + 2 * (ctx->lo->kept + 1) * (int64_t)g.S * 64 *
+                                                           (int64_t)sizeof(__nv_bfloat16);
+            }
             std::string why2;
             cudaError_t ce = cgemm_init(cb, ctx->sm_count, &ctx->cg, &why2);
             if (ce != cudaSuccess) {
@@ -503,7 +528,6 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
                 return bail(LFD_ECUDA);
             }
         }
-        CREATE_CK(fft_init(fplan, g, ctx->W32, fbufs(ctx), st));
         CREATE_CK(launch_fill_cm(ctx->Rcm, (int64_t)g.S * L2, 1.0f, st));
         CREATE_CK(fft_backward(fplan, g, fbufs(ctx), 1, ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
         // Voxels whose sensitivity H^T 1 is below kLowSensitivity of the largest
@@ -603,6 +627,18 @@ lfd_status lfd_get_exact_plan(const lfd_ctx* ctx, int64_t* n_low, int64_t* in_ru
     if (!ctx) return LFD_EINVAL;
     if (n_low) *n_low = ctx->exact ? ctx->n_low : 0;
     exact_plan_counts(ctx->exact, in_runs, runs, single);
+    return LFD_OK;
+}
+
+lfd_status lfd_get_spectra(const lfd_ctx* ctx, int64_t* bytes, int64_t* lo_tiles_kept, int64_t* lo_tiles) {
+    if (!ctx) return LFD_EINVAL;
+    const FftPlan* fp = static_cast<const FftPlan*>(ctx->fft);
+    const bool tc = fp && ctx->cg;
+    const int64_t tiles = fp ? (int64_t)fp->bins * ((fp->Cw + 63) / 64) : 0;
+    if (bytes) *bytes = tc ? ctx->spectra_bytes : 0;
+    if (lo_tiles) *lo_tiles = tc ? tiles : 0;
+    if (lo_tiles_kept)
+        *lo_tiles_kept = !tc ? 0 : ctx->lo ? ctx->lo->kept : fft_products(ctx) == 3 ? tiles : 0;
     return LFD_OK;
 }
 

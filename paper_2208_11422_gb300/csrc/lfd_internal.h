@@ -76,6 +76,7 @@ struct StageTimes {
 };
 
 struct ExactPlan;  // exact.h
+struct LoPlanes;   // tc_cgemm.h
 
 }  // namespace lfd
 
@@ -147,6 +148,8 @@ struct lfd_ctx {
     float* psf_dev = nullptr;    // original PSF [Nz][N][N][P][P] (FFT variant)
     float* rimg = nullptr;       // ratio image [H][W] (FFT variant)
     lfd::ExactPlan* exact = nullptr;  // voxels backprojected exactly (FFT variant)
+    lfd::LoPlanes* lo = nullptr;      // adaptive lo planes of the PSF spectra (split BF16)
+    int64_t spectra_bytes = 0;        // PSF spectra planes the contractions stream
     int64_t n_low = 0;
 };
 

@@ -186,6 +186,7 @@ struct PsfSet {
     Geo gmax{};
     FftPlan plan{};
     FftBuffers fb{};
+    LoPlanes lo{};         // adaptive lo planes of the PSF spectra (split BF16)
     float* psf = nullptr;  // [Nz][N][N][P][P] for the exact backprojection
     std::vector<void*> owned;
     int max_tiles = 0, XSmax = 0, YSmax = 0;
@@ -206,6 +207,7 @@ struct PsfSet {
 
     ~PsfSet() {
         if (fb.cg) cgemm_destroy(fb.cg);
+        cgemm_free_lo(&lo);
         for (void* p : owned) cudaFree(p);
         if (h_fr) cudaFreeHost(h_fr);
         if (h_colf) cudaFreeHost(h_colf);
@@ -576,6 +578,15 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
     }
     ADD_CK(ps->dev(&b.Xh, (int64_t)p.bins * ncolp * p.Cf));
     ADD_CK(ps->dev(&b.Yh, (int64_t)p.bins * ncolp * p.Sf));
+    {  // PSF spectra from the packed taps (freed afterwards)
+        float* W32 = nullptr;
+        ADD_CK(cudaMalloc((void**)&W32, sizeof(float) * (size_t)g.taps() * g.Spad * g.Cpad));
+        cudaError_t e = launch_repack_psf(ps->psf, g, W32, nullptr, nullptr, ps->st);
+        if (e == cudaSuccess) e = fft_init(p, g, W32, b, ps->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ps->st);
+        cudaFree(W32);
+        ADD_CK(e);
+    }
     if (split) {
         CgemmBuffers cb{};
         cb.bins = p.bins;
@@ -594,21 +605,24 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
         }
         cb.Yout = b.Yh;
         cb.Xout = b.Xh;
+        if (products == 3 && o.spectra_lo_tau > 0.f) {
+            // adaptive lo planes: keep the tiles that matter, free the full lo planes
+            ADD_CK(cgemm_compact_lo(cb, o.spectra_lo_tau, ps->st, &ps->lo, &ps->resident));
+            for (int i : {1, 3}) {
+                ps->owned.erase(std::find(ps->owned.begin(), ps->owned.end(), (void*)b.Wp[i]));
+                cudaFree(b.Wp[i]);
+                ps->resident -= (int64_t)p.bins * g.S * p.Cw * (int64_t)sizeof(__nv_bfloat16);
+                b.Wp[i] = nullptr;
+                cb.W[i] = nullptr;
+            }
+            cb.lo = ps->lo;
+        }
         std::string why2;
         const cudaError_t ce = cgemm_init(cb, s->sm_count, &b.cg, &why2);
         if (ce != cudaSuccess) {
             s->err = "cgemm_init: " + (why2.empty() ? std::string(cudaGetErrorString(ce)) : why2);
             return LFD_ECUDA;
         }
-    }
-    {  // PSF spectra from the packed taps (freed afterwards)
-        float* W32 = nullptr;
-        ADD_CK(cudaMalloc((void**)&W32, sizeof(float) * (size_t)g.taps() * g.Spad * g.Cpad));
-        cudaError_t e = launch_repack_psf(ps->psf, g, W32, nullptr, nullptr, ps->st);
-        if (e == cudaSuccess) e = fft_init(p, g, W32, b, ps->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ps->st);
-        cudaFree(W32);
-        ADD_CK(e);
     }
     ADD_CK(ps->dev(&ps->d_fr, mf));
     ADD_CK(ps->dev(&ps->d_colf, (int64_t)mf * ps->max_tiles));

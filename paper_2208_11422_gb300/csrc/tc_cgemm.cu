@@ -12,7 +12,11 @@
 // instruction descriptor). With BF16 PSF spectra (no lo planes of Wf) the
 // passes are hi*hi + hi*lo: the PSF spectra are rounded once, the transformed
 // data still carry hi + lo, and the spectra stream is 4 bytes per complex
-// value instead of 8. One block owns 128 output rows (phases s for the
+// value instead of 8. With adaptive lo planes the PSF's lo planes are kept
+// only for the (bin, 64-channel block) tiles whose largest hi value reaches
+// tau x the largest of all spectra (compact planes [slot][S][64], slot 0 all
+// zeros); elsewhere the dropped lo part is below 2^-9 tau of the largest
+// value, and the k-block runs the two hi passes only. One block owns 128 output rows (phases s for the
 // forward, channels c for the adjoint) by a chunk of 16, 32 or 64 columns
 // (frame x tile) of one bin, so a spectra tile is loaded once for up to 64
 // columns; units are ordered bin-major so the blocks working on one bin share
@@ -43,14 +47,18 @@ constexpr int kPlaneA = 128 * 64 * 2;  // 16 KB
 constexpr int kThreads = 192;
 constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 MMA steps
 
-// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4). SW: the PSF
-// spectra as four planes (split BF16, three products per term); otherwise as
-// their two hi planes (BF16 spectra, two products per term: W x_hi + W x_lo).
-template <int NG, bool SW>
+// PSF spectra planes: MODE_BF16 the two hi planes (two products per term:
+// W x_hi + W x_lo); MODE_SPLIT four planes (three products per term);
+// MODE_ADAPTIVE the two hi planes plus, for the tiles that keep them, the two
+// compact lo planes (three products there, two elsewhere).
+constexpr int MODE_BF16 = 0, MODE_SPLIT = 1, MODE_ADAPTIVE = 2;
+
+// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4).
+template <int NG, int MODE>
 struct Cg {
     static constexpr int N = 16 * NG;                        // MMA N
-    static constexpr int NA = SW ? 4 : 2;                    // PSF planes per stage
-    static constexpr int NP = SW ? 3 : 2;                    // products per term
+    static constexpr int NA = MODE == MODE_BF16 ? 2 : 4;     // PSF planes per stage
+    static constexpr int NP = MODE == MODE_BF16 ? 2 : 3;     // products per term (at most)
     static constexpr int kPlaneB = N * 64 * 2;               // 2, 4 or 8 KB
     static constexpr int kStageBytes = NA * kPlaneA + 4 * kPlaneB;
     static constexpr int kStages = (232448 - 1280) / kStageBytes < 6 ? (232448 - 1280) / kStageBytes : 6;
@@ -69,16 +77,18 @@ struct CgArgs {
     int ld;            // row length of the output (Sf or Cf)
     float2* out;       // [bins][ntile][ld]
     int* err;
+    const int* lo_slot;  // adaptive lo planes: [bins][nkbc] compact slot, 0 = dropped
+    int nkbc;            // 64-channel blocks of the PSF spectra
 };
 
-template <bool ADJ, int NG, bool SW>
+template <bool ADJ, int NG, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
            const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
            const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
            const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
            const CgArgs a) {
-    using G = Cg<NG, SW>;
+    using G = Cg<NG, MODE>;
     constexpr int kStages = G::kStages, kStageBytes = G::kStageBytes;
     constexpr int kPlaneB = G::kPlaneB, N = G::N, NA = G::NA;
     constexpr uint32_t kTmemCols = G::kTmemCols;
@@ -94,6 +104,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    volatile int* stage_lo = reinterpret_cast<volatile int*>(tmem_slot + 3);  // [kStages]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_units = a.nbins * a.nchunk * a.mtiles;
@@ -131,19 +142,59 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
+            // adaptive lo planes: the compact slots of a k-block's channel block
+            // (forward) or of a tile's two 64-channel atoms (adjoint), read one
+            // step ahead so that the table lookup overlaps the ring's waits
+            const int units_per_bin = a.nchunk * a.mtiles;
+            auto unit_slots = [&](int u_, int kb_, int& s0, int& s1) {
+                s0 = s1 = 0;
+                if (MODE != MODE_ADAPTIVE || u_ >= n_units) return;
+                const int bin_ = u_ / units_per_bin, mt_ = (u_ % units_per_bin) % a.mtiles;
+                const int* ls = a.lo_slot + (int64_t)bin_ * a.nkbc;
+                if (!ADJ) {
+                    s0 = ls[kb_];
+                } else {
+                    s0 = 2 * mt_ < a.nkbc ? ls[2 * mt_] : 0;
+                    s1 = 2 * mt_ + 1 < a.nkbc ? ls[2 * mt_ + 1] : 0;
+                }
+            };
+            int nxt0, nxt1;
+            unit_slots(blockIdx.x, 0, nxt0, nxt1);
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int bin = u / (a.nchunk * a.mtiles), rem = u % (a.nchunk * a.mtiles);
+                const int bin = u / units_per_bin, rem = u % units_per_bin;
                 const int q = rem / a.mtiles, mt = rem % a.mtiles;
+                int ulo0 = 0, ulo1 = 0;
+                if (MODE == MODE_ADAPTIVE && ADJ) {  // per unit; the next unit's now
+                    ulo0 = nxt0;
+                    ulo1 = nxt1;
+                    unit_slots(u + gridDim.x, 0, nxt0, nxt1);
+                }
                 for (int kb = 0; kb < a.nkb && ok; ++kb) {
+                    int lo0 = ulo0, lo1 = ulo1;
+                    if (MODE == MODE_ADAPTIVE && !ADJ) {  // per k-block; the next step's now
+                        lo0 = nxt0;
+                        if (kb + 1 < a.nkb) unit_slots(u, kb + 1, nxt0, nxt1);
+                        else unit_slots(u + gridDim.x, 0, nxt0, nxt1);
+                    }
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], kStageBytes);
+                    const bool lo = MODE == MODE_SPLIT || (MODE == MODE_ADAPTIVE && (lo0 | lo1) != 0);
+                    if (MODE == MODE_ADAPTIVE) stage_lo[stage] = lo ? 1 : 0;
+                    mbar_expect_tx(&full[stage], lo || MODE == MODE_BF16 ? kStageBytes : kStageBytes - 2 * kPlaneA);
                     const uint32_t sA = sbase + stage * kStageBytes, sB = sA + NA * kPlaneA;
 #pragma unroll
                     for (int i = 0; i < NA; ++i) {
-                        if (ADJ) {  // MN-major: two 64-channel atoms of 64 phases
+                        if (MODE == MODE_ADAPTIVE && (i & 1)) {  // compact lo plane [slot][S][64]
+                            if (!lo) continue;
+                            if (ADJ) {
+                                tma_3d(sA + i * kPlaneA, A[i], 0, kb * 64, lo0, &full[stage]);
+                                tma_3d(sA + i * kPlaneA + 8192, A[i], 0, kb * 64, lo1, &full[stage]);
+                            } else {
+                                tma_3d(sA + i * kPlaneA, A[i], 0, mt * 128, lo0, &full[stage]);
+                            }
+                        } else if (ADJ) {  // MN-major: two 64-channel atoms of 64 phases
                             tma_3d(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage]);
                             tma_3d(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage]);
                         } else {
@@ -191,10 +242,11 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         }
                         tc_fence_after();
                         const uint32_t sA = sbase + stage * kStageBytes, sB = sA + NA * kPlaneA;
+                        const int np = MODE == MODE_ADAPTIVE && !stage_lo[stage] ? 2 : G::NP;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
                             // B planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo; A planes
-                            // the same (SW), or 0 real hi, 1 imag hi
+                            // the same (four planes), or 0 real hi, 1 imag hi
                             uint64_t ad[NA], bd[4];
 #pragma unroll
                             for (int i = 0; i < NA; ++i)
@@ -206,10 +258,12 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                                 bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 2 * N * 16, N * 16, 128);
 #pragma unroll
                             for (int p = 0; p < G::NP; ++p) {
-                                // SW: (hi, hi), (hi, lo), (lo, hi); else (hi, hi), (hi, lo)
-                                const int ia = (SW && p == 2) ? 1 : 0;
+                                if (p >= np) break;
+                                // four planes: (hi, hi), (hi, lo), (lo, hi); two: (hi, hi), (hi, lo)
+                                constexpr bool four = NA == 4;
+                                const int ia = (four && p == 2) ? 1 : 0;
                                 const int ib = p == 1 ? 1 : 0;
-                                const uint64_t wr = ad[ia], wi = ad[SW ? 2 + ia : 1];
+                                const uint64_t wr = ad[ia], wi = ad[four ? 2 + ia : 1];
                                 const uint32_t acc0 = (first && ks == 0 && p == 0) ? 0u : 1u;
                                 if (!ADJ) {
                                     umma_bf16(dR, wr, bd[ib], id_p, acc0);          // + Wr Xr
@@ -337,24 +391,34 @@ bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bin
 constexpr int kNg[3] = {1, 2, 4};
 
 struct CgState {
-    CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (two of them without SW)
+    CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (see the modes)
     CUtensorMap fb[3][4], ab[3][4];  // per chunk width
     CgArgs fwd, adj;
     int sm_count = 0, ncolp = 16, nwidths = 1;
-    bool sw = true;
+    int mode = MODE_SPLIT;
     int* err = nullptr;
 };
 
-template <bool ADJ, int NG, bool SW>
+template <bool ADJ, int NG, int MODE>
 cudaError_t launch_width(const CUtensorMap* A, const CUtensorMap* B, CgArgs a, int sm_count,
                          cudaStream_t st) {
-    using G = Cg<NG, SW>;
+    using G = Cg<NG, MODE>;
     a.nchunk = (a.ncol + G::N - 1) / G::N;
     const int grid = std::min(a.nbins * a.nchunk * a.mtiles, sm_count);
-    k_tc_cgemm<ADJ, NG, SW><<<grid, kThreads, G::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
-                                                                   B[2], B[3], a);
+    k_tc_cgemm<ADJ, NG, MODE><<<grid, kThreads, G::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
+                                                                     B[2], B[3], a);
     count_launch();
     return cudaGetLastError();
+}
+
+template <bool ADJ, int MODE>
+cudaError_t launch_mode(int ng, const CUtensorMap* A, const CUtensorMap* B, const CgArgs& a, int sm_count,
+                        cudaStream_t st) {
+    switch (ng) {
+        case 1: return launch_width<ADJ, 1, MODE>(A, B, a, sm_count, st);
+        case 2: return launch_width<ADJ, 2, MODE>(A, B, a, sm_count, st);
+        default: return launch_width<ADJ, 4, MODE>(A, B, a, sm_count, st);
+    }
 }
 
 template <bool ADJ>
@@ -368,31 +432,127 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     while (j + 1 < s->nwidths && kNg[j] < ncg) ++j;
     const CUtensorMap* A = ADJ ? s->aa : s->fa;
     const CUtensorMap* B = ADJ ? s->ab[j] : s->fb[j];
-    if (s->sw) {
-        switch (kNg[j]) {
-            case 1: return launch_width<ADJ, 1, true>(A, B, a, s->sm_count, st);
-            case 2: return launch_width<ADJ, 2, true>(A, B, a, s->sm_count, st);
-            default: return launch_width<ADJ, 4, true>(A, B, a, s->sm_count, st);
-        }
-    }
-    switch (kNg[j]) {
-        case 1: return launch_width<ADJ, 1, false>(A, B, a, s->sm_count, st);
-        case 2: return launch_width<ADJ, 2, false>(A, B, a, s->sm_count, st);
-        default: return launch_width<ADJ, 4, false>(A, B, a, s->sm_count, st);
+    switch (s->mode) {
+        case MODE_BF16: return launch_mode<ADJ, MODE_BF16>(kNg[j], A, B, a, s->sm_count, st);
+        case MODE_ADAPTIVE: return launch_mode<ADJ, MODE_ADAPTIVE>(kNg[j], A, B, a, s->sm_count, st);
+        default: return launch_mode<ADJ, MODE_SPLIT>(kNg[j], A, B, a, s->sm_count, st);
     }
 }
 
-template <int NG, bool SW>
+template <int MODE>
 cudaError_t set_smem() {
-    constexpr int bytes = Cg<NG, SW>::kSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm<false, NG, SW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_cgemm<true, NG, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes);
+    cudaError_t e = cudaSuccess;
+    auto one = [&](auto kern, int bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    one(k_tc_cgemm<false, 1, MODE>, Cg<1, MODE>::kSmemBytes);
+    one(k_tc_cgemm<true, 1, MODE>, Cg<1, MODE>::kSmemBytes);
+    one(k_tc_cgemm<false, 2, MODE>, Cg<2, MODE>::kSmemBytes);
+    one(k_tc_cgemm<true, 2, MODE>, Cg<2, MODE>::kSmemBytes);
+    one(k_tc_cgemm<false, 4, MODE>, Cg<4, MODE>::kSmemBytes);
+    one(k_tc_cgemm<true, 4, MODE>, Cg<4, MODE>::kSmemBytes);
+    return e;
+}
+
+// largest |real| / |imag| hi value of every (bin, 64-channel block) tile of the
+// PSF spectra [bins][S][Cw]: one block per tile
+__global__ void k_tile_max(const __nv_bfloat16* __restrict__ re, const __nv_bfloat16* __restrict__ im, int S,
+                           int Cw, int nkbc, float* __restrict__ tmax) {
+    const int bin = blockIdx.x / nkbc, kb = blockIdx.x % nkbc;
+    const int c = kb * 64 + (threadIdx.x & 63);
+    float m = 0.f;
+    if (c < Cw) {
+        for (int s = threadIdx.x >> 6; s < S; s += blockDim.x >> 6) {
+            const int64_t o = ((int64_t)bin * S + s) * Cw + c;
+            m = fmaxf(m, fmaxf(fabsf(__bfloat162float(re[o])), fabsf(__bfloat162float(im[o]))));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        tmax[blockIdx.x] = fmaxf(m, wm[0]);
+    }
+}
+
+// compact lo planes: tile k of the list (bin, block) goes to slot k + 1
+__global__ void k_gather_lo(const __nv_bfloat16* __restrict__ lo, const int2* __restrict__ tiles, int S, int Cw,
+                            __nv_bfloat16* __restrict__ dst) {
+    const int2 t = tiles[blockIdx.x];  // (bin, block)
+    __nv_bfloat16* d = dst + (int64_t)(blockIdx.x + 1) * S * 64;
+    for (int e = threadIdx.x; e < S * 64; e += blockDim.x) {
+        const int s = e >> 6, c = t.y * 64 + (e & 63);
+        d[e] = c < Cw ? lo[((int64_t)t.x * S + s) * Cw + c] : __float2bfloat16(0.f);
+    }
 }
 
 }  // namespace
+
+cudaError_t cgemm_compact_lo(const CgemmBuffers& b, float tau, cudaStream_t st, LoPlanes* out, int64_t* bytes) {
+    *out = LoPlanes{};
+    const int nkbc = (b.Cw + 63) / 64;
+    const int64_t ntiles = (int64_t)b.bins * nkbc;
+    float* dmax = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dmax, sizeof(float) * ntiles);
+    if (e != cudaSuccess) return e;
+    k_tile_max<<<(unsigned)ntiles, 256, 0, st>>>(b.W[0], b.W[2], b.S, b.Cw, nkbc, dmax);
+    count_launch();
+    std::vector<float> tmax(ntiles);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmax.data(), dmax, sizeof(float) * ntiles, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dmax);
+    if (e != cudaSuccess) return e;
+    float gmax = 0.f;
+    for (float m : tmax) gmax = std::max(gmax, m);
+    std::vector<int> slot(ntiles, 0);
+    std::vector<int2> keep;
+    for (int64_t i = 0; i < ntiles; ++i)
+        if (tmax[i] >= tau * gmax) {
+            keep.push_back(make_int2((int)(i / nkbc), (int)(i % nkbc)));
+            slot[i] = (int)keep.size();
+        }
+    out->nkbc = nkbc;
+    out->tiles = ntiles;
+    out->kept = (int64_t)keep.size();
+    const size_t plane = (keep.size() + 1) * (size_t)b.S * 64;
+    int2* dtiles = nullptr;
+    auto alloc = [&](void** p, size_t n) {
+        if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+        cudaError_t r = cudaMalloc(p, n);
+        if (r == cudaSuccess) *bytes += (int64_t)n;
+        return r;
+    };
+    if ((e = alloc((void**)&out->slot, sizeof(int) * ntiles)) != cudaSuccess) return e;
+    if ((e = alloc((void**)&out->lo[0], sizeof(__nv_bfloat16) * plane)) != cudaSuccess) return e;
+    if ((e = alloc((void**)&out->lo[1], sizeof(__nv_bfloat16) * plane)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(out->slot, slot.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)  // slot 0: zeros
+        e = cudaMemsetAsync(out->lo[q], 0, sizeof(__nv_bfloat16) * b.S * 64, st);
+    if (e == cudaSuccess && !keep.empty()) {
+        if ((e = cudaMalloc((void**)&dtiles, sizeof(int2) * keep.size())) != cudaSuccess) return e;
+        e = cudaMemcpyAsync(dtiles, keep.data(), sizeof(int2) * keep.size(), cudaMemcpyHostToDevice, st);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            k_gather_lo<<<(unsigned)keep.size(), 256, 0, st>>>(b.W[2 * q + 1], dtiles, b.S, b.Cw, out->lo[q]);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dtiles);
+    }
+    return e;
+}
+
+void cgemm_free_lo(LoPlanes* p) {
+    if (p->slot) cudaFree(p->slot);
+    if (p->lo[0]) cudaFree(p->lo[0]);
+    if (p->lo[1]) cudaFree(p->lo[1]);
+    *p = LoPlanes{};
+}
 
 cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::string* why) {
     CgState* s = new (std::nothrow) CgState();
@@ -404,12 +564,19 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     if ((e = cudaMemset(s->err, 0, sizeof(int))) != cudaSuccess) return e;
     s->nwidths = 1;
     while (s->nwidths < 3 && 16 * kNg[s->nwidths] <= b.ncolp) ++s->nwidths;
-    s->sw = b.W[1] && b.W[3];
+    s->mode = b.lo.slot ? MODE_ADAPTIVE : (b.W[1] && b.W[3]) ? MODE_SPLIT : MODE_BF16;
+    const int nslot = (int)b.lo.kept + 1;
     for (int i = 0; i < 4; ++i) {
-        // without the lo planes the kernel's PSF planes are 0 (real hi), 2 (imag hi)
-        const __nv_bfloat16* w = s->sw ? b.W[i] : b.W[(i & 1) * 2];
-        bool ok = w && map3(&s->fa[i], w, b.Cw, b.S, b.bins, 64, 128) &&
-                  map3(&s->aa[i], w, b.Cw, b.S, b.bins, 64, 64);
+        bool ok;
+        if (s->mode == MODE_ADAPTIVE && (i & 1)) {  // compact lo planes [slot][S][64]
+            ok = map3(&s->fa[i], b.lo.lo[i >> 1], 64, b.S, nslot, 64, 128) &&
+                 map3(&s->aa[i], b.lo.lo[i >> 1], 64, b.S, nslot, 64, 64);
+        } else {
+            // BF16 spectra: the kernel's two PSF planes are 0 (real hi), 2 (imag hi)
+            const __nv_bfloat16* w = s->mode == MODE_BF16 ? b.W[(i & 1) * 2] : b.W[i];
+            ok = w && map3(&s->fa[i], w, b.Cw, b.S, b.bins, 64, 128) &&
+                 map3(&s->aa[i], w, b.Cw, b.S, b.bins, 64, 64);
+        }
         for (int j = 0; j < s->nwidths && ok; ++j)
             ok = map4_grouped(&s->fb[j][i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16 * kNg[j]) &&
                  map4_grouped(&s->ab[j][i], b.Y[i], b.Sw / 8, b.bins, b.ncolp, 16 * kNg[j]);
@@ -428,6 +595,8 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     f.ld = b.Sf;
     f.out = b.Yout;
     f.err = s->err;
+    f.lo_slot = b.lo.slot;
+    f.nkbc = b.lo.nkbc;
     CgArgs& g = s->adj;
     g = f;
     g.mtiles = (b.C + 127) / 128;
@@ -437,14 +606,11 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.out = b.Xout;
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
-    if (s->sw) {
-        if ((e = set_smem<1, true>()) != cudaSuccess) return e;
-        if ((e = set_smem<2, true>()) != cudaSuccess) return e;
-        return set_smem<4, true>();
+    switch (s->mode) {
+        case MODE_BF16: return set_smem<MODE_BF16>();
+        case MODE_ADAPTIVE: return set_smem<MODE_ADAPTIVE>();
+        default: return set_smem<MODE_SPLIT>();
     }
-    if ((e = set_smem<1, false>()) != cudaSuccess) return e;
-    if ((e = set_smem<2, false>()) != cudaSuccess) return e;
-    return set_smem<4, false>();
 }
 
 cudaError_t cgemm_forward(void* state, int ncol, cudaStream_t st) {

@@ -6,7 +6,20 @@
 
 namespace lfd {
 
+// Adaptive lo planes of the PSF spectra (cgemm_compact_lo): the lo planes of
+// the (bin, 64-channel block) tiles whose largest hi value reaches tau x the
+// largest of all, as compact planes [kept + 1][S][64] (slot 0 all zeros), and
+// slot[bin][block] (0: dropped).
+struct LoPlanes {
+    __nv_bfloat16* lo[2] = {};  // real lo, imag lo
+    int* slot = nullptr;
+    int nkbc = 0;               // 64-channel blocks per bin
+    int64_t kept = 0, tiles = 0;
+};
+
 // Operands are BF16 planes: [0] real hi, [1] real lo, [2] imag hi, [3] imag lo.
+// The PSF spectra: all four planes (split BF16), the two hi planes (W[1], W[3]
+// null: BF16 spectra), or the two hi planes and lo.slot != null (adaptive).
 struct CgemmBuffers {
     int bins, ntile;          // frequency bins; tiles per frame
     int ncolp;                // columns of the X / Y planes (padded to 16)
@@ -18,7 +31,14 @@ struct CgemmBuffers {
     const __nv_bfloat16* Y[4];  // [Sw/8][ncolp][bins][8] ratio spectra (adjoint input)
     float2* Yout;             // [bins][ncol][Sf] forward output
     float2* Xout;             // [bins][ncol][Cf] adjoint output
+    LoPlanes lo;              // adaptive lo planes (slot null otherwise)
 };
+
+// Builds the adaptive lo planes from the full planes b.W[0..3] ([bins][S][Cw]);
+// the caller may free b.W[1] and b.W[3] afterwards. Device bytes allocated
+// are added to *bytes.
+cudaError_t cgemm_compact_lo(const CgemmBuffers& b, float tau, cudaStream_t st, LoPlanes* out, int64_t* bytes);
+void cgemm_free_lo(LoPlanes* p);
 
 cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::string* why);
 // ncol = frames x tiles of this call (<= ncolp)

@@ -45,6 +45,7 @@ class lfd_options(ctypes.Structure):
         ("max_frames", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("fft_size", ctypes.c_int),
+        ("spectra_lo_tau", ctypes.c_float),
     ]
 
 
@@ -120,6 +121,7 @@ _SIGS = {
     "lfd_get_fft_plan": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
     "lfd_get_exact_plan": (_I, [_VP] + [ctypes.POINTER(ctypes.c_int64)] * 4),
+    "lfd_get_spectra": (_I, [_VP] + [ctypes.POINTER(ctypes.c_int64)] * 3),
     "lfd_launch_count": (ctypes.c_uint64, []),
     "lfd_debug_fail_allocs": (None, [_I]),
     "lfd_selftest_bounded_wait": (_I, [ctypes.c_int64, ctypes.POINTER(_I)]),
@@ -327,6 +329,12 @@ def lfd_get_exact_plan(ctx) -> dict:
     v = [ctypes.c_int64(0) for _ in range(4)]
     _check(load().lfd_get_exact_plan(ctx, *[ctypes.byref(x) for x in v]), ctx)
     return dict(zip(("n_low", "in_runs", "runs", "single"), (x.value for x in v)))
+
+
+def lfd_get_spectra(ctx) -> dict:
+    v = [ctypes.c_int64(0) for _ in range(3)]
+    _check(load().lfd_get_spectra(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return dict(zip(("bytes", "lo_tiles_kept", "lo_tiles"), (x.value for x in v)))
 
 
 def lfd_debug_fail_allocs(n: int):
