@@ -237,6 +237,10 @@ def fft_plan_numbers(g, plan):
 # precision, kernel); each entry names its summary under profiles/ and is
 # removed when that kernel changes.
 NCU_TRAFFIC = {
+    ("lf_large_2025px_51z_psf345", "bf16x3", "forward contraction"):
+        (41.024e9 + 0.188e9, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+    ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
+        (33.181e9 + 3.093e9, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
         ((0.0789e9 + 0.1840e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
