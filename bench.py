@@ -230,7 +230,7 @@ def fft_plan_numbers(g, plan):
     """(F, bins, tiles, Cf, S, C) of the FFT tiling the library chose (lfd_get_fft_plan)."""
     N = g.nnum
     S, C = N * N, g.nz * N * N
-    return plan["F"], plan["bins"], plan["tiles"], (C + 3) // 4 * 4, S, C
+    return plan["F"], plan["bins"], plan["tiles"], (C + 7) // 8 * 8, S, C
 
 
 # DRAM bytes (read + write) per launch from one ncu capture, by (workload,

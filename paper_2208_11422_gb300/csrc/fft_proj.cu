@@ -40,7 +40,7 @@ struct FftSize {
     static constexpr int CPW = 64 / F;         // channels per warp (lanes / HF)
     static constexpr int R2C_WARPS = 8;        // per R2C block
     static constexpr int R2C_CH = R2C_WARPS * CPW;
-    static constexpr int C2R_WARPS = 4;        // per C2R block
+    static constexpr int C2R_WARPS = F == 64 ? 8 : 4;  // per C2R block
     static constexpr int C2R_CH = C2R_WARPS * CPW;
 };
 
@@ -471,21 +471,26 @@ __global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const fl
     const int ch = warp * Z::CPW + sub;
     const int tile = blockIdx.x, c0 = blockIdx.y * CH, c = c0 + ch;
     const auto view = dst.bind(tile);
-    // spectra of 4 consecutive channels per bin, into [channel][bin]
-    for (int e = threadIdx.x; e < Z::BINS * (CH / 4); e += blockDim.x) {
-        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + 4 * g;
-        float2 v[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                       make_float2(0.f, 0.f)};
-        if (cg < ldc) {
+    // spectra of VG consecutive channels per bin (one thread reads them with
+    // 16-byte loads), into [channel][bin]
+    constexpr int VG = CH < 8 ? CH : 8;
+    static_assert(VG % 4 == 0, "channel groups of 4 or 8");
+    for (int e = threadIdx.x; e < Z::BINS * (CH / VG); e += blockDim.x) {
+        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + VG * g;
+        float2 v[VG];
+#pragma unroll
+        for (int k = 0; k < VG; ++k) v[k] = make_float2(0.f, 0.f);
+        if (cg < ldc) {  // ldc is a multiple of VG (run_c2r checks)
             const float4* q = reinterpret_cast<const float4*>(in + ((int64_t)bin * ntile + tile) * ldc + cg);
-            const float4 w0 = q[0], w1 = q[1];
-            v[0] = make_float2(w0.x, w0.y);
-            v[1] = make_float2(w0.z, w0.w);
-            v[2] = make_float2(w1.x, w1.y);
-            v[3] = make_float2(w1.z, w1.w);
+#pragma unroll
+            for (int k = 0; k < VG / 2; ++k) {
+                const float4 w = q[k];
+                v[2 * k] = make_float2(w.x, w.y);
+                v[2 * k + 1] = make_float2(w.z, w.w);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sm[(size_t)(4 * g + k) * Z::BINS + bin] = v[k];
+        for (int k = 0; k < VG; ++k) sm[(size_t)(VG * g + k) * Z::BINS + bin] = v[k];
     }
     __syncthreads();
     float2* R = sm + (size_t)ch * Z::BINS;  // [F][H2]
@@ -985,6 +990,7 @@ cudaError_t r2c_grouped(const FftPlan& p, Src src, int nch, int ldc, int ntile,
 template <int F, class Dst>
 cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
                     cudaStream_t st) {
+    if (ldc % 8 != 0) return cudaErrorInvalidValue;  // whole 8-channel groups per row
     const size_t smem = fft_smem<F>(false);
     cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1014,8 +1020,8 @@ bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, int tc_prod
         if (q.ntile > 64) continue;
         if (g.S > 256) continue;  // one thread per phase in the FP32 forward contraction
         q.bins = F * (F / 2 + 1);
-        q.Cf = (g.C + 3) & ~3;
-        q.Sf = (g.S + 3) & ~3;
+        q.Cf = (g.C + 7) & ~7;
+        q.Sf = (g.S + 7) & ~7;
         q.Cw = (g.C + 7) & ~7;
         q.Sw = (g.S + 7) & ~7;
         // complex64, split BF16 (4 planes) or BF16 (2 planes)

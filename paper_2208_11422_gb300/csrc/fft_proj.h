@@ -10,7 +10,8 @@ struct FftPlan {
     int h = 0;          // tap halo
     int tiles_y = 0, tiles_x = 0, ntile = 0;
     int bins = 0;       // F * (F/2 + 1)
-    int Cf = 0, Sf = 0; // channel / phase counts padded to 4 (row lengths of the spectra)
+    int Cf = 0, Sf = 0; // channel / phase counts padded to 8 (row lengths of the complex64
+                        // spectra; the inverse transform reads whole 8-channel groups)
     int Cw = 0, Sw = 0; // padded to 8 (row lengths of the BF16 planes)
 };
 
