@@ -244,7 +244,7 @@ NCU_TRAFFIC = {
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
         ((0.0789e9 + 0.1840e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
-        ((0.2467e9 + 0.0483e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        ((0.2466e9 + 0.0485e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
 
 
