@@ -289,10 +289,20 @@ lfd_status lfd_get_spectra(const lfd_ctx* ctx, int64_t* bytes, int64_t* lo_tiles
  * allocations and releases on the first-fit free list of the serving arena and
  * checks it against a byte map: no overlap, 256-byte alignment, failure only
  * when no free run is large enough, exact accounting, full coalescing at the
- * end. LFD_OK, LFD_EINTERNAL on a violation, LFD_EINVAL for steps < 1. */
+ * end. LFD_OK, LFD_EINTERNAL on a violation, LFD_EINVAL for steps < 1.
+ * lfd_selftest_exact_runs(seed, Nnum, Nz, k, L): host only; builds the plan
+ * of runs for the exact low-sensitivity sums (lfd_get_exact_plan) from a
+ * seeded synthetic voxel list on an L x L lenslet grid (Nnum, Nz depths, PSF
+ * k lenslets wide): border bands, corner blocks and scattered voxels of each
+ * channel. Checks that every listed voxel is summed exactly once, that a
+ * piece holds voxels of one channel along one lenslet row or column in
+ * increasing order within the piece and staging limits, that its PSF tile is
+ * the voxel's (or its transposed copy), and the cost order. LFD_OK,
+ * LFD_EINTERNAL on a violation, LFD_EINVAL for an invalid shape. */
 void lfd_debug_fail_allocs(int n);
 lfd_status lfd_selftest_bounded_wait(int64_t limit_ns, int* code);
 lfd_status lfd_selftest_freelist(int seed, int steps);
+lfd_status lfd_selftest_exact_runs(int seed, int Nnum, int Nz, int k, int L);
 
 /* Number of kernels the library has launched in this process (all contexts). */
 uint64_t lfd_launch_count(void);

@@ -21,6 +21,7 @@
 // one-warp-per-voxel kernel (k_exact_bwd).
 #include <algorithm>
 #include <cstring>
+#include <random>
 #include <new>
 #include <unordered_map>
 #include <vector>
@@ -236,14 +237,23 @@ cudaError_t slots_for(RunsKernel k, int threads, size_t smem, int* slots) {
 }
 }  // namespace
 
-cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const float* psf, int max_frames,
-                              cudaStream_t st, ExactPlan** out, int64_t* bytes, std::string* why) {
-    *out = nullptr;
-    ExactPlan* p = new (std::nothrow) ExactPlan();
-    if (!p) return cudaErrorMemoryAllocation;
-    p->g = g;
-    p->max_frames = max_frames;
-    p->psf = psf;
+namespace {
+
+// The host half of a plan: the pieces (long ones first, each kind sorted by
+// cost), their voxels' positions along the run and output indices, the voxels
+// left to one warp each, and the channels whose PSF tile is transposed.
+struct RunPlan {
+    std::vector<ExactRun> runs;
+    int nlong = 0, nshort = 0;
+    std::vector<int> pos;
+    std::vector<int64_t> out;
+    std::vector<int64_t> single;
+    std::vector<int> tchan;
+    int span_long = 0, span_short = 0;
+};
+
+RunPlan build_runs(const int64_t* low, int64_t n, const Geo& g) {
+    RunPlan rp;
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
     const int ns = (g.P + 31) / 32;
     // run lengths along rows (c, Iy) and columns (c, Ix); each voxel joins the
@@ -264,12 +274,11 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
     };
     std::vector<Item> items;
     items.reserve(n);
-    std::vector<int64_t> single;
     const bool runs_ok = ns <= kNsMax;  // else every voxel takes the one-warp-per-voxel kernel
     for (int64_t i = 0; i < n; ++i) {
         const int lr = nrow[(int64_t)cs[i] * g.Ly + iys[i]], lc = ncol[(int64_t)cs[i] * g.Lx + ixs[i]];
         if (!runs_ok) {
-            single.push_back(low[i]);
+            rp.single.push_back(low[i]);
             continue;
         }
         if (lr >= lc) items.push_back({0, cs[i], iys[i], ixs[i], low[i]});
@@ -281,10 +290,7 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         if (a.fixed != b.fixed) return a.fixed < b.fixed;
         return a.pos < b.pos;
     });
-    std::vector<ExactRun> runs, shorts;
-    std::vector<int> pos;
-    std::vector<int64_t> outs;
-    std::vector<int> tchan;                     // channels whose tile is transposed
+    std::vector<ExactRun> shorts;
     std::unordered_map<int, int> tslot;
     for (size_t a = 0; a < items.size();) {
         size_t b = a;
@@ -298,8 +304,8 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         if (h.orient) {
             auto it = tslot.find(h.c);
             if (it == tslot.end()) {
-                it = tslot.emplace(h.c, (int)tchan.size()).first;
-                tchan.push_back(h.c);
+                it = tslot.emplace(h.c, (int)rp.tchan.size()).first;
+                rp.tchan.push_back(h.c);
             }
             ktile = (int64_t)it->second * g.P * g.P;
         }
@@ -317,21 +323,21 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
             r.fixed = h.fixed;
             r.pf = h.orient ? tx : ty;
             r.pp = h.orient ? ty : tx;
-            r.first = (int)pos.size();
+            r.first = (int)rp.pos.size();
             r.count = (int)(e - s);
             for (size_t i = s; i < e; ++i) {
-                pos.push_back(items[i].pos);
-                outs.push_back(items[i].idx);
+                rp.pos.push_back(items[i].pos);
+                rp.out.push_back(items[i].idx);
             }
             const int span = (items[e - 1].pos - items[s].pos) * g.N + 32 * ns;
-            int& sm = is_long ? p->span_long : p->span_short;
+            int& sm = is_long ? rp.span_long : rp.span_short;
             sm = std::max(sm, span);
-            (is_long ? runs : shorts).push_back(r);
+            (is_long ? rp.runs : shorts).push_back(r);
             s = e;
         }
         a = b;
     }
-    std::sort(single.begin(), single.end());
+    std::sort(rp.single.begin(), rp.single.end());
     // costliest pieces first (voxels x PSF rows inside the sensor), so that the
     // grid's block-stride deal ends evenly
     auto cost = [&](const ExactRun& r) {
@@ -339,11 +345,35 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
         return (int64_t)r.count * std::max(0, std::min(g.P, Hh + c0 - ip) - std::max(0, c0 - ip));
     };
     auto by_cost = [&](const ExactRun& a, const ExactRun& b) { return cost(a) > cost(b); };
-    std::stable_sort(runs.begin(), runs.end(), by_cost);
+    std::stable_sort(rp.runs.begin(), rp.runs.end(), by_cost);
     std::stable_sort(shorts.begin(), shorts.end(), by_cost);
-    p->nlong = (int)runs.size();
-    p->nshort = (int)shorts.size();
-    runs.insert(runs.end(), shorts.begin(), shorts.end());
+    rp.nlong = (int)rp.runs.size();
+    rp.nshort = (int)shorts.size();
+    rp.runs.insert(rp.runs.end(), shorts.begin(), shorts.end());
+    return rp;
+}
+
+}  // namespace
+
+cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const float* psf, int max_frames,
+                              cudaStream_t st, ExactPlan** out, int64_t* bytes, std::string* why) {
+    *out = nullptr;
+    ExactPlan* p = new (std::nothrow) ExactPlan();
+    if (!p) return cudaErrorMemoryAllocation;
+    p->g = g;
+    p->max_frames = max_frames;
+    p->psf = psf;
+    const int ns = (g.P + 31) / 32;
+    RunPlan rp = build_runs(low, n, g);
+    const std::vector<ExactRun>& runs = rp.runs;
+    const std::vector<int>& pos = rp.pos;
+    const std::vector<int64_t>& outs = rp.out;
+    const std::vector<int64_t>& single = rp.single;
+    const std::vector<int>& tchan = rp.tchan;
+    p->nlong = rp.nlong;
+    p->nshort = rp.nshort;
+    p->span_long = rp.span_long;
+    p->span_short = rp.span_short;
     p->in_runs = (int64_t)pos.size();
     p->nsingle = (int64_t)single.size();
     int64_t total = 0;
@@ -450,3 +480,75 @@ void exact_plan_destroy(ExactPlan* p) {
 }
 
 }  // namespace lfd
+
+// Host-only check of the run plan on a seeded synthetic list (border bands,
+// corner blocks, scattered voxels): every voxel is summed exactly once, a
+// piece holds voxels of one channel along one lenslet row or column in
+// increasing order, within the piece and staging limits, its PSF tile offset
+// names the voxel's channel (or its transposed copy), and the long pieces
+// come first, each kind sorted by cost.
+extern "C" lfd_status lfd_selftest_exact_runs(int seed, int N, int Nz, int k, int L) {
+    using namespace lfd;
+    if (N < 1 || N % 2 == 0 || Nz < 1 || k < 1 || k % 2 == 0 || L < 1 || L > 256) return LFD_EINVAL;
+    Geo g{};
+    std::string why;
+    if (!make_geo(k * N, N, Nz, L * N, L * N, &g, &why)) return LFD_EINVAL;
+    std::mt19937_64 rng((uint64_t)seed);
+    const int64_t L2 = (int64_t)g.Ly * g.Lx;
+    std::vector<char> mark((size_t)g.C * L2, 0);
+    for (int c = 0; c < g.C; ++c) {
+        const int kind = (int)(rng() % 5);
+        const int w = 1 + (int)(rng() % 3);
+        for (int iy = 0; iy < g.Ly; ++iy)
+            for (int ix = 0; ix < g.Lx; ++ix) {
+                bool on = false;
+                if (kind == 0) on = iy < w;                             // top band
+                if (kind == 1) on = ix >= g.Lx - w;                     // right band
+                if (kind == 2) on = iy < w + 2 && ix < w + 2;           // corner block
+                if (kind == 3) on = rng() % 97 == 0;                    // scattered
+                if (on) mark[(size_t)c * L2 + (size_t)iy * g.Lx + ix] = 1;
+            }
+    }
+    std::vector<int64_t> low;
+    for (size_t i = 0; i < mark.size(); ++i)
+        if (mark[i]) low.push_back((int64_t)i);
+    const RunPlan rp = build_runs(low.data(), (int64_t)low.size(), g);
+    const int ns = (g.P + 31) / 32;
+    std::vector<char> seen(mark.size(), 0);
+    auto cost = [&](const ExactRun& r) {
+        const int ip = r.fixed * g.N + r.pf, c0 = (g.P - 1) / 2, Hh = r.orient ? g.W : g.H;
+        return (int64_t)r.count * std::max(0, std::min(g.P, Hh + c0 - ip) - std::max(0, c0 - ip));
+    };
+    if (rp.nlong + rp.nshort != (int)rp.runs.size()) return LFD_EINTERNAL;
+    for (size_t r = 0; r < rp.runs.size(); ++r) {
+        const ExactRun& R = rp.runs[r];
+        const bool is_long = (int)r < rp.nlong;
+        if (R.count < 1 || R.count > (is_long ? kMaxPiece : kShortVpw)) return LFD_EINTERNAL;
+        if (r > 0 && (int)r != rp.nlong && cost(rp.runs[r - 1]) < cost(R)) return LFD_EINTERNAL;
+        const int span = (rp.pos[R.first + R.count - 1] - rp.pos[R.first]) * g.N + 32 * ns;
+        if (span > (is_long ? rp.span_long : rp.span_short) || span > (is_long ? kLongSpan : kShortSpan))
+            return LFD_EINTERNAL;
+        for (int v = 0; v < R.count; ++v) {
+            const int64_t idx = rp.out[R.first + v];
+            if (idx < 0 || idx >= (int64_t)mark.size() || !mark[idx] || seen[idx]) return LFD_EINTERNAL;
+            seen[idx] = 1;
+            const int c = (int)(idx / L2), iy = (int)((idx % L2) / g.Lx), ix = (int)(idx % g.Lx);
+            const int t = c % g.S, ty = t / g.N, tx = t % g.N;
+            const int fixed = R.orient ? ix : iy, along = R.orient ? iy : ix;
+            if (R.fixed != fixed || rp.pos[R.first + v] != along) return LFD_EINTERNAL;
+            if (R.pf != (R.orient ? tx : ty) || R.pp != (R.orient ? ty : tx)) return LFD_EINTERNAL;
+            if (v > 0 && rp.pos[R.first + v] <= rp.pos[R.first + v - 1]) return LFD_EINTERNAL;
+            const int64_t tile = R.ktile / ((int64_t)g.P * g.P);
+            if (R.ktile % ((int64_t)g.P * g.P) != 0) return LFD_EINTERNAL;
+            if (R.orient ? (tile >= (int64_t)rp.tchan.size() || rp.tchan[tile] != c) : tile != c)
+                return LFD_EINTERNAL;
+        }
+    }
+    for (int64_t idx : rp.single) {
+        if (!mark[idx] || seen[idx]) return LFD_EINTERNAL;
+        seen[idx] = 1;
+    }
+    for (size_t i = 0; i < mark.size(); ++i)
+        if (mark[i] != seen[i]) return LFD_EINTERNAL;
+    return LFD_OK;
+}

@@ -182,3 +182,18 @@ def test_serving_arena_free_list(lib, seed):
     """The serving arena's first-fit free list against a byte-map model."""
     assert lib.lfd_selftest_freelist(seed, 400) == lfd.LFD_OK
     assert lib.lfd_selftest_freelist(seed, 0) == lfd.LFD_EINVAL
+
+
+@pytest.mark.parametrize("seed,N,Nz,k,L", [(1, 5, 3, 5, 15), (2, 15, 4, 11, 41), (3, 3, 2, 23, 20),
+                                           (4, 15, 2, 23, 90), (5, 7, 5, 31, 30)])
+def test_exact_runs_plan(lib, seed, N, Nz, k, L):
+    """The plan of runs for the exact low-sensitivity sums covers every listed
+    voxel once, along lenslet rows / columns of one channel, within limits
+    (k = 31 with N = 7 gives PSF rows of 217 taps; k = 23 with N = 15 345)."""
+    assert lib.lfd_selftest_exact_runs(seed, N, Nz, k, L) == lfd.LFD_OK
+
+
+def test_exact_runs_plan_rejects_bad_shapes(lib):
+    assert lib.lfd_selftest_exact_runs(1, 4, 2, 5, 10) == lfd.LFD_EINVAL   # even Nnum
+    assert lib.lfd_selftest_exact_runs(1, 5, 2, 4, 10) == lfd.LFD_EINVAL   # even k
+    assert lib.lfd_selftest_exact_runs(1, 5, 0, 5, 10) == lfd.LFD_EINVAL
