@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--cap", type=int, default=40)
     p.add_argument("--depths", type=int, default=None,
                    help="override the number of depths (small cases for profiler captures)")
+    p.add_argument("--lenslets", type=int, default=None,
+                   help="override the lenslets per side (small cases for profiler captures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-fp32-ref", action="store_true")
@@ -167,12 +169,17 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ inputs --
-def make_inputs(cfg: int, depths=None):
+def make_inputs(cfg: int, depths=None, lenslets=None):
     """PSF, ground truth and the seeded parameters of the workload (optionally
-    with fewer depths, for small profiler cases)."""
+    with another number of depths or lenslets, for small profiler cases)."""
     import dataclasses
     from paper_2208_11422_gb300 import synth
     g = synth.CONFIGS[cfg]
+    if lenslets:
+        g = dataclasses.replace(g, lenslets=lenslets,
+                                beads=max(1, g.beads * lenslets ** 2 // g.lenslets ** 2),
+                                filaments=g.filaments * lenslets // g.lenslets,
+                                name=g.name + "_%dl" % lenslets)
     if depths:
         g = dataclasses.replace(g, nz=depths, z_c=depths // 2,
                                 beads=max(1, g.beads * depths // g.nz),
@@ -218,6 +225,57 @@ def cpu_baseline_sample(cfg: int, psf=None):
               "(%dx%d lenslets, Nz %d, PSF %d px) took %.2f s; scaled to the full %dx%d frame by the "
               "exact multiply-add ratio %.1f" % (Hc, Wc, Lc, Lc, g.nz, g.P, dt, g.W, g.H, ratio))
     return it_s, dt, sample, cores
+
+
+# ------------------------------------------------------ accuracy vs oracle --
+ACC_CROP = 256     # crop 0 of the four seeded 256x256 test crops (default_rng(300))
+ACC_BLOCK = 64     # backprojection checked at every depth of the crop's central 64x64 voxels
+
+
+def accuracy_regions(g):
+    """(i0, j0) of the forward crop and of the backprojection block."""
+    rng = np.random.default_rng(300)
+    i0 = int(rng.integers(0, g.H - ACC_CROP + 1))
+    j0 = int(rng.integers(0, g.W - ACC_CROP + 1))
+    d = (ACC_CROP - ACC_BLOCK) // 2
+    return (i0, j0), (i0 + d, j0 + d)
+
+
+def ratio_like_image(g):
+    """The backprojection's input for the accuracy check: uniform in [0.5, 1.5]."""
+    from paper_2208_11422_gb300 import synth
+    return synth.random_image(7, g.H, g.W, 0.5, 1.5)
+
+
+def gpu_crop_outputs(lfd, torch, ctx, g, vt_d, r_d):
+    """A path's full-frame forward of the ground truth and backprojection of
+    the ratio-like image, cut to the accuracy regions (host arrays)."""
+    (i0, j0), (b0, b1) = accuracy_regions(g)
+    hv = torch.empty((g.H, g.W), device=vt_d.device)
+    ht = torch.empty((g.nz, g.H, g.W), device=vt_d.device)
+    lfd.lfd_forward(ctx, vt_d, hv)
+    lfd.lfd_backward(ctx, r_d, ht)
+    torch.cuda.synchronize()
+    f = hv[i0:i0 + ACC_CROP, j0:j0 + ACC_CROP].cpu().numpy()
+    b = ht[:, b0:b0 + ACC_BLOCK, b1:b1 + ACC_BLOCK].cpu().numpy()
+    del hv, ht
+    return f, b
+
+
+def oracle_crop_values(g, psf, vt, r):
+    """The FP64 oracle on the accuracy regions (part of the CPU-baseline leg)."""
+    import oracle
+    (i0, j0), (b0, b1) = accuracy_regions(g)
+    psf64 = psf.astype(np.float64)
+    f = oracle.forward_crop(psf64, g.nnum, vt, i0, i0 + ACC_CROP, j0, j0 + ACC_CROP)
+    b = oracle.backward_block(psf64, g.nnum, r, 0, g.nz, b0, b0 + ACC_BLOCK, b1, b1 + ACC_BLOCK)
+    return f, b
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 # ---------------------------------------------------------------- GPU arm --
@@ -330,11 +388,13 @@ def fft_roofline(g, plan, prec, stage, peaks, peak_src, fp32_peak, smax, spectra
     return roof
 
 
-def time_path(lfd, torch, dev, psf_d, g, y_d, variant, precision, iters, warm, stream):
-    """RL iterations/s of one path; returns (it/s, stage times, final volume)."""
+def time_path(lfd, torch, dev, psf_d, g, y_d, variant, precision, iters, warm, stream, acc=None):
+    """RL iterations/s of one path; returns (it/s, stage times, final volume,
+    crop outputs for the accuracy check or None). acc: (vt_d, r_d) or None."""
     ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W,
                          lfd.lfd_default_options(precision=precision, variant=variant))
     try:
+        crops = gpu_crop_outputs(lfd, torch, ctx, g, *acc) if acc else None
         v = torch.ones((g.nz, g.H, g.W), device=dev)
         if warm:
             lfd.lfd_rl_iterate(ctx, y_d, v, warm)
@@ -346,7 +406,7 @@ def time_path(lfd, torch, dev, psf_d, g, y_d, variant, precision, iters, warm, s
         lfd.lfd_rl_iterate(ctx, y_d, v, iters, False, stream)
         b.record(stream)
         torch.cuda.synchronize()
-        return iters / (a.elapsed_time(b) / 1e3), lfd.lfd_stage_times(ctx), v
+        return iters / (a.elapsed_time(b) / 1e3), lfd.lfd_stage_times(ctx), v, crops
     finally:
         lfd.lfd_destroy(ctx)
 
@@ -363,7 +423,7 @@ def run_lfd(args, rank, world, local):
     prec = args.precision or "bf16x3"
     steps = args.steps if args.steps is not None else 5
     warm = max(3, args.warmup)
-    g, psf, vt = make_inputs(args.config, args.depths)
+    g, psf, vt = make_inputs(args.config, args.depths, args.lenslets)
     psf_d = torch.from_numpy(psf).to(dev)
     stream = torch.cuda.current_stream()
 
@@ -378,8 +438,21 @@ def run_lfd(args, rank, world, local):
     lfd.lfd_forward(ctx, vt_d, hv)
     torch.cuda.synchronize()
     y = synth.poisson_data(hv.cpu().numpy(), g.scale, g.background, 200 + args.config)
-    del vt_d, hv
+    del hv
     y_d = torch.from_numpy(y).to(dev)
+    # accuracy against the oracle (rank 0 at N = 1, with the CPU-baseline leg):
+    # every path's forward of the ground truth and backprojection of a
+    # ratio-like image on crop 0 of the four seeded test crops
+    do_acc = rank == 0 and world == 1 and not args.no_cpu_baseline and not args.depths \
+        and not args.lenslets
+    acc_in = None
+    gpu_crops = {}
+    if do_acc:
+        r_img = ratio_like_image(g)
+        acc_in = (vt_d, torch.from_numpy(r_img).to(dev))
+        gpu_crops[(variant, prec)] = gpu_crop_outputs(lfd, torch, ctx, g, *acc_in)
+    else:
+        del vt_d
     v = torch.ones((g.nz, g.H, g.W), device=dev)
 
     # warm-up (untimed)
@@ -461,8 +534,10 @@ def run_lfd(args, rank, world, local):
             if (var, pr) == (variant, prec):
                 continue
             n_it = 1 if (var, pr) == ("direct", "fp32") else steps
-            it_s, st_ms, vo = time_path(lfd, torch, dev, psf_d, g, y_d, var, pr, n_it,
-                                        0 if n_it == 1 else 2, stream)
+            it_s, st_ms, vo, crops = time_path(lfd, torch, dev, psf_d, g, y_d, var, pr, n_it,
+                                               0 if n_it == 1 else 2, stream, acc_in)
+            if crops is not None:
+                gpu_crops[(var, pr)] = crops
             rel = rel32 = None
             if n_it == steps:
                 rel = float(torch.linalg.vector_norm(vo - v_head) / torch.linalg.vector_norm(v_head))
@@ -513,10 +588,23 @@ def run_lfd(args, rank, world, local):
     roof["stage_ms"] = stage_ms
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.depths:
+    accuracy = None
+    if do_acc:
+        del acc_in, vt_d
+        torch.cuda.empty_cache()
         it_s, dt, sample, cores = cpu_baseline_sample(args.config, psf)
         cpu = {"value": it_s, "unit": "RL iterations/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "extrapolated": True, "sample_seconds": dt}
+        t0 = time.perf_counter()
+        ref_f, ref_b = oracle_crop_values(g, psf, vt, r_img)
+        (i0, j0), (b0, b1) = accuracy_regions(g)
+        accuracy = {"forward_crop": [i0, j0, ACC_CROP], "backward_block": [b0, b1, ACC_BLOCK, g.nz],
+                    "inputs": "forward: the ground-truth volume; backprojection: an image uniform "
+                              "in [0.5, 1.5]; oracle: FP64 direct summation",
+                    "oracle_seconds": time.perf_counter() - t0, "paths": {}}
+        for (var, pr), (gf, gb) in gpu_crops.items():
+            accuracy["paths"][PATH_NAMES[(var, pr)]] = {"forward_rel_l2": rel_l2(gf, ref_f),
+                                                        "backward_rel_l2": rel_l2(gb, ref_b)}
 
     clocks = clk.summary()
     out = {
@@ -526,9 +614,9 @@ def run_lfd(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
         "data": "synthetic (seeded beads + filaments, Poisson noise)",
-        "config": frame_config(g, prec, variant, world),
+        "config": frame_config(g, world), "path": {"variant": variant, "precision": prec},
         "e2e": e2e, "e2e_volume_roundtrip": e2e_rt, "gpu_launches": launches, "clocks": clocks,
-        "roofline": roof, "cpu_baseline": cpu, "paths": paths,
+        "roofline": roof, "cpu_baseline": cpu, "paths": paths, "accuracy_vs_oracle": accuracy,
         "rel_l2_vs_fft_fp32_after_%d_iterations" % steps: head_vs_fp32,
         "entropy": ent, "predicted_iteration": pred,
     }
@@ -752,17 +840,19 @@ def run_serve(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
-def frame_config(g, prec, variant, world):
-    """The `config` object of the frame workload (both arms print the same)."""
+def frame_config(g, world):
+    """The `config` object of the frame workload (both arms print the same; the
+    arithmetic each arm ran is in its `dtype` and `path`)."""
     return {"workload": g.name, "H": g.H, "W": g.W, "Nnum": g.nnum, "Nz": g.nz, "P": g.P,
-            "precision": prec, "variant": variant,
             "parallelism": "replicas" if world > 1 else "single GPU",
             "l2": "inputs larger than L2 (volume %.2f GB)" % (g.nz * g.H * g.W * 4 / 1e9)}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle on bounded samples of the workload
-    (one RL iteration on a crop per step, scaled to the frame)."""
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload.
+    One step is one oracle RL iteration on a 195x195 px crop (all depths, the
+    full PSF); `ms_per_step` is that measured crop iteration, and `value` the
+    full frame's iterations/s extrapolated by the exact multiply-add ratio."""
     if rank != 0:
         return
     steps = args.steps if args.steps is not None else 1
@@ -784,11 +874,14 @@ def run_reference(args, rank, world):
         "impl": "reference",
         "metric": "RL iterations/s, 2025x2025 px x 51 depths, PSF 345 px (Nnum 15)",
         "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps, "warmup": warm,
-        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": statistics.mean(vals) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": frame_config(g, args.precision or "bf16x3", args.variant, world),
+        "config": frame_config(g, world), "path": {"variant": "oracle", "precision": "f64"},
+        "extrapolated": True,
+        "extrapolation": {"step": "one FP64 RL iteration on a %dx%d px crop (measured: ms_per_step)"
+                                  % (Hc, Hc), "multiply_add_ratio_to_full_frame": ratio},
         "cpu_baseline": {"value": value, "unit": "RL iterations/s", "cores": cores,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample, "extrapolated": True},
         "e2e": {"value": value, "unit": "RL iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -197,29 +197,31 @@ lfd_status lfd_autotune(const float* psf, int P, int Nnum, int Nz, int H, int W,
  * Synchronises the stream. */
 lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda_stream);
 
-/* DCT entropy of a z-maximum projection image, without allocating memory.
+/* Image-quality value of a z-maximum projection image, without allocating memory.
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc, for example a host application that owns all device
  * memory and gives a plug-in only fixed buffers, or a real-time acquisition loop
  * that cannot afford the device-wide synchronisation an allocation may cause.
- * It computes the same quantity as lfd_quality (Eq. 12 over the triangle of
- * Eq. 6), from the image instead of the volume, and needs no context.
- *   mip            [H][W] FP32 image in device memory (e.g. max over z of v)
+ * It returns the same value as lfd_quality, computed from the projection image
+ * instead of the volume, and needs no context.
+ *   mip            [H][W] FP32 image in device (or managed) memory, e.g. the
+ *                  maximum over z of a volume
  *   H, W           1..4096 each
  *   XS, YS         region width / height: 1..min(W, 128) and 1..min(H, 128)
  *                  (lfd_region_size gives the paper's values)
  *   l2_over_region as in lfd_options
- *   entropy        one double in device memory; receives the entropy
+ *   entropy        one double in device (or managed) memory; receives the value
  * Intermediates live in one static device array of about 4.2 MB that every
  * GPU loading the library holds until the process exits. Sizes beyond the
- * limits above return LFD_EINVAL with a message on stderr; nothing is
- * allocated, by this function or on its behalf. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Every call shares
- * the array and leaves its contents behind (each call writes every entry it
- * reads before reading it), so calls that may overlap on the GPU (different
- * streams, or different host threads) race and must be serialised by the
- * caller. Asynchronous: the result is ready when the stream reaches it.
+ * limits above, and host pointers (this function stages nothing), return
+ * LFD_EINVAL with a message on stderr; nothing is allocated, by this function
+ * or on its behalf. Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, so the first call on a device
+ * should come before any stream capture. Every call shares the array and
+ * leaves its contents behind (each call writes every entry it reads before
+ * reading it), so calls that may overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.
+ * Asynchronous: the result is ready when the stream reaches it.
  * Errors: LFD_EINVAL, LFD_ECUDA (lookup or launch failure). */
 lfd_status lfd_quality_mip_static(const float* mip, int H, int W, int XS, int YS,
                                   int l2_over_region, double* entropy, void* cuda_stream);
@@ -425,7 +427,9 @@ lfd_status lfd_cancel(lfd_server* srv, uint64_t ticket);
 
 lfd_status lfd_server_stats_get(const lfd_server* srv, lfd_server_stats* stats);
 
-/* Last error message of the server (scheduler or API), "" if none. */
+/* Last error message of the server (scheduler or API), "" if none. The text is
+ * copied under the server's lock into a buffer of the calling thread, valid
+ * until that thread calls lfd_server_last_error again. */
 const char* lfd_server_last_error(const lfd_server* srv);
 
 /* Finishes the requests already admitted, cancels the queued ones, stops the

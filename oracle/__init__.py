@@ -7,8 +7,9 @@ and the two share no code: this package reads only its own C file
 (``lfd_oracle.c``) and numpy.
 
 Contents
-  * ``forward`` / ``backward`` (+ ``*_at`` sampled variants): the light-field
-    projection H and its transpose, direct FP64 summation (lfd_oracle.c).
+  * ``forward`` / ``backward`` (+ ``*_at`` sampled variants, ``forward_crop``
+    and ``backward_block`` for dense blocks): the light-field projection H and
+    its transpose, direct FP64 summation (lfd_oracle.c).
   * ``metric``: z-MIP, orthonormal 2-D DCT (Eqs. 1-4), region size (Eqs. 6-11),
     DCT entropy (Eqs. 5 and 12), stopping rule (Section 2.2).
   * ``rl``: the Richardson-Lucy iteration built from the pieces above.
@@ -61,6 +62,8 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [dp, i, i, i, i, i, dp, ctypes.c_long, ip, dp, i]
                 f.restype = None
+            lib.orc_backward_block.argtypes = [dp, i, i, i, i, i, dp, i, i, i, i, i, i, dp, i]
+            lib.orc_backward_block.restype = None
             lib.orc_macs.argtypes = [i, i, i, i]
             lib.orc_macs.restype = ctypes.c_double
             _lib = lib
@@ -138,6 +141,45 @@ def backward_at(psf, nnum: int, r, vox, nthreads: int | None = None) -> np.ndarr
                             vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                             _dptr(out), nthreads or default_threads())
     return out
+
+
+def backward_block(psf, nnum: int, r, z0: int, z1: int, i0: int, i1: int, j0: int, j1: int,
+                   nthreads: int | None = None) -> np.ndarray:
+    """H^T r at every voxel of the block [z0, z1) x [i0, i1) x [j0, j1), as an
+    array [z1-z0][i1-i0][j1-j0]; the same sums as ``backward_at`` (bit for bit),
+    several neighbouring voxels computed side by side."""
+    psf = _f64(psf)
+    r = _f64(r)
+    Nz, P = _geom(psf, nnum)
+    H, W = r.shape
+    if not (0 <= z0 < z1 <= Nz and 0 <= i0 < i1 <= H and 0 <= j0 < j1 <= W):
+        raise ValueError("block outside the volume")
+    out = np.zeros((z1 - z0, i1 - i0, j1 - j0), np.float64)
+    _load().orc_backward_block(_dptr(psf), P, nnum, Nz, H, W, _dptr(r), z0, z1, i0, i1, j0, j1,
+                               _dptr(out), nthreads or default_threads())
+    return out
+
+
+def forward_crop(psf, nnum: int, v, i0: int, i1: int, j0: int, j1: int,
+                 nthreads: int | None = None) -> np.ndarray:
+    """Hv on the pixels [i0, i1) x [j0, j1) of the sensor, by ``forward`` over
+    a window of the volume. A pixel (i, j) sums the voxels with |i - i'| <= c
+    and |j - j'| <= c (c = (P-1)/2) only, so the window is the crop widened by
+    c on every side (inside the sensor), with its origin moved down to a
+    multiple of Nnum so that every voxel keeps its lenslet phase (i' mod Nnum,
+    j' mod Nnum). Inside the crop the window's forward adds the same terms in
+    the same order as the full frame's: the values are equal bit for bit."""
+    psf = _f64(psf)
+    Nz, P = _geom(psf, nnum)
+    H, W = v.shape[1:]
+    if not (0 <= i0 < i1 <= H and 0 <= j0 < j1 <= W):
+        raise ValueError("crop outside the sensor")
+    c = (P - 1) // 2
+    wy0 = max(0, i0 - c) // nnum * nnum
+    wx0 = max(0, j0 - c) // nnum * nnum
+    wy1, wx1 = min(H, i1 + c), min(W, j1 + c)
+    win = forward(psf, nnum, np.asarray(v)[:, wy0:wy1, wx0:wx1], nthreads)
+    return win[i0 - wy0:i1 - wy0, j0 - wx0:j1 - wx0]
 
 
 def macs_per_projection(P: int, Nz: int, H: int, W: int) -> float:

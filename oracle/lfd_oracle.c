@@ -213,3 +213,67 @@ double orc_macs(int P, int Nz, int H, int W) {
     for (int i = 0; i < W; ++i) sw += imin(P, W + c - i) - imax(0, c - i);
     return (double)Nz * sh * sw;
 }
+
+/* ---------------------------------------------------------- voxel blocks --
+ * backward at every voxel of the block [z0,z1) x [i0,i1) x [j0,j1), written
+ * to out[z-z0][i'-i0][j'-j0]. Each voxel's value is the sum bwd_one forms, in
+ * the same order (PSF taps row by row); eight neighbouring voxels of a row
+ * whose windows lie inside the sensor along x are carried side by side, which
+ * only interleaves independent sums, so the results equal backward_at's bit
+ * for bit.                                                                   */
+typedef struct {
+    job_t j;
+    int z0, i0, i1, j0, j1;
+} blk_t;
+
+static void *bwd_blk(void *arg) {
+    const blk_t *b = (const blk_t *)arg;
+    const job_t *j = &b->j;
+    const int P = j->P, N = j->N, H = j->H, W = j->W, c = (P - 1) / 2;
+    const int ni = b->i1 - b->i0, nj = b->j1 - b->j0;
+    for (long zr = j->lo; zr < j->hi; ++zr) {
+        const int z = b->z0 + (int)(zr / ni), ip = b->i0 + (int)(zr % ni);
+        double *orow = j->out + (size_t)zr * nj;
+        const int mi_lo = imax(0, c - ip), mi_hi = imin(P, H + c - ip);
+        int jp = b->j0;
+        for (; jp + 7 < b->j1; jp += 8) {
+            if (jp - c < 0 || jp + 7 + c >= W) {
+                for (int q = 0; q < 8; ++q) orow[jp + q - b->j0] = bwd_one(j, z, ip, jp + q);
+                continue;
+            }
+            const double *K[8];
+            for (int q = 0; q < 8; ++q) K[q] = PSF_AT(j->psf, N, P, z, ip % N, (jp + q) % N);
+            double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int mi = mi_lo; mi < mi_hi; ++mi) {
+                const double *r = j->in + (size_t)(ip + mi - c) * W + (jp - c);
+                const size_t o = (size_t)mi * P;
+                for (int mj = 0; mj < P; ++mj)
+                    for (int q = 0; q < 8; ++q) s[q] += r[mj + q] * K[q][o + mj];
+            }
+            for (int q = 0; q < 8; ++q) orow[jp + q - b->j0] = s[q];
+        }
+        for (; jp < b->j1; ++jp) orow[jp - b->j0] = bwd_one(j, z, ip, jp);
+    }
+    return NULL;
+}
+
+void orc_backward_block(const double *psf, int P, int N, int Nz, int H, int W,
+                        const double *r, int z0, int z1, int i0, int i1, int j0, int j1,
+                        double *out, int nthreads) {
+    const long total = (long)(z1 - z0) * (i1 - i0);
+    if (total <= 0 || j1 <= j0) return;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((long)nthreads > total) nthreads = (int)total;
+    pthread_t th[256];
+    blk_t jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        job_t base = {psf, P, N, Nz, H, W, r, out, NULL, total * t / nthreads,
+                      total * (t + 1) / nthreads};
+        blk_t b = {base, z0, i0, i1, j0, j1};
+        jobs[t] = b;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, bwd_blk, &jobs[t]);
+    bwd_blk(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+}

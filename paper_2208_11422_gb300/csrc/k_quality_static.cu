@@ -8,7 +8,6 @@
 // output; nothing else is touched.
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "lfd_internal.h"
 
@@ -25,10 +24,6 @@ constexpr long long kQsDoubles =
 // Shared by every call on a device and kept until the process exits
 // (about 4.2 MB per GPU that loads the library).
 static __device__ __align__(256) double g_qs_scratch[kQsDoubles];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_qs_mutex;
-double* g_qs_addr[kMaxDevices] = {};
 
 // orthonormal DCT-II basis C_k(x; Z) = c(k, Z) cos((2x+1) pi k / (2Z)) (Eqs. 2-4)
 __device__ __forceinline__ double qs_basis(int k, int x, int Z) {
@@ -122,21 +117,26 @@ __global__ void k_qs_entropy(int H, int XS, int YS, int l2_over_region, const do
     if (threadIdx.x == 0) out[0] = norm > 0.0 ? -ent / (0.5 * (double)XS * (double)YS) : 0.0;
 }
 
-// device address of the scratch array for the current device, looked up once
+// Device address of the scratch array on the current device. It is looked up
+// on every call (cheap, allocates nothing), so a reloaded module after a
+// device reset never leaves a stale address behind.
 cudaError_t qs_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_qs_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_qs_mutex);
-    if (!g_qs_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_qs_scratch);
-        if (e != cudaSuccess) return e;
-        g_qs_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_qs_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
+}
+
+// true when p is device (or managed) memory the kernels may dereference; a
+// host address handed to them would fault or read the wrong memory
+bool qs_device_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered host pointer may report an error here
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -160,6 +160,12 @@ extern "C" lfd_status lfd_quality_mip_static(const float* mip, int H, int W, int
                      "lfd_quality_mip_static: region %d x %d must lie in 1..min(W, %d) x "
                      "1..min(H, %d)\n",
                      XS, YS, kQsMaxXS, kQsMaxYS);
+        return LFD_EINVAL;
+    }
+    if (!qs_device_ptr(mip) || !qs_device_ptr(entropy)) {
+        std::fprintf(stderr,
+                     "lfd_quality_mip_static: the image and the output must be device memory "
+                     "(this entry point stages nothing)\n");
         return LFD_EINVAL;
     }
     double* s = nullptr;

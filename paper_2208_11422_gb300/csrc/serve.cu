@@ -245,7 +245,7 @@ struct lfd_server {
     std::vector<std::unique_ptr<PsfSet>> sets;
     Arena arena;
     bool started = false, stop = false;
-    std::mutex mu;
+    mutable std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Job*> queue;
     std::unordered_map<uint64_t, Job*> jobs;
@@ -822,7 +822,16 @@ lfd_status lfd_server_stats_get(const lfd_server* cs, lfd_server_stats* out) {
     return LFD_OK;
 }
 
-const char* lfd_server_last_error(const lfd_server* s) { return s ? s->err.c_str() : "NULL server"; }
+// The scheduler thread may replace s->err at any time, so the message is
+// copied under the server's lock into a buffer of the calling thread; the
+// pointer stays valid until this thread's next call.
+const char* lfd_server_last_error(const lfd_server* s) {
+    if (!s) return "NULL server";
+    thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(s->mu);
+    copy = s->err;
+    return copy.c_str();
+}
 
 void lfd_server_destroy(lfd_server* s) {
     if (!s) return;

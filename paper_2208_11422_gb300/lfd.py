@@ -267,6 +267,10 @@ def lfd_quality_mip_static(mip, H: int, W: int, XS: int, YS: int, l2_over_region
                            entropy_out, stream=None):
     """Allocation-free DCT entropy of a device image ``mip`` [H][W]; the result is
     written to ``entropy_out`` (a float64 CUDA tensor of one element, or an address)."""
+    for name, x in (("mip", mip), ("entropy_out", entropy_out)):
+        if not isinstance(x, int) and not getattr(x, "is_cuda", False):
+            raise ValueError("lfd_quality_mip_static: %s must be a CUDA tensor or a device "
+                             "address (the call stages nothing)" % name)
     out = entropy_out if isinstance(entropy_out, int) else entropy_out.data_ptr()
     st = load().lfd_quality_mip_static(_ptr(mip), H, W, XS, YS, int(l2_over_region), out,
                                        _stream(stream))

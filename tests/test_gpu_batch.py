@@ -172,3 +172,62 @@ def test_batch_rejects_too_many_frames():
         import torch
         lfd.lfd_create(torch.from_numpy(psf).to("cuda:0"), g.P, g.nnum, g.nz, g.H, g.W,
                        lfd.lfd_default_options(max_frames=2))
+
+
+def test_autotune_picks_the_faster_fft_size_and_its_context_matches_oracle():
+    """lfd_autotune on the mid-size frame (615 px, 31 depths, PSF 165 px) with 8
+    frames: the size it returns is 32 or 64, its time is within noise of the
+    faster of the two sizes timed here directly, and a context created with
+    that size reproduces the stored FP64 oracle run (frame 0 of the batch)."""
+    import os
+    import time
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    g = synth.CONFIGS[1]
+    psf = synth.make_psf(1)
+    dev = torch.device("cuda:0")
+    psf_d = torch.from_numpy(psf).to(dev)
+    nf = 8
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "lf_mid_615px_31z_psf165.npz"))
+    y = (d["y_counts"].astype(np.float64) + float(d["background"])).astype(np.float32)
+    ys = torch.from_numpy(np.stack([y] * nf)).to(dev)
+    opt = lfd.lfd_default_options(precision="bf16x3", variant="fft", max_frames=nf)
+    best, tuned_ms = lfd.lfd_autotune(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+    assert best in (32, 64)
+    direct = {}
+    for F in (32, 64):
+        o = lfd.lfd_default_options(precision="bf16x3", variant="fft", max_frames=nf, fft_size=F)
+        ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, o)
+        try:
+            v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+            lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, 1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, 3)
+            b.record()
+            torch.cuda.synchronize()
+            direct[F] = a.elapsed_time(b) / 3
+        finally:
+            lfd.lfd_destroy(ctx)
+    fast = min(direct, key=direct.get)
+    print("autotune: picked F=%d at %.2f ms/iteration; timed directly %s" % (best, tuned_ms, direct))
+    assert tuned_ms <= 1.15 * direct[fast]
+    if max(direct.values()) > 1.15 * min(direct.values()):
+        assert best == fast
+    opt.fft_size = best
+    ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+    try:
+        assert lfd.lfd_get_fft_plan(ctx)["F"] == best
+        v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+        done, pred, ent, _ = lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, int(d["n_iter"]))
+        vox = d["sample_vox"]
+        v0 = v[0].cpu().numpy()
+        e = rel_l2(v0[vox[:, 0], vox[:, 1], vox[:, 2]], d["v_last"])
+        print("autotuned F=%d: frame 0 sampled rel-L2 %.2e vs oracle, predicted %d (oracle %d)"
+              % (best, e, pred[0], int(d["predicted"])))
+        assert e <= TOL_RL["bf16x3"]
+        assert pred[0] == int(d["predicted"])
+    finally:
+        lfd.lfd_destroy(ctx)

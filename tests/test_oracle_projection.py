@@ -155,3 +155,40 @@ def test_mac_count(orc):
                     if 0 <= i + mi - c < H and 0 <= j + mj - c < W:
                         brute += 1
     assert orc.macs_per_projection(P, Nz, H, W) == Nz * brute
+
+
+# crops (i0, i1, j0, j1) of a 60 x 75 px sensor: interior, at the borders,
+# origins not on the lenslet grid, a single pixel, the whole sensor
+CROPS = [(20, 41, 31, 52), (0, 13, 0, 9), (47, 60, 61, 75), (7, 8, 44, 45), (0, 60, 0, 75)]
+
+
+@pytest.mark.parametrize("crop", CROPS)
+def test_forward_crop_equals_full_forward(orc, crop):
+    """forward_crop runs the forward model over a window of the volume; inside
+    the crop it adds the same terms in the same order as the full frame."""
+    N, Nz, P = 3, 3, 15
+    H, W = 60, 75
+    psf = synth.random_psf(31, N, Nz, P).astype(np.float64)
+    v = synth.random_volume(32, Nz, H, W).astype(np.float64)
+    v[v < 0.6] = 0.0                 # sparse, like the bead volumes
+    i0, i1, j0, j1 = crop
+    full = orc.forward(psf, N, v)
+    assert np.array_equal(orc.forward_crop(psf, N, v, i0, i1, j0, j1), full[i0:i1, j0:j1])
+
+
+@pytest.mark.parametrize("crop", CROPS)
+def test_backward_block_equals_full_backward(orc, crop):
+    """backward_block gives every voxel of the block the sum backward_at forms;
+    the block's rows mix voxels whose windows are cut by the sensor and voxels
+    computed eight side by side."""
+    N, Nz, P = 3, 3, 15
+    H, W = 60, 75
+    psf = synth.random_psf(33, N, Nz, P).astype(np.float64)
+    r = synth.random_image(34, H, W, 0.1, 2.0).astype(np.float64)
+    i0, i1, j0, j1 = crop
+    full = orc.backward(psf, N, r)
+    blk = orc.backward_block(psf, N, r, 1, Nz, i0, i1, j0, j1)
+    assert np.array_equal(blk, full[1:, i0:i1, j0:j1])
+    zz, ii, jj = np.meshgrid(np.arange(1, Nz), np.arange(i0, i1), np.arange(j0, j1), indexing="ij")
+    vox = np.stack([zz.ravel(), ii.ravel(), jj.ravel()], 1)
+    assert np.array_equal(orc.backward_at(psf, N, r, vox), blk.ravel())
