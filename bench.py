@@ -37,7 +37,7 @@ def parse():
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lfd", choices=["lfd", "reference"])
-    p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
+    p.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16", "bf16x3"])
     p.add_argument("--variant", default="fft", choices=["fft", "direct"])
     p.add_argument("--config", type=int, default=WORKLOAD_CFG)
     p.add_argument("--workload", default="large", choices=["large", "batch", "serve"],
@@ -281,7 +281,7 @@ def rel_l2(a, b) -> float:
 # ---------------------------------------------------------------- GPU arm --
 PATH_NAMES = {("fft", "fp32"): "fft_fp32", ("fft", "bf16x3"): "fft_bf16x3", ("fft", "bf16"): "fft_bf16",
               ("direct", "bf16x3"): "direct_bf16x3", ("direct", "bf16"): "direct_bf16",
-              ("direct", "fp32"): "direct_fp32"}
+              ("direct", "tf32"): "direct_tf32", ("direct", "fp32"): "direct_fp32"}
 
 
 def fft_plan_numbers(g, plan):
@@ -306,17 +306,24 @@ NCU_TRAFFIC = {
 }
 
 
+# dense tensor rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
 def direct_tensor_roofline(g, prec, st_ms):
     """Tensor-pipe fraction of the direct (implicit GEMM) projections: the
     algorithmic flops 2*H*W*Nz*P^2 per projection, and the executed ones (the
     dense tap union (k+2)^2/k^2, three products per term in split BF16),
-    against the sustained BF16 peak (the projections run inside a long step)."""
+    against the sustained BF16 peak (the projections run inside a long step);
+    TF32 against that peak times the nominal TF32 / BF16 ratio."""
     peaks, src = measured_peaks()
     k = g.psf_lenslets
     fl = algorithmic_flops_per_projection(g)
     ex = fl * ((k + 2) / k) ** 2 * (3 if prec == "bf16x3" else 1)
     ms = max(st_ms[0], st_ms[2])
-    peak = peaks["bf16_tflops_sustained"]
+    peak = peaks["bf16_tflops_sustained"] * (TF32_OVER_BF16 if prec == "tf32" else 1.0)
+    if prec == "tf32":
+        src += ", x %.3f nominal TF32/BF16" % TF32_OVER_BF16
     return {"kernel": "forward projection" if st_ms[0] >= st_ms[2] else "backprojection",
             "algorithmic_TFLOPs": fl / (ms / 1e3) / 1e12, "executed_TFLOPs": ex / (ms / 1e3) / 1e12,
             "peak": peak, "frac_algorithmic": fl / (ms / 1e3) / 1e12 / peak,
@@ -530,7 +537,7 @@ def run_lfd(args, rank, world, local):
     if not args.skip_fp32_ref:
         v_fp32 = None
         for var, pr in (("fft", "fp32"), ("fft", "bf16x3"), ("fft", "bf16"), ("direct", "bf16x3"),
-                        ("direct", "bf16"), ("direct", "fp32")):
+                        ("direct", "bf16"), ("direct", "tf32"), ("direct", "fp32")):
             if (var, pr) == (variant, prec):
                 continue
             n_it = 1 if (var, pr) == ("direct", "fp32") else steps
@@ -551,7 +558,7 @@ def run_lfd(args, rank, world, local):
                 "forward_ms": st_ms[0], "backward_ms": st_ms[2],
                 "rel_l2_vs_headline_after_%d_iterations" % steps: rel,
                 "rel_l2_vs_fft_fp32_after_%d_iterations" % steps: rel32}
-            if var == "direct" and pr in ("bf16", "bf16x3"):
+            if var == "direct" and pr in ("bf16", "bf16x3", "tf32"):
                 paths[PATH_NAMES[(var, pr)]]["tensor_roofline"] = direct_tensor_roofline(g, pr, st_ms)
             if vo is not v_fp32:
                 del vo
@@ -580,9 +587,12 @@ def run_lfd(args, rank, world, local):
     else:
         dom_ms = max(stage[0], stage[2])
         dom = "forward projection" if stage[0] >= stage[2] else "backprojection"
-        peak = peaks["bf16_tflops_sustained"]
+        ratio = TF32_OVER_BF16 if prec == "tf32" else 1.0
+        peak = peaks["bf16_tflops_sustained"] * ratio
         roof = {"bound": "tensor", "kernel": dom, "achieved": fl / (dom_ms / 1e3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": "bf16_tflops_sustained (%s)" % peak_src}
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "bf16_tflops_sustained (%s)%s" % (
+                    peak_src, " x %.3f nominal TF32/BF16" % ratio if prec == "tf32" else "")}
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof.setdefault("traffic", None)
     roof["stage_ms"] = stage_ms
@@ -612,7 +622,7 @@ def run_lfd(args, rank, world, local):
         "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": tmax * 1e3 / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
         "data": "synthetic (seeded beads + filaments, Poisson noise)",
         "config": frame_config(g, world), "path": {"variant": variant, "precision": prec},
         "e2e": e2e, "e2e_volume_roundtrip": e2e_rt, "gpu_launches": launches, "clocks": clocks,

@@ -66,7 +66,10 @@ typedef enum {
  * FP64 reductions in every mode). */
 typedef enum {
     LFD_FP32 = 0,   /* FP32 inputs and FP32 FMA accumulation on the CUDA cores   */
-    LFD_TF32 = 1,   /* reserved                                                  */
+    LFD_TF32 = 1,   /* TF32 on tcgen05 tensor cores, FP32 accumulation (LFD_DIRECT
+                       only; LFD_EUNSUPPORTED with LFD_FFT): the PSF, the iterate
+                       and the ratio image rounded to TF32 (10-bit mantissa,
+                       round to nearest), one product per term               */
     LFD_BF16 = 2,   /* BF16 on tcgen05 tensor cores, FP32 accumulation. LFD_DIRECT:
                        PSF and data rounded to BF16, one product per term.
                        LFD_FFT: the PSF spectra rounded once to BF16 (4 bytes
@@ -103,8 +106,8 @@ typedef struct {
 
 /* How the two projections are computed (same results up to rounding). */
 typedef enum {
-    LFD_DIRECT = 0,  /* polyphase implicit GEMM: tcgen05 (BF16 precisions) or CUDA
-                        cores (FP32)                                                */
+    LFD_DIRECT = 0,  /* polyphase implicit GEMM: tcgen05 (BF16, split BF16, TF32) or
+                        CUDA cores (FP32)                                           */
     LFD_FFT = 1      /* overlap-save FFT on the lenslet grid with cached PSF spectra,
                         FP32 transforms; complex contractions in FP32 on the CUDA
                         cores (LFD_FP32), or on tcgen05 in split BF16 (LFD_BF16X3)
@@ -124,7 +127,8 @@ void lfd_default_options(lfd_options* opt);
  * Work done here: the PSF is repacked into the polyphase layout the projection
  * kernels read, H^T 1 is computed, and the metric's cosine tables are built.
  * Errors: LFD_EINVAL (shape rules above, NULL out), LFD_ENOMEM, LFD_ECUDA,
- * LFD_EUNSUPPORTED (precision needs tensor cores the device lacks).
+ * LFD_EUNSUPPORTED (precision needs tensor cores the device lacks; LFD_TF32
+ * with LFD_FFT; max_frames > 1 with LFD_DIRECT).
  * On error *out is NULL. */
 lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
                       const lfd_options* opt, void* cuda_stream, lfd_ctx** out);
@@ -225,6 +229,47 @@ lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda
  * Errors: LFD_EINVAL, LFD_ECUDA (lookup or launch failure). */
 lfd_status lfd_quality_mip_static(const float* mip, int H, int W, int XS, int YS,
                                   int l2_over_region, double* entropy, void* cuda_stream);
+
+/* ------------------------------------------------------------ depth split --
+ * Section 2.1 and Fig. 1 of the paper divide the depth layers (and the PSF
+ * slices that belong to them) among several GPUs. A context made over the
+ * depths [z0, z1) of a PSF (psf + z0 * Nnum * Nnum * P * P, Nz = z1 - z0)
+ * owns that part of the volume; the forward projection is the sum over all
+ * parts of their partial projections, the backprojection and the update are
+ * per depth, the z-maximum projection is the maximum of the parts', and the
+ * flux the sum of theirs. These calls cut one RL iteration (model above) at
+ * those two exchange points; the caller does the reductions between them
+ * (paper_2208_11422_gb300/depth_split.py does them with torch.distributed):
+ *   lfd_split_load(ctx, v)         iterate <- v, this part's [Nz][H][W] (host or device)
+ *   per iteration:
+ *     lfd_split_forward(ctx, hv)   hv [H][W] (device) <- partial H v of the iterate
+ *     (sum hv over all parts)
+ *     lfd_split_update(ctx, y, hv, mip, flux)
+ *                                  r = y / (hv + eps); v <- max(0, v H^T r / H^T 1);
+ *                                  mip [H][W] <- max over this part's depths of the new v;
+ *                                  *flux (one double) <- sum(H^T 1 * v) over this part
+ *                                  (y, hv, mip, flux in device memory)
+ *     (max of mip and sum of flux over all parts; lfd_quality_mip gives the
+ *      entropy of the reduced mip, and the stopping rule of lfd_rl_iterate
+ *      applies to the entropies)
+ *   lfd_split_store(ctx, v, previous)  v <- the current iterate (previous = 0)
+ *                                  or the one before the last update (1)
+ * All calls are ordered on cuda_stream; lfd_split_store with a host v and
+ * lfd_quality_mip synchronise it. lfd_forward and lfd_rl_iterate reuse the
+ * iterate buffers: after them lfd_split_load is needed again.
+ * Errors: LFD_EINVAL (NULL or host pointers where device memory is required,
+ * no iterate loaded, no previous iterate), LFD_ECUDA, LFD_ETIMEDOUT. */
+lfd_status lfd_split_load(lfd_ctx* ctx, const float* v, void* cuda_stream);
+lfd_status lfd_split_forward(lfd_ctx* ctx, float* hv_part, void* cuda_stream);
+lfd_status lfd_split_update(lfd_ctx* ctx, const float* y, const float* hv, float* mip_part,
+                            double* flux_part, void* cuda_stream);
+lfd_status lfd_split_store(lfd_ctx* ctx, float* v, int previous, void* cuda_stream);
+
+/* DCT entropy (Eq. 12 over the region of Eq. 6) of a z-maximum projection
+ * image mip [H][W] (host or device) with the context's region and tables; the
+ * metric step of lfd_rl_iterate on an image reduced outside the library (the
+ * depth split above). Synchronises the stream. */
+lfd_status lfd_quality_mip(lfd_ctx* ctx, const float* mip, double* entropy, void* cuda_stream);
 
 /* Frees the context and everything it owns. NULL is a no-op. */
 void lfd_destroy(lfd_ctx* ctx);

@@ -221,7 +221,41 @@ __global__ void k_entropy(const double* __restrict__ coef, const double* __restr
     }
 }
 
+// r = y / (hv + eps) per pixel, 0 where hv + eps <= 0 (the ratio of an RL
+// iteration whose forward projection was summed outside the library)
+__global__ void k_ratio_image(const float* __restrict__ y, const float* __restrict__ hv, float eps,
+                              int64_t n, float* __restrict__ r) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float den = hv[e] + eps;
+        r[e] = den > 0.f ? y[e] / den : 0.f;
+    }
+}
+
+// out[0] = sum of p[0..n) in a fixed order (one block)
+__global__ void k_sum_doubles(const double* __restrict__ p, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) out[0] = a;
+}
+
 }  // namespace
+
+cudaError_t launch_ratio_image(const float* y, const float* hv, float eps, int64_t n, float* r,
+                               cudaStream_t st) {
+    int64_t b = (n + 255) / 256;
+    k_ratio_image<<<(unsigned)(b < 4864 ? (b > 0 ? b : 1) : 4864), 256, 0, st>>>(y, hv, eps, n, r);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_doubles(const double* p, int64_t n, double* out, cudaStream_t st) {
+    k_sum_doubles<<<1, 256, 0, st>>>(p, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_update(const float* vin, float* vout, __nv_bfloat16* hi, __nv_bfloat16* lo,
                           const float* parts, int nsplit, const float* inv, const Geo& g,

@@ -144,11 +144,13 @@ FftBuffers fbufs(const lfd_ctx* ctx) {
     return b;
 }
 
-// direct-variant tensor-core path
+// direct-variant tensor-core path (BF16, split BF16 or TF32)
 bool uses_tc(const lfd_ctx* ctx) {
     return ctx->opt.variant == LFD_DIRECT &&
-           (ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3);
+           (ctx->opt.precision == LFD_BF16 || ctx->opt.precision == LFD_BF16X3 ||
+            ctx->opt.precision == LFD_TF32);
 }
+bool uses_tf32(const lfd_ctx* ctx) { return uses_tc(ctx) && ctx->opt.precision == LFD_TF32; }
 bool uses_lo(const lfd_ctx* ctx) { return ctx->opt.precision == LFD_BF16X3; }
 // FFT-variant contraction: tensor-core products per term (3 split BF16, 2 BF16
 // PSF spectra), 0 for FP32 on the CUDA cores
@@ -200,7 +202,8 @@ lfd_status ensure_stage(lfd_ctx* ctx, bool vol) {
 }
 
 void free_all(lfd_ctx* ctx) {
-    void* ptrs[] = {ctx->W32, ctx->Wb[0], ctx->Wb[1], ctx->Vp32[0], ctx->Vp32[1], ctx->Vpb[0],
+    void* ptrs[] = {ctx->Vpt, ctx->Rpt, ctx->WT,
+                    ctx->W32, ctx->Wb[0], ctx->Wb[1], ctx->Vp32[0], ctx->Vp32[1], ctx->Vpb[0],
                     ctx->Vpb[1], ctx->Rp32, ctx->Rpb[0], ctx->Rpb[1], ctx->Fwd, ctx->Bwd,
                     ctx->invHt1, ctx->ypoly, ctx->mip, ctx->cosW, ctx->cosH, ctx->G, ctx->rowE2,
                     ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
@@ -324,14 +327,14 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (!make_geo(P, Nnum, Nz, H, W, &g, &why)) return LFD_EINVAL;
     lfd_options opt;
     if (opt_in) opt = *opt_in; else lfd_default_options(&opt);
-    if (opt.precision < LFD_FP32 || opt.precision > LFD_BF16X3 || opt.precision == LFD_TF32)
-        return LFD_EINVAL;
+    if (opt.precision < LFD_FP32 || opt.precision > LFD_BF16X3) return LFD_EINVAL;
     if (!(opt.eps >= 0.f)) return LFD_EINVAL;
     if (opt.variant != LFD_DIRECT && opt.variant != LFD_FFT) return LFD_EINVAL;
     if (opt.max_frames < 1 || opt.max_frames > 4096) return LFD_EINVAL;
     if (opt.fft_size != 0 && opt.fft_size != 32 && opt.fft_size != 64) return LFD_EINVAL;
     if (!(opt.spectra_lo_tau >= 0.f && opt.spectra_lo_tau < 1.f)) return LFD_EINVAL;
     if (opt.max_frames > 1 && opt.variant != LFD_FFT) return LFD_EUNSUPPORTED;
+    if (opt.precision == LFD_TF32 && opt.variant != LFD_DIRECT) return LFD_EUNSUPPORTED;
     int XS = opt.XS, YS = opt.YS;
     if (XS <= 0 || YS <= 0) {
         if (lfd_region_size(Nnum, H, W, opt.dML_um, opt.Q, opt.NA, opt.lambda_um, &XS, &YS) != LFD_OK)
@@ -431,7 +434,11 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
         CREATE_TRY(dalloc(ctx, &ctx->Bwd, (int64_t)bparts * g.M_pad * g.Cpad, true));
         CREATE_TRY(dalloc(ctx, &ctx->invHt1, g.M_pad * g.Cpad, true));
         CREATE_TRY(dalloc(ctx, &ctx->ypoly, g.M_pad * g.Spad, true));
-        if (uses_tc(ctx)) {
+        if (uses_tf32(ctx)) {
+            CREATE_TRY(dalloc(ctx, &ctx->WT, wcount, false));
+            CREATE_TRY(dalloc(ctx, &ctx->Vpt, g.rows * g.Cpad, true));
+            CREATE_TRY(dalloc(ctx, &ctx->Rpt, g.rows * g.Spad, true));
+        } else if (uses_tc(ctx)) {
             const int nb = uses_lo(ctx) ? 2 : 1;
             for (int b = 0; b < nb; ++b) {
                 CREATE_TRY(dalloc(ctx, &ctx->Wb[b], wcount, false));
@@ -663,6 +670,7 @@ lfd_status lfd_forward(lfd_ctx* ctx, const float* v, float* y_out, void* cuda_st
         LFD_TRY(ensure_stage(ctx, false));
         yd = ctx->stage_img;
     }
+    ctx->split_cur = -1;  // the iterate buffers are reused below
     if (ctx->fft) {
         const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
         LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
@@ -716,6 +724,157 @@ lfd_status lfd_backward(lfd_ctx* ctx, const float* r, float* v_out, void* cuda_s
         LFD_CK(cudaMemcpyAsync(v_out, vd, nvol * sizeof(float), cudaMemcpyDeviceToHost, st));
         LFD_CK(cudaStreamSynchronize(st));
     }
+    return LFD_OK;
+}
+
+// ------------------------------------------------------------ depth split --
+// One RL iteration cut at its two exchange points, for a context made over a
+// range of depths (Section 2.1, Fig. 1: the depths are divided among GPUs).
+// The caller sums the partial forward projections of all depth ranges and
+// takes the maximum of their partial z-projections and the sum of their flux
+// between the calls.
+
+lfd_status lfd_split_load(lfd_ctx* ctx, const float* v, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!v) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const float* vd = v;
+    if (!is_device_ptr(v)) {
+        LFD_TRY(ensure_stage(ctx, true));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_vol, v, (int64_t)g.Nz * g.H * g.W * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+        vd = ctx->stage_vol;
+    }
+    if (ctx->fft)
+        LFD_CK(launch_poly_volume_cm(vd, g, ctx->Vcm[0], st));
+    else
+        LFD_CK(launch_poly_volume(vd, g, ctx->Vp32[0], ctx->Vpb[0], ctx->Vpb[1], st));
+    ctx->split_cur = 0;
+    ctx->split_prev = 0;
+    return LFD_OK;
+}
+
+lfd_status lfd_split_forward(lfd_ctx* ctx, float* hv_part, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!hv_part || !is_device_ptr(hv_part)) {
+        ctx->err = "hv_part must be device memory";
+        return LFD_EINVAL;
+    }
+    if (ctx->split_cur < 0) {
+        ctx->err = "no iterate loaded (lfd_split_load)";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int cur = ctx->split_cur;
+    if (ctx->fft) {
+        const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
+        LFD_CK(fft_forward(fp, g, fbufs(ctx), 1, ctx->Vcm[cur], hv_part, nullptr, nullptr, nullptr, 0.f,
+                           st, nullptr));
+    } else {
+        LFD_TRY(run_forward(ctx, cur, st));
+        LFD_CK(launch_fwd_finish_image(ctx->Fwd, fwd_parts(ctx), g, hv_part, st));
+    }
+    return LFD_OK;
+}
+
+lfd_status lfd_split_update(lfd_ctx* ctx, const float* y, const float* hv, float* mip_part,
+                            double* flux_part, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!y || !hv || !mip_part || !flux_part || !is_device_ptr(y) || !is_device_ptr(hv) ||
+        !is_device_ptr(mip_part) || !is_device_ptr(flux_part)) {
+        ctx->err = "y, hv, mip_part and flux_part must be device memory";
+        return LFD_EINVAL;
+    }
+    if (ctx->split_cur < 0) {
+        ctx->err = "no iterate loaded (lfd_split_load)";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int cur = ctx->split_cur, nxt = cur ^ 1;
+    const int64_t nimg = (int64_t)g.H * g.W;
+    if (ctx->fft) {
+        const FftPlan& fp = *static_cast<const FftPlan*>(ctx->fft);
+        LFD_CK(launch_ratio_image(y, hv, ctx->opt.eps, nimg, ctx->rimg, st));
+        LFD_CK(launch_poly_image_cm(ctx->rimg, g, ctx->Rcm, st));
+        LFD_CK(fft_backward(fp, g, fbufs(ctx), 1, ctx->Rcm, ctx->Xcm, nullptr, st, nullptr));
+        LFD_CK(exact_bwd(ctx->exact, 1, ctx->rimg, ctx->Xcm, st));
+        LFD_CK(launch_update_cm(ctx->Vcm[cur], ctx->Vcm[nxt], ctx->Xcm, ctx->invcm, g, 1, mip_part,
+                                ctx->flux_part, st));
+    } else {
+        LFD_TRY(ensure_stage(ctx, false));
+        LFD_CK(launch_ratio_image(y, hv, ctx->opt.eps, nimg, ctx->stage_img, st));
+        __nv_bfloat16* rhi = uses_tc(ctx) ? ctx->Rpb[0] : nullptr;
+        __nv_bfloat16* rlo = uses_lo(ctx) ? ctx->Rpb[1] : nullptr;
+        __nv_bfloat16* vhi = uses_tc(ctx) ? ctx->Vpb[0] : nullptr;
+        __nv_bfloat16* vlo = uses_lo(ctx) ? ctx->Vpb[1] : nullptr;
+        LFD_CK(launch_poly_image(ctx->stage_img, g, ctx->Rp32, g.m_base, rhi, rlo, st));
+        LFD_TRY(run_backward(ctx, st));
+        LFD_CK(launch_update(ctx->Vp32[cur], ctx->Vp32[nxt], vhi, vlo, ctx->Bwd, bwd_parts(ctx), ctx->invHt1,
+                             g, mip_part, ctx->flux_part, st));
+    }
+    LFD_CK(launch_sum_doubles(ctx->flux_part, ctx->nflux, flux_part, st));
+    ctx->split_cur = nxt;
+    ctx->split_prev = 1;
+    return LFD_OK;
+}
+
+lfd_status lfd_split_store(lfd_ctx* ctx, float* v, int previous, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!v) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    if (ctx->split_cur < 0 || (previous && !ctx->split_prev)) {
+        ctx->err = previous ? "no previous iterate (no lfd_split_update since lfd_split_load)"
+                            : "no iterate loaded (lfd_split_load)";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int buf = previous ? ctx->split_cur ^ 1 : ctx->split_cur;
+    const bool vdev = is_device_ptr(v);
+    float* vd = v;
+    if (!vdev) {
+        LFD_TRY(ensure_stage(ctx, true));
+        vd = ctx->stage_vol;
+    }
+    if (ctx->fft)
+        LFD_CK(launch_depoly_volume_cm(ctx->Vcm[buf], g, vd, st));
+    else
+        LFD_CK(launch_depoly_volume(ctx->Vp32[buf], g.m_base, g, vd, st));
+    if (!vdev) {
+        LFD_CK(cudaMemcpyAsync(v, vd, (int64_t)g.Nz * g.H * g.W * sizeof(float), cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaStreamSynchronize(st));
+    }
+    return LFD_OK;
+}
+
+lfd_status lfd_quality_mip(lfd_ctx* ctx, const float* mip, double* entropy, void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!mip || !entropy) {
+        ctx->err = "NULL argument";
+        return LFD_EINVAL;
+    }
+    const Geo& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const float* md = mip;
+    if (!is_device_ptr(mip)) {
+        LFD_TRY(ensure_stage(ctx, false));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_img, mip, (int64_t)g.H * g.W * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+        md = ctx->stage_img;
+    }
+    LFD_CK(launch_metric(md, ctx->cosW, ctx->cosH, g.H, g.W, ctx->XS, ctx->YS, ctx->opt.l2_over_region,
+                         ctx->G, ctx->rowE2, ctx->coef, nullptr, 0, ctx->hist, nullptr, st));
+    LFD_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->hist, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LFD_CK(cudaStreamSynchronize(st));
+    *entropy = ctx->host_pinned[0];
     return LFD_OK;
 }
 
@@ -833,6 +992,7 @@ lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int sto
     const Geo& g = ctx->g;
     const int64_t nvol = (int64_t)g.Nz * g.H * g.W, nimg = (int64_t)g.H * g.W, L2 = (int64_t)g.Ly * g.Lx;
     const bool prof = ctx->prof.on;
+    ctx->split_cur = -1;  // the iterate buffers are reused below
     const bool graphs = ctx->opt.use_graph && !prof;
     // all work runs on the context's stream, ordered after the caller's
     cudaStream_t st = ctx->wstream;

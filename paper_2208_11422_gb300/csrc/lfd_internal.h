@@ -97,6 +97,12 @@ struct lfd_ctx {
     // padded polyphase image [rows][Spad]
     float* Rp32 = nullptr;
     __nv_bfloat16* Rpb[2] = {nullptr, nullptr};
+    // TF32 (direct variant): operand copies rounded to TF32 - the iterate
+    // [rows][Cpad], the ratio [rows][Spad] and the transposed packed PSF
+    // [T*T][Cpad][Spad] (W32 itself is rounded in place once H^T 1 is known)
+    float* Vpt = nullptr;
+    float* Rpt = nullptr;
+    float* WT = nullptr;
     // projection outputs indexed by output position m
     float* Fwd = nullptr;        // [fwd_splits][M_pad][Spad]
     float* Bwd = nullptr;        // [bwd_splits][M_pad][Cpad]
@@ -151,6 +157,10 @@ struct lfd_ctx {
     lfd::LoPlanes* lo = nullptr;      // adaptive lo planes of the PSF spectra (split BF16)
     int64_t spectra_bytes = 0;        // PSF spectra planes the contractions stream
     int64_t n_low = 0;
+    // depth split (lfd_split_*): iterate buffer holding the current iterate
+    // (-1: none loaded) and whether the other buffer holds the previous one
+    int split_cur = -1;
+    int split_prev = 0;
 };
 
 namespace lfd {
@@ -222,6 +232,11 @@ cudaError_t launch_update(const float* vin, float* vout, __nv_bfloat16* hi, __nv
                           const float* parts, int nsplit, const float* inv, const Geo& g,
                           float* mip, double* flux_part, cudaStream_t st);
 cudaError_t launch_mip(const float* vp32, const Geo& g, float* mip, cudaStream_t st);
+// r[e] = y[e] / (hv[e] + eps) (0 where hv + eps <= 0), e < n
+cudaError_t launch_ratio_image(const float* y, const float* hv, float eps, int64_t n, float* r,
+                               cudaStream_t st);
+// out[0] = sum of p[0..n) (device, fixed order)
+cudaError_t launch_sum_doubles(const double* p, int64_t n, double* out, cudaStream_t st);
 // DCT entropy of nf frames' MIPs (frame-major arrays: mip H*W, G H*XS, rowE2 H,
 // coef XS*YS, flux_part nflux per frame); frame f writes out_entropy[f*out_stride]
 // and out_flux[f*out_stride]

@@ -14,6 +14,12 @@
 // and in MN-major form for the backward (same array, contraction over s). In
 // split-BF16 mode each step runs three passes: hi*hi, hi*lo, lo*hi.
 //
+// TF32 mode (kind::tf32): the operands are FP32 copies rounded to TF32
+// (round to nearest, 10-bit mantissa), a k-block is 32 values (the same
+// 128 bytes, so tiles, swizzle and descriptors are those of BF16), one pass.
+// Both operands are K-major: the backprojection reads a transposed copy of
+// the packed PSF, [tap][c][s], instead of the MN-major form.
+//
 // Warp roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues
 // the MMAs (one thread), warps 2-5 drain the accumulators to global memory.
 // Blocks are persistent over work units (row tile, column tile, K split); a K
@@ -41,7 +47,7 @@ using namespace tcx;
 
 constexpr int kStages = 3;
 constexpr int kBM = 256;
-constexpr int kBK = 64;                       // bf16 elements per k-block = 128 B
+constexpr int kBK = 64;                       // bf16 elements per k-block = 128 B (32 for TF32)
 constexpr int kABytes = kBM * kBK * 2;        // 32 KB
 constexpr int kBBytesMax = 256 * kBK * 2;     // 32 KB
 constexpr int kStageBytes = kABytes + kBBytesMax;
@@ -89,7 +95,7 @@ __device__ __forceinline__ Unit decode(const TcArgs& a, int u) {
     return r;
 }
 
-template <bool FWD>
+template <bool FWD, bool TF32>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
@@ -107,6 +113,8 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
+    constexpr int kBKe = TF32 ? 32 : kBK;   // elements per k-block (128 bytes)
+    constexpr int kKS = TF32 ? 8 : 16;      // elements per MMA step (32 bytes)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -157,9 +165,11 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                         const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
                         const CUtensorMap* ma = (p == 2) ? &mA1 : &mA0;
                         const CUtensorMap* mb = (p == 1) ? &mB1 : &mB0;
-                        tma_2d(sA, ma, cb * kBK, row, &full[stage]);
+                        tma_2d(sA, ma, cb * kBKe, row, &full[stage]);
                         if (FWD) {
-                            tma_3d(sB, mb, cb * kBK, 0, tap, &full[stage]);
+                            tma_3d(sB, mb, cb * kBKe, 0, tap, &full[stage]);
+                        } else if (TF32) {  // K-major [tap][c][s]: bn rows of 32 phases
+                            tma_3d(sB, mb, cb * kBKe, n0, tap, &full[stage]);
                         } else {
                             for (int j = 0; j < a.bn / 64; ++j)
                                 tma_3d(sB + j * 8192, mb, n0 + j * 64, cb * kBK, tap, &full[stage]);
@@ -180,8 +190,8 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer --
-            constexpr bool kBMn = !FWD;
-            const uint32_t idesc = idesc_bf16(128, a.bn, kBMn);
+            constexpr bool kBMn = !FWD && !TF32;
+            const uint32_t idesc = TF32 ? idesc_tf32(128, a.bn) : idesc_bf16(128, a.bn, kBMn);
             int stage = 0, consumed = 0, ci = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -205,17 +215,21 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                             tc_fence_after();
                             const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
                             const int cb = a.tap_inner ? kb / a.taps : kb % a.kb_per_tap;
-                            const int ksteps = min(kBK / 16, (a.kvalid - cb * kBK + 15) / 16);
+                            const int ksteps = min(kBKe / kKS, (a.kvalid - cb * kBKe + kKS - 1) / kKS);
 #pragma unroll
-                            for (int ks = 0; ks < kBK / 16; ++ks) {
+                            for (int ks = 0; ks < 4; ++ks) {
                                 if (ks >= ksteps) break;
-                                const uint64_t bd = FWD ? sdesc(sB + ks * 32, 16, 1024)
-                                                        : sdesc(sB + ks * 2048, 8192, 1024);
+                                const uint64_t bd = (FWD || TF32) ? sdesc(sB + ks * 32, 16, 1024)
+                                                                  : sdesc(sB + ks * 2048, 8192, 1024);
 #pragma unroll
                                 for (int half = 0; half < 2; ++half) {
                                     const uint64_t ad = sdesc(sA + half * 16384 + ks * 32, 16, 1024);
-                                    umma_bf16(tmem + half * 256, ad, bd, idesc,
-                                              (first && ks == 0) ? 0u : 1u);
+                                    if (TF32)
+                                        umma_tf32(tmem + half * 256, ad, bd, idesc,
+                                                  (first && ks == 0) ? 0u : 1u);
+                                    else
+                                        umma_bf16(tmem + half * 256, ad, bd, idesc,
+                                                  (first && ks == 0) ? 0u : 1u);
                                 }
                             }
                             first = false;
@@ -291,12 +305,63 @@ k_tc_conv(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ----------------------------------------------------- TF32 operand copies --
+// x rounded to TF32 (10-bit mantissa), round to nearest with ties away from
+// zero; the low 13 bits of the result are zero
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_tf32_copy(const float* src, float* dst, int64_t n) {  // src == dst allowed
+    const int64_t n4 = n >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = s4[e];
+        d4[e] = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+    }
+    for (int64_t e = (n4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = to_tf32(src[e]);
+}
+
+// WT[tap][c][s] = tf32(W[tap][s][c]) for s < Spad, c < Cpad, through 32 x 32
+// shared-memory tiles (grid x: c tiles, y: s tiles, z: taps)
+__global__ void k_tf32_transpose(const float* __restrict__ W, float* __restrict__ WT, int Spad, int Cpad) {
+    __shared__ float t[32][33];
+    const int64_t tap = blockIdx.z;
+    const float* w = W + tap * Spad * (int64_t)Cpad;
+    float* wt = WT + tap * Spad * (int64_t)Cpad;
+    const int c0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int s = s0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (s < Spad && c < Cpad) ? w[(int64_t)s * Cpad + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, s = s0 + threadIdx.x;
+        if (c < Cpad && s < Spad) wt[(int64_t)c * Spad + s] = to_tf32(t[threadIdx.x][i]);
+    }
+}
+
+cudaError_t launch_tf32_copy(const float* src, float* dst, int64_t n, cudaStream_t st) {
+    int64_t b = (n / 4 + 255) / 256;
+    b = std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+    k_tf32_copy<<<(unsigned)b, 256, 0, st>>>(src, dst, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------- host --
 struct TcState {
-    CUtensorMap fa[2], fb[2];   // forward: A = Vpb hi/lo, B = Wb hi/lo (K-major)
-    CUtensorMap ba[2], bb[2];   // backward: A = Rpb hi/lo, B = Wb hi/lo (MN-major)
+    CUtensorMap fa[2], fb[2];   // forward: A = Vpb hi/lo, B = Wb hi/lo (K-major); TF32: Vpt, W32
+    CUtensorMap ba[2], bb[2];   // backward: A = Rpb hi/lo, B = Wb hi/lo (MN-major); TF32: Rpt, WT
     TcArgs fwd, bwd;
     int fwd_grid = 0, bwd_grid = 0;
+    bool tf32 = false;
     int* err = nullptr;
 };
 
@@ -314,11 +379,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, const void* ptr, int rank, const cuuint64_t* dims,
-              const cuuint64_t* strides, const cuuint32_t* box) {
+              const cuuint64_t* strides, const cuuint32_t* box,
+              CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims, strides, box,
+    return fn(m, dt, rank, const_cast<void*>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -380,9 +446,52 @@ cudaError_t tc_init(lfd_ctx* ctx) {
     if (e != cudaSuccess) return e;
 
     const bool split = ctx->opt.precision == LFD_BF16X3;
+    const bool tf32 = s->tf32 = ctx->opt.precision == LFD_TF32;
     const int lo = split ? 1 : 0;
+    if (tf32) {
+        // operands: the TF32-rounded copies Vpt [rows][Cpad], Rpt [rows][Spad],
+        // W32 [taps][Spad][Cpad] (rounded in place) and WT [taps][Cpad][Spad]
+        if (!ctx->Vpt || !ctx->Rpt || !ctx->WT || !ctx->W32) {
+            ctx->err = "TF32 operand buffers missing";
+            return cudaErrorInvalidValue;
+        }
+        const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        const cuuint32_t bn = (cuuint32_t)bwd_bn(g);
+        const cuuint64_t da[2] = {(cuuint64_t)g.Cpad, (cuuint64_t)g.rows};
+        const cuuint64_t sa[1] = {(cuuint64_t)g.Cpad * 4};
+        const cuuint32_t boxa[2] = {32, 256};
+        const cuuint64_t dw[3] = {(cuuint64_t)g.Cpad, (cuuint64_t)g.Spad, (cuuint64_t)g.taps()};
+        const cuuint64_t sw[2] = {(cuuint64_t)g.Cpad * 4, (cuuint64_t)g.Cpad * 4 * g.Spad};
+        const cuuint32_t boxw[3] = {32, (cuuint32_t)g.Spad, 1};
+        const cuuint64_t dr[2] = {(cuuint64_t)g.Spad, (cuuint64_t)g.rows};
+        const cuuint64_t sr[1] = {(cuuint64_t)g.Spad * 4};
+        const cuuint64_t dt[3] = {(cuuint64_t)g.Spad, (cuuint64_t)g.Cpad, (cuuint64_t)g.taps()};
+        const cuuint64_t stt[2] = {(cuuint64_t)g.Spad * 4, (cuuint64_t)g.Spad * 4 * g.Cpad};
+        const cuuint32_t boxt[3] = {32, bn, 1};
+        if (!make_map(&s->fa[0], ctx->Vpt, 2, da, sa, boxa, F32) ||
+            !make_map(&s->fb[0], ctx->W32, 3, dw, sw, boxw, F32) ||
+            !make_map(&s->ba[0], ctx->Rpt, 2, dr, sr, boxa, F32) ||
+            !make_map(&s->bb[0], ctx->WT, 3, dt, stt, boxt, F32))
+            goto fail;
+        s->fa[1] = s->fa[0];
+        s->fb[1] = s->fb[0];
+        s->ba[1] = s->ba[0];
+        s->bb[1] = s->bb[0];
+        // the PSF operands, once: transposed copy first (from the FP32 values),
+        // then the forward copy rounded in place
+        const int64_t wcount = g.taps() * g.Spad * (int64_t)g.Cpad;
+        dim3 tg((unsigned)((g.Cpad + 31) / 32), (unsigned)((g.Spad + 31) / 32), (unsigned)g.taps());
+        k_tf32_transpose<<<tg, dim3(32, 8), 0, 0>>>(ctx->W32, ctx->WT, g.Spad, g.Cpad);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_tf32_copy(ctx->W32, ctx->W32, wcount, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+    }
     // forward A: Vpb [rows][Cpad]; B: Wb [taps][Spad][Cpad]
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 2 && !tf32; ++b) {
         const int idx = b == 0 ? 0 : lo;
         {
             const cuuint64_t dims[2] = {(cuuint64_t)g.Cpad, (cuuint64_t)g.rows};
@@ -415,7 +524,8 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         f.n_ntiles = 1;
         f.nsplit = fwd_split_for(g, ctx->sm_count);
         f.n_units = f.n_mtiles * f.nsplit;
-        f.kb_per_tap = g.Cpad / kBK;
+        // TF32: k-blocks of 32 values, only as many as reach a valid channel
+        f.kb_per_tap = tf32 ? (g.C + 31) / 32 : g.Cpad / kBK;
         f.kb_total = (int)(g.taps() * f.kb_per_tap);
         f.bn = g.Spad;
         f.n_valid = g.Spad;
@@ -424,7 +534,7 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         f.tap_inner = 1;
         f.chunk_kb = kChainSteps / (4 * f.passes);
         f.kvalid = g.C;
-        f.tx_bytes = (uint32_t)(kABytes + kBK * 2 * g.Spad);
+        f.tx_bytes = (uint32_t)(kABytes + 128 * g.Spad);
         f.out = ctx->Fwd;
         f.slot_stride = g.M_pad * g.Spad;
         f.err = s->err;
@@ -435,31 +545,45 @@ cudaError_t tc_init(lfd_ctx* ctx) {
         b.n_ntiles = bwd_ntiles(g);
         b.nsplit = bwd_split_for(g, ctx->sm_count);
         b.n_units = b.n_mtiles * b.n_ntiles * b.nsplit;
-        b.kb_per_tap = (g.Spad + kBK - 1) / kBK;
+        b.kb_per_tap = tf32 ? (g.S + 31) / 32 : (g.Spad + kBK - 1) / kBK;
         b.tap_inner = 0;
         b.kvalid = g.S;
         b.kb_total = (int)(g.taps() * b.kb_per_tap);
         b.bn = bwd_bn(g);
         b.n_valid = g.Cpad;
-        b.tx_bytes = (uint32_t)(kABytes + (b.bn / 64) * 8192);
+        b.tx_bytes = (uint32_t)(kABytes + 128 * b.bn);  // bn rows of 128 B (BF16: bn/64 atoms of 8 KB)
         b.out = ctx->Bwd;
         b.slot_stride = g.M_pad * g.Cpad;
         s->bwd_grid = std::min(b.n_units, ctx->sm_count);
     }
-    e = cudaFuncSetAttribute(k_tc_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (tf32) {
+        e = cudaFuncSetAttribute(k_tc_conv<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_tc_conv<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kSmemBytes);
+    }
+    e = cudaFuncSetAttribute(k_tc_conv<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    e = cudaFuncSetAttribute(k_tc_conv<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     return e;
 fail:
     ctx->err = "cuTensorMapEncodeTiled failed (or the driver entry point is missing)";
     return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_forward(lfd_ctx* ctx, int /*buf*/, cudaStream_t st) {
+cudaError_t tc_forward(lfd_ctx* ctx, int buf, cudaStream_t st) {
     TcState* s = static_cast<TcState*>(ctx->tc);
     if (!s) return cudaErrorNotReady;
-    k_tc_conv<true><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fb[0],
-                                                               s->fb[1], s->fwd);
+    if (s->tf32) {  // the iterate rounded to TF32 (halo rows and padding stay zero)
+        const Geo& g = ctx->g;
+        cudaError_t e = launch_tf32_copy(ctx->Vp32[buf], ctx->Vpt, g.rows * g.Cpad, st);
+        if (e != cudaSuccess) return e;
+        k_tc_conv<true, true><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fb[0],
+                                                                          s->fb[1], s->fwd);
+    } else {
+        k_tc_conv<true, false><<<s->fwd_grid, kThreads, kSmemBytes, st>>>(s->fa[0], s->fa[1], s->fb[0],
+                                                                           s->fb[1], s->fwd);
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -467,8 +591,16 @@ cudaError_t tc_forward(lfd_ctx* ctx, int /*buf*/, cudaStream_t st) {
 cudaError_t tc_backward(lfd_ctx* ctx, cudaStream_t st) {
     TcState* s = static_cast<TcState*>(ctx->tc);
     if (!s) return cudaErrorNotReady;
-    k_tc_conv<false><<<s->bwd_grid, kThreads, kSmemBytes, st>>>(s->ba[0], s->ba[1], s->bb[0],
-                                                                s->bb[1], s->bwd);
+    if (s->tf32) {  // the ratio image rounded to TF32
+        const Geo& g = ctx->g;
+        cudaError_t e = launch_tf32_copy(ctx->Rp32, ctx->Rpt, g.rows * g.Spad, st);
+        if (e != cudaSuccess) return e;
+        k_tc_conv<false, true><<<s->bwd_grid, kThreads, kSmemBytes, st>>>(s->ba[0], s->ba[1], s->bb[0],
+                                                                           s->bb[1], s->bwd);
+    } else {
+        k_tc_conv<false, false><<<s->bwd_grid, kThreads, kSmemBytes, st>>>(s->ba[0], s->ba[1], s->bb[0],
+                                                                            s->bb[1], s->bwd);
+    }
     count_launch();
     return cudaGetLastError();
 }

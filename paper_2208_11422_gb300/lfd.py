@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(PKG, "liblfd.so")
 LFD_OK, LFD_EINVAL, LFD_ENOMEM, LFD_ECUDA, LFD_ENOTREADY, LFD_ETIMEDOUT, LFD_EBUSY, \
     LFD_EINTERNAL, LFD_EUNSUPPORTED, LFD_ECANCELED = range(10)
 LFD_FP32, LFD_TF32, LFD_BF16, LFD_BF16X3 = range(4)
-PRECISIONS = {"fp32": LFD_FP32, "bf16": LFD_BF16, "bf16x3": LFD_BF16X3}
+PRECISIONS = {"fp32": LFD_FP32, "tf32": LFD_TF32, "bf16": LFD_BF16, "bf16x3": LFD_BF16X3}
 LFD_DIRECT, LFD_FFT = 0, 1
 VARIANTS = {"direct": LFD_DIRECT, "fft": LFD_FFT}
 
@@ -111,6 +111,11 @@ _SIGS = {
     "lfd_autotune": (_I, [_VP, _I, _I, _I, _I, _I, ctypes.POINTER(lfd_options), _VP,
                           ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "lfd_quality_mip_static": (_I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
+    "lfd_quality_mip": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
+    "lfd_split_load": (_I, [_VP, _VP, _VP]),
+    "lfd_split_forward": (_I, [_VP, _VP, _VP]),
+    "lfd_split_update": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "lfd_split_store": (_I, [_VP, _VP, _I, _VP]),
     "lfd_destroy": (None, [_VP]),
     "lfd_last_error": (ctypes.c_char_p, [_VP]),
     "lfd_status_string": (ctypes.c_char_p, [_I]),
@@ -276,6 +281,40 @@ def lfd_quality_mip_static(mip, H: int, W: int, XS: int, YS: int, l2_over_region
                                        _stream(stream))
     if st != LFD_OK:
         raise LfdError(st, "lfd_quality_mip_static: %s" % lfd_status_string(st))
+
+
+def lfd_quality_mip(ctx, mip, stream=None) -> float:
+    """DCT entropy of a z-maximum projection image with the context's tables."""
+    e = _D(0)
+    _check(load().lfd_quality_mip(ctx, _ptr(mip), ctypes.byref(e), _stream(stream)), ctx)
+    return e.value
+
+
+def _dptr(x):
+    """Address of a device buffer (CUDA tensor of any dtype, or an int address)."""
+    if isinstance(x, int):
+        return x
+    if getattr(x, "is_cuda", False) and x.is_contiguous():
+        return x.data_ptr()
+    raise ValueError("expected a contiguous CUDA tensor or a device address")
+
+
+def lfd_split_load(ctx, v, stream=None):
+    _check(load().lfd_split_load(ctx, _ptr(v), _stream(stream)), ctx)
+
+
+def lfd_split_forward(ctx, hv_part, stream=None):
+    _check(load().lfd_split_forward(ctx, _dptr(hv_part), _stream(stream)), ctx)
+
+
+def lfd_split_update(ctx, y, hv, mip_part, flux_part, stream=None):
+    """flux_part: a float64 CUDA tensor of one element (or a device address)."""
+    _check(load().lfd_split_update(ctx, _dptr(y), _dptr(hv), _dptr(mip_part), _dptr(flux_part),
+                                   _stream(stream)), ctx)
+
+
+def lfd_split_store(ctx, v, previous: bool = False, stream=None):
+    _check(load().lfd_split_store(ctx, _ptr(v), int(bool(previous)), _stream(stream)), ctx)
 
 
 def lfd_autotune(psf, P: int, Nnum: int, Nz: int, H: int, W: int, opt: lfd_options, stream=None):

@@ -70,6 +70,10 @@ def test_create_rejects_null_psf_and_bad_options(lib):
     assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
                           ctypes.byref(out)) == lfd.LFD_EINVAL
     assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, None, None, None) == lfd.LFD_EINVAL
+    o = lfd.lfd_default_options(precision="tf32", variant="fft")   # TF32 is a direct-GEMM mode
+    assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
+                          ctypes.byref(out)) == lfd.LFD_EUNSUPPORTED
+    assert out.value is None
 
 
 def test_null_context_calls(lib):
@@ -154,7 +158,7 @@ def test_server_rejects_bad_options_before_cuda(lib):
         assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL, kw
         assert not srv.value
     o = lfd.lfd_server_default_options()
-    o.opt.precision = lfd.LFD_TF32   # reserved: split BF16, BF16 or FP32 only
+    o.opt.precision = lfd.LFD_TF32   # the server runs the FFT variant: split BF16, BF16 or FP32
     srv = ctypes.c_void_p()
     assert lib.lfd_server_create(ctypes.byref(o), ctypes.byref(srv)) == lfd.LFD_EINVAL
 

@@ -16,6 +16,7 @@ Bounds per projection (relative L2 per crop):
   split BF16 (FFT and direct)       1e-4           (the split-BF16 bound)
   BF16 PSF spectra (FFT)            2^-9 ~ 2e-3    (one BF16 rounding per spectrum value)
   BF16 (direct)                     2^-8 ~ 3.9e-3  (both operands rounded to BF16)
+  TF32 (direct)                     2^-10 ~ 9.8e-4 (both operands rounded to TF32)
 The errors are printed for every path and crop."""
 import threading
 
@@ -32,7 +33,8 @@ pytestmark = pytest.mark.gpu
 CROP = 256
 NCROPS = 4
 TOL = {("fft", "fp32"): 1e-5, ("fft", "bf16x3"): 1e-4, ("fft", "bf16"): 2.0 ** -9,
-       ("direct", "fp32"): 1e-5, ("direct", "bf16x3"): 1e-4, ("direct", "bf16"): 2.0 ** -8}
+       ("direct", "fp32"): 1e-5, ("direct", "bf16x3"): 1e-4, ("direct", "bf16"): 2.0 ** -8,
+       ("direct", "tf32"): 2.0 ** -10}
 
 
 def crop_origins(H, W, n=NCROPS, size=CROP, seed=300):
