@@ -46,7 +46,13 @@ def parse():
     p.add_argument("--frames", type=int, default=64)
     p.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
-    p.add_argument("--pool", type=int, default=32, help="serving: distinct frames")
+    p.add_argument("--pool", type=int, default=256, help="serving: distinct frames")
+    p.add_argument("--serve-requests", type=int, default=600,
+                   help="requests of the serving run inside the default (large-frame) line")
+    p.add_argument("--no-serve", action="store_true",
+                   help="default line without its serving run")
+    p.add_argument("--no-batch", action="store_true",
+                   help="default line without its time-lapse batch run")
     p.add_argument("--serve-frames", type=int, default=32, help="serving: frames per PSF set batch")
     p.add_argument("--cap", type=int, default=40)
     p.add_argument("--depths", type=int, default=None,
@@ -617,6 +623,15 @@ def run_lfd(args, rank, world, local):
                                                         "backward_rel_l2": rel_l2(gb, ref_b)}
 
     clocks = clk.summary()
+    # the metric's other two parts on the same GPU (N = 1, full workload only):
+    # serving p50 / p99 under a bounded Poisson stream, and the 64-frame time-lapse
+    full = world == 1 and not args.depths and not args.lenslets
+    torch.cuda.empty_cache()
+    serve = batch = None
+    if full and not args.no_serve:
+        serve = measure_serve(args, rank, world, local, args.serve_requests, args.pool)
+    if full and not args.no_batch:
+        batch = measure_batch(args, rank, world, local, ("bf16x3", "fp32"))
     out = {
         "metric": "RL iterations/s, 2025x2025 px x 51 depths, PSF 345 px (Nnum 15)",
         "value": value, "unit": "RL iterations/s", "n_gpus": world, "steps": steps,
@@ -629,23 +644,25 @@ def run_lfd(args, rank, world, local):
         "roofline": roof, "cpu_baseline": cpu, "paths": paths, "accuracy_vs_oracle": accuracy,
         "rel_l2_vs_fft_fp32_after_%d_iterations" % steps: head_vs_fp32,
         "entropy": ent, "predicted_iteration": pred,
+        "serve": serve,
+        "batch": {"workload": "lf_timelapse_%dx615px_31z_psf165" % args.frames, "frames": args.frames,
+                  "cap": args.cap, "paths": batch} if batch else None,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def run_batch(args, rank, world, local):
+def measure_batch(args, rank, world, local, precisions=("bf16x3", "bf16", "fp32")):
     """Time-lapse batch: frames of the 615 px geometry sharing one PSF, beads
     drifting by N(0, 0.5) voxel per frame, photon scale per frame U[100, 2000];
     all frames advance together (one launch per stage, one CUDA graph per
-    iteration) and each stops at its own predicted iteration (cap --cap)."""
+    iteration) and each stops at its own predicted iteration (cap --cap).
+    Returns {precision: result} (frames/s over all ranks, the tuned FFT size,
+    stopping iterations)."""
     import torch
-    from paper_2208_11422_gb300 import build, lfd, synth
+    from paper_2208_11422_gb300 import lfd, synth
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    build.build()
-    lfd.load()
     g = synth.CONFIGS[1]
     nf, cap = args.frames, args.cap
     psf = synth.make_psf(1)
@@ -665,7 +682,7 @@ def run_batch(args, rank, world, local):
     y_d = torch.from_numpy(np.stack(ys)).to(dev)
     stream = torch.cuda.current_stream()
     results = {}
-    for prec in ("bf16x3", "bf16", "fp32"):
+    for prec in precisions:
         opt = lfd.lfd_default_options(precision=prec, variant="fft", max_frames=nf)
         best, tune_ms = lfd.lfd_autotune(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
         opt.fft_size = best
@@ -693,9 +710,24 @@ def run_batch(args, rank, world, local):
         lfd.lfd_destroy(ctx)
         del v
         torch.cuda.empty_cache()
-    for prec in ("bf16x3", "bf16"):   # frames whose stopping iteration equals the FP32 run's
-        results[prec]["stops_equal_to_fp32"] = sum(
-            int(d == e) for d, e in zip(results[prec]["iters_done"], results["fp32"]["iters_done"]))
+    if "fp32" in results:
+        for prec in results:   # frames whose stopping iteration equals the FP32 run's
+            if prec != "fp32":
+                results[prec]["stops_equal_to_fp32"] = sum(
+                    int(d == e) for d, e in zip(results[prec]["iters_done"], results["fp32"]["iters_done"]))
+    del psf_d, y_d
+    torch.cuda.empty_cache()
+    return results
+
+
+def run_batch(args, rank, world, local):
+    import torch
+    from paper_2208_11422_gb300 import build, lfd
+    torch.cuda.set_device(local)
+    build.build()
+    lfd.load()
+    nf, cap = args.frames, args.cap
+    results = measure_batch(args, rank, world, local)
     head = results["bf16x3"]
     out = {
         "metric": "RL frames/s, %d-frame time-lapse 615x615 px x 31 depths, PSF 165 px, each frame "
@@ -711,31 +743,30 @@ def run_batch(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
-def run_serve(args, rank, world, local):
-    """Serving: a Poisson stream of --requests requests (mean --rate per second)
+def measure_serve(args, rank, world, local, requests, pool_size):
+    """Serving: a Poisson stream of `requests` requests (mean --rate per second)
     over 4 resident PSF sets (Nnum, Nz drawn per set, PSF 11 lenslets wide).
     Each request has its own lenslet grid (33..121 per axis), bead count
     (50..5000) and photon scale (log-uniform 100..5000). The server admits
     requests by device footprint, batches them per PSF set in split BF16 and
     stops each at its predicted iteration (cap --cap). The frames' data come
-    from a pool of --pool distinct requests, projected once before the run;
-    arrival i uses pool entry i mod --pool. Host buffers are page-locked."""
+    from a pool of `pool_size` distinct requests (bead volumes made on the
+    device, projected once before the run); arrival i uses pool entry
+    i mod pool_size. Host buffers are page-locked. Returns the summary."""
     import collections
     import torch
-    from paper_2208_11422_gb300 import build, lfd, synth
+    from paper_2208_11422_gb300 import lfd, synth
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    build.build()
-    lfd.load()
     sets = [synth.serve_psf_set(j) for j in (1, 2, 3, 4)]
-    pool = synth.serve_requests(args.pool, 910 + rank)
-    arrivals = synth.serve_requests(args.requests, 920 + rank, args.rate)
+    pool = synth.serve_requests(pool_size, 910 + rank)
+    arrivals = synth.serve_requests(requests, 920 + rank, args.rate)
     Lmax = synth.SERVE_LENSLETS[1]
     # pool data: y = Poisson(scale * H v) + 5 with H v from an FP32 context at the
     # largest sensor of the set (the volume is zero outside the request's frame,
     # so the crop is the frame's own projection)
     ys = [None] * len(pool)
+    t_prep = time.perf_counter()
     for si, (nnum, nz, P, psf) in enumerate(sets):
         Hm = Lmax * nnum
         ctx = lfd.lfd_create(torch.from_numpy(psf).to(dev), P, nnum, nz, Hm, Hm,
@@ -747,7 +778,7 @@ def run_serve(args, rank, world, local):
                 continue
             H, W = rq.ly * nnum, rq.lx * nnum
             vbig.zero_()
-            vbig[:, :H, :W] = torch.from_numpy(synth.serve_volume(rq, nnum, nz)).to(dev)
+            synth.beads_device(rq.seed, nz, H, W, rq.beads, 2.0, 0.3, device=dev, out=vbig[:, :H, :W])
             lfd.lfd_forward(ctx, vbig, hv)
             torch.cuda.synchronize()
             ys[k] = torch.from_numpy(synth.poisson_data(hv[:H, :W].cpu().numpy(), rq.scale, 5.0,
@@ -755,6 +786,7 @@ def run_serve(args, rank, world, local):
         lfd.lfd_destroy(ctx)
         del vbig, hv
         torch.cuda.empty_cache()
+    t_prep = time.perf_counter() - t_prep
 
     opt = lfd.lfd_server_default_options("bf16x3", max_iter=args.cap,
                                          max_frames_per_set=args.serve_frames)
@@ -818,33 +850,50 @@ def run_serve(args, rank, world, local):
         t_end = max(rec[4] for rec in done_rec)
     stats = lfd.lfd_server_stats_get(srv)
     lfd.lfd_server_destroy(srv)
+    del ys, free_v
+    torch.cuda.empty_cache()
     ok = [rec for rec in done_rec if rec[1] is not None and rec[1]["status"] == lfd.LFD_OK]
     lat = np.array([r["latency_us"] / 1e3 + (t_sub - t_arr) * 1e3 for _, r, t_arr, t_sub, _ in ok])
     queue = np.array([r["queue_us"] / 1e3 for _, r, _, _, _ in ok])
     iters = np.array([r["iters_run"] for _, r, _, _, _ in ok])
     span = t_end - t0
-    frames_s = len(ok) / span
-    out = {
-        "metric": "served frames/s, Poisson stream of %d requests at %g req/s over 4 resident PSF sets "
-                  "(mixed sensor sizes, Nnum 11-15, 21-51 depths), split BF16, predicted stop (cap %d)"
-                  % (len(arrivals), args.rate, args.cap),
-        "value": frames_s, "unit": "frames/s", "n_gpus": world, "steps": len(arrivals), "warmup": 0,
-        "ms_per_step": span * 1e3 / max(1, len(ok)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3",
-        "data": "synthetic (beads, Poisson noise; %d distinct frames reused)" % len(pool),
-        "config": {"workload": "lf_serve_4sets_poisson%greq_s" % args.rate, "requests": len(arrivals),
-                   "rate_req_s": args.rate, "cap": args.cap, "pool": len(pool),
-                   "max_frames_per_set": args.serve_frames,
-                   "psf_sets": [{"Nnum": n, "Nz": z, "P": p} for n, z, p, _ in sets]},
+    return {
+        "frames_per_s": len(ok) / span, "requests": len(arrivals), "pool": len(pool),
+        "rate_req_s": args.rate, "cap": args.cap, "max_frames_per_set": args.serve_frames,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean())},
         "queue_ms_mean": float(queue.mean()),
         "offered_req_s": len(arrivals) / max(a.arrival_s for a in arrivals),
+        "achieved_req_s": len(ok) / span,
         "completed": len(ok), "rejected": rejected, "iterations_mean": float(iters.mean()),
-        "frame_iterations_per_s": float(iters.sum() / span),
+        "frame_iterations_per_s": float(iters.sum() / span), "seconds": span,
+        "pool_preparation_s": t_prep,
         "server": {k: stats[k] for k in ("ticks", "frame_iterations", "columns", "arena_bytes",
                                          "arena_peak_bytes", "resident_bytes")},
+        "psf_sets": [{"Nnum": n, "Nz": z, "P": p} for n, z, p, _ in sets],
         "gpu_launches": lfd.lfd_launch_count() - l0, "clocks": clk.summary(),
+    }
+
+
+def run_serve(args, rank, world, local):
+    import torch
+    from paper_2208_11422_gb300 import build, lfd
+    torch.cuda.set_device(local)
+    build.build()
+    lfd.load()
+    r = measure_serve(args, rank, world, local, args.requests, args.pool)
+    out = {
+        "metric": "served frames/s, Poisson stream of %d requests at %g req/s over 4 resident PSF sets "
+                  "(mixed sensor sizes, Nnum 11-15, 21-51 depths), split BF16, predicted stop (cap %d)"
+                  % (r["requests"], args.rate, args.cap),
+        "value": r["frames_per_s"], "unit": "frames/s", "n_gpus": world, "steps": r["requests"],
+        "warmup": 0, "ms_per_step": r["seconds"] * 1e3 / max(1, r["completed"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+        "data": "synthetic (beads, Poisson noise; %d distinct frames reused)" % r["pool"],
+        "config": {"workload": "lf_serve_4sets_poisson%greq_s" % args.rate, "requests": r["requests"],
+                   "rate_req_s": args.rate, "cap": args.cap, "pool": r["pool"],
+                   "max_frames_per_set": args.serve_frames, "psf_sets": r["psf_sets"]},
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "serve": r,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

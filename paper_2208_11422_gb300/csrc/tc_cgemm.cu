@@ -139,10 +139,6 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
             // ------------------------------------------------- TMA producer --
             const CUtensorMap* A[4] = {&a0, &a1, &a2, &a3};
             const CUtensorMap* B[4] = {&b0, &b1, &b2, &b3};
-            // the PSF spectra stream through once per projection: they leave
-            // L2 first, so the data columns stay there for the other row
-            // tiles (or channel tiles) of the same bin
-            const uint64_t pol = policy_evict_first();
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -193,16 +189,16 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         if (MODE == MODE_ADAPTIVE && (i & 1)) {  // compact lo plane [slot][S][64]
                             if (!lo) continue;
                             if (ADJ) {
-                                tma_3d_hint(sA + i * kPlaneA, A[i], 0, kb * 64, lo0, &full[stage], pol);
-                                tma_3d_hint(sA + i * kPlaneA + 8192, A[i], 0, kb * 64, lo1, &full[stage], pol);
+                                tma_3d(sA + i * kPlaneA, A[i], 0, kb * 64, lo0, &full[stage]);
+                                tma_3d(sA + i * kPlaneA + 8192, A[i], 0, kb * 64, lo1, &full[stage]);
                             } else {
-                                tma_3d_hint(sA + i * kPlaneA, A[i], 0, mt * 128, lo0, &full[stage], pol);
+                                tma_3d(sA + i * kPlaneA, A[i], 0, mt * 128, lo0, &full[stage]);
                             }
                         } else if (ADJ) {  // MN-major: two 64-channel atoms of 64 phases
-                            tma_3d_hint(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage], pol);
-                            tma_3d_hint(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage], pol);
+                            tma_3d(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage]);
+                            tma_3d(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage]);
                         } else {
-                            tma_3d_hint(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage], pol);
+                            tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
                     }
 #pragma unroll

@@ -157,6 +157,45 @@ def beads(seed: int, nz: int, H: int, W: int, count: int, radius: float,
     return v
 
 
+def beads_device(seed: int, nz: int, H: int, W: int, count: int, radius: float,
+                 amp_lo: float, amp_hi: float = 1.0, device="cuda", out=None):
+    """The volume of ``beads`` built on a torch device (float32): the same seeded
+    draws, each bead splatted over the grid points within 4r of its centre.
+    Equal to ``beads`` up to float rounding; for timing inputs that must be
+    made quickly (serving pools). out: a zeroed [Nz][H][W] tensor to fill."""
+    import torch
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(0, W, count)
+    cy = rng.uniform(0, H, count)
+    cz = rng.uniform(0, nz, count)
+    amp = rng.uniform(amp_lo, amp_hi, count)
+    v = torch.zeros((nz, H, W), dtype=torch.float32, device=device) if out is None else out
+    rad = 4.0 * radius
+    k = int(math.ceil(rad)) + 1
+    off = torch.arange(-k, k + 1, device=device, dtype=torch.float64)
+    c = torch.tensor(np.stack([cz, cy, cx], 1), device=device, dtype=torch.float64)   # [n, 3]
+    a = torch.tensor(amp, device=device, dtype=torch.float64)
+    base = torch.floor(c)                                                             # [n, 3]
+    for chunk in range(0, count, 512):
+        cc, bb, aa = c[chunk:chunk + 512], base[chunk:chunk + 512], a[chunk:chunk + 512]
+        pz = bb[:, 0, None] + off[None, :]          # [m, 2k+1] candidate grid coordinates
+        py = bb[:, 1, None] + off[None, :]
+        px = bb[:, 2, None] + off[None, :]
+        dz = pz - cc[:, 0, None]
+        dy = py - cc[:, 1, None]
+        dx = px - cc[:, 2, None]
+        d2 = dz[:, :, None, None] ** 2 + dy[:, None, :, None] ** 2 + dx[:, None, None, :] ** 2
+        val = aa[:, None, None, None] * torch.exp(-d2 / (2.0 * radius * radius))
+        ok = (d2 <= rad * rad) & (pz >= 0)[:, :, None, None] & (pz < nz)[:, :, None, None] \
+            & (py >= 0)[:, None, :, None] & (py < H)[:, None, :, None] \
+            & (px >= 0)[:, None, None, :] & (px < W)[:, None, None, :]
+        zi = pz[:, :, None, None].expand_as(d2)[ok].long()
+        yi = py[:, None, :, None].expand_as(d2)[ok].long()
+        xi = px[:, None, None, :].expand_as(d2)[ok].long()
+        v.index_put_((zi, yi, xi), val[ok].to(torch.float32), accumulate=True)
+    return v
+
+
 def filaments(seed: int, nz: int, H: int, W: int, count: int, radius: float = 1.5,
               amp_lo: float = 0.3, amp_hi: float = 1.0) -> np.ndarray:
     """Tubular random-walk filaments [Nz][H][W] float64 (max-combined)."""
