@@ -37,14 +37,12 @@ __constant__ float2 c_tw[32];  // exp(-2 pi i k / 64), k < 32
 template <int F>
 struct FftSize {
     static constexpr int LOG = F == 64 ? 6 : 5;
-    static constexpr int HF = F / 2;           // lanes per channel in a transform warp
+    static constexpr int HF = F / 2;           // points of each lane's 1-D transform (F/2)
     static constexpr int H2 = F / 2 + 1;       // half-spectrum columns
     static constexpr int BINS = F * H2;
-    static constexpr int CPW = 64 / F;         // channels per warp (lanes / HF)
-    static constexpr int R2C_WARPS = 8;        // per R2C block
-    static constexpr int R2C_CH = R2C_WARPS * CPW;
-    static constexpr int C2R_WARPS = F == 64 ? 8 : 4;  // per C2R block
-    static constexpr int C2R_CH = C2R_WARPS * CPW;
+    static constexpr int THREADS = 512;        // per transform block
+    static constexpr int R2C_CH = THREADS / F; // channels per block: F lanes each
+    static constexpr int C2R_CH = THREADS / F;
 };
 
 __device__ __forceinline__ int brev_c(int i, int log) {
@@ -94,6 +92,18 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[N]) {
 template <int N, bool INV>
 __device__ __forceinline__ void fft_reg(float2 (&a)[N]) {
     fft_stage<N, 2, INV>(a);
+}
+
+// v * exp(-+2 pi i n / F) for 0 <= n < F/2 (the decimation-in-frequency
+// twiddle; INV: conjugate), a constant-bank operand when n is a constant
+template <int F, bool INV>
+__device__ __forceinline__ float2 twiddle(float2 v, int n) {
+    const int tw = n * (64 / F);
+    if (tw == 0) return v;
+    if (tw == 16) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    const float2 w = c_tw[tw];
+    const float wy = INV ? -w.y : w.y;
+    return make_float2(fmaf(v.x, w.x, -v.y * wy), fmaf(v.x, wy, v.y * w.x));
 }
 
 // A source or destination is bound to one column (one tile of one frame)
@@ -244,81 +254,111 @@ struct OutPlanesG {
 
 // R2C 2-D transform of the F x F patches of FftSize<F>::R2C_CH channels of
 // one tile; bin = fy*(F/2+1) + fx, out.put8 for every channel below ldc (zeros
-// for channels >= nch). Each channel belongs to F/2 lanes of one warp:
-//   load:    the patch goes through shared memory (row stride F+1): lanes
-//            along x, so the global loads are coalesced, all issued before
-//            the first store;
-//   rows:    lane l transforms rows l and l + F/2 packed as one complex row
-//            (z = p_l + i p_{l+F/2}) and separates the two half spectra; the
+// for channels >= nch). Each channel has F lanes, q = h * F/2 + l: every 1-D
+// transform of F points is split over the two lanes (h = 0, 1) of one l by
+// decimation in frequency: lane h = 0 transforms u[n] = x[n] + x[n + F/2] and
+// obtains the even outputs X[2r], lane h = 1 transforms
+// u[n] = (x[n] - x[n + F/2]) exp(-2 pi i n / F) and obtains the odd ones
+// X[2r + 1]; both read their inputs from shared memory. An F/2-point
+// transform in registers per lane keeps the block at 512 threads.
+//   load:    lane q loads column q of every patch row (coalesced across lanes,
+//            all loads issued before the stores); patch rows in shared memory
+//            (row stride F+1);
+//   rows:    lanes (h, l) transform rows l and l + F/2 packed as one complex
+//            row z = p_l + i p_{l+F/2} and separate the two half spectra (X[k]
+//            and X[F-k] have the same parity, so each lane holds both); the
 //            real bins fx = 0 and F/2 of a row go to slot 0 as one complex
 //            value (bin 0 real part, bin F/2 real part);
-//   columns: lane l transforms column slot l, for lane 0 the packed real
-//            columns 0 and F/2, which it separates afterwards.
+//   columns: lanes (h, l) transform column slot l, for l = 0 the packed real
+//            columns 0 and F/2, which they separate afterwards.
 // The half spectra stay in shared memory [channel][fy or row][fx], in place.
 // Grid: x = channel group (fastest, so blocks running together fill adjacent
 // parts of the same output rows), y = column.
 template <int F, class Src, class Out>
-__global__ void __launch_bounds__(32 * FftSize<F>::R2C_WARPS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
+__global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
     using Z = FftSize<F>;
-    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH;
+    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH, PS = F + 1;
     extern __shared__ float2 sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sub = lane / HF, l = lane % HF;
-    const int ch = warp * Z::CPW + sub;            // channel within the block
+    const int ch = threadIdx.x / F, q = threadIdx.x % F;
+    const int h = q / HF, l = q % HF;
     const int tile = blockIdx.y, c0 = blockIdx.x * CH, c = c0 + ch;
     const auto view = src.bind(tile);
     float2* R = sm + (size_t)ch * Z::BINS;          // [F][H2]
+    float* Pm = reinterpret_cast<float*>(R);        // [F][PS] real patch (same space)
+    const bool on = c < nch;
     {
-        constexpr int PS = F + 1;
-        float* Pm = reinterpret_cast<float*>(R);    // [F][PS] real patch
-        const bool on = c < nch;
-        const bool ok0 = on && view.col_ok(l), ok1 = on && view.col_ok(l + HF);
-        {
-            float t[2 * F];
+        const bool okx = on && view.col_ok(q);
+        constexpr int RB = F < 32 ? F : 32;  // rows per batch of loads in flight
 #pragma unroll
-            for (int r = 0; r < F; ++r) {
-                const SrcRow w = view.row(on ? c : 0, r);
-                t[2 * r] = (ok0 && w.ok) ? view.at(w, l) : 0.f;
-                t[2 * r + 1] = (ok1 && w.ok) ? view.at(w, l + HF) : 0.f;
+        for (int r0 = 0; r0 < F; r0 += RB) {
+            float t[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const SrcRow w = view.row(on ? c : 0, r0 + r);
+                t[r] = (okx && w.ok) ? view.at(w, q) : 0.f;
             }
 #pragma unroll
-            for (int r = 0; r < F; ++r) {
-                Pm[r * PS + l] = t[2 * r];
-                Pm[r * PS + l + HF] = t[2 * r + 1];
-            }
-        }
-        __syncwarp();
-        float2 a[F];
-#pragma unroll
-        for (int x = 0; x < F; ++x) a[brev_c(x, LOG)] = make_float2(Pm[l * PS + x], Pm[(l + HF) * PS + x]);
-        __syncwarp();  // the half spectra below overwrite the patch
-        fft_reg<F, false>(a);
-        R[l * H2] = make_float2(a[0].x, a[HF].x);
-        R[(l + HF) * H2] = make_float2(a[0].y, a[HF].y);
-#pragma unroll
-        for (int k = 1; k < HF; ++k) {
-            const float2 z = a[k], m = a[F - k];
-            R[l * H2 + k] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
-            R[(l + HF) * H2 + k] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+            for (int r = 0; r < RB; ++r) Pm[(r0 + r) * PS + q] = t[r];
         }
     }
-    __syncwarp();
-    {
-        float2 a[F];
+    __syncthreads();
+    float2 a[HF];
+    if (h == 0) {
 #pragma unroll
-        for (int r = 0; r < F; ++r) a[brev_c(r, LOG)] = R[r * H2 + l];
-        fft_reg<F, false>(a);
-        if (l == 0) {  // slot HF is free: the rows left it unused
-#pragma unroll
-            for (int fy = 0; fy < F; ++fy) {
-                const float2 z = a[fy], m = a[(F - fy) & (F - 1)];
-                R[fy * H2] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
-                R[fy * H2 + HF] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
-            }
-        } else {
-#pragma unroll
-            for (int fy = 0; fy < F; ++fy) R[fy * H2 + l] = a[fy];
+        for (int n = 0; n < HF; ++n) {
+            const float2 z0 = make_float2(Pm[l * PS + n], Pm[(l + HF) * PS + n]);
+            const float2 z1 = make_float2(Pm[l * PS + n + HF], Pm[(l + HF) * PS + n + HF]);
+            a[brev_c(n, LOG - 1)] = cadd(z0, z1);
         }
+    } else {
+#pragma unroll
+        for (int n = 0; n < HF; ++n) {
+            const float2 z0 = make_float2(Pm[l * PS + n], Pm[(l + HF) * PS + n]);
+            const float2 z1 = make_float2(Pm[l * PS + n + HF], Pm[(l + HF) * PS + n + HF]);
+            a[brev_c(n, LOG - 1)] = twiddle<F, false>(csub(z0, z1), n);
+        }
+    }
+    __syncthreads();  // the half spectra below overwrite the patch
+    fft_reg<HF, false>(a);  // a[r] = Z[2r + h]
+    if (h == 0) {
+        R[l * H2] = make_float2(a[0].x, a[HF / 2].x);
+        R[(l + HF) * H2] = make_float2(a[0].y, a[HF / 2].y);
+#pragma unroll
+        for (int r = 1; r < HF / 2; ++r) {
+            const float2 z = a[r], m = a[HF - r];
+            R[l * H2 + 2 * r] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
+            R[(l + HF) * H2 + 2 * r] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < HF / 2; ++r) {
+            const float2 z = a[r], m = a[HF - 1 - r];
+            R[l * H2 + 2 * r + 1] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
+            R[(l + HF) * H2 + 2 * r + 1] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+        }
+    }
+    __syncthreads();
+    if (h == 0) {
+#pragma unroll
+        for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = cadd(R[n * H2 + l], R[(n + HF) * H2 + l]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < HF; ++n)
+            a[brev_c(n, LOG - 1)] = twiddle<F, false>(csub(R[n * H2 + l], R[(n + HF) * H2 + l]), n);
+    }
+    __syncthreads();  // every lane has read its column before the columns are rewritten
+    fft_reg<HF, false>(a);  // a[s] = Y[2s + h]
+    if (l == 0) {  // packed real columns 0 (real part) and F/2 (imaginary part); slot HF is free
+#pragma unroll
+        for (int s2 = 0; s2 < HF; ++s2) {
+            const float2 z = a[s2], m = h == 0 ? a[(HF - s2) & (HF - 1)] : a[HF - 1 - s2];
+            const int fy = 2 * s2 + h;
+            R[fy * H2] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
+            R[fy * H2 + HF] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+        }
+    } else {
+#pragma unroll
+        for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
     }
     __syncthreads();
     // every bin of 8 consecutive channels at a time
@@ -449,120 +489,131 @@ struct TabVolDst {
     }
 };
 
-// C2R 2-D transform of FftSize<F>::CH channels of one tile: rows and columns
-// [off, off + B) of the real result, times `scale`, go to dst. Each channel
-// belongs to F/2 lanes of one warp:
-//   columns: lane l (1 <= l < F/2) inverse-transforms column fx = l; lane 0
-//            packs columns 0 and F/2 (whose inverses are real) into one and
-//            leaves both results in slot 0 (real part: column 0, imaginary
-//            part: column F/2);
-//   rows:    lane i < B/2 inverse-transforms output rows off+i and
-//            off+i+B/2 packed as one complex row (each row's spectrum extended
-//            by conjugate symmetry), then the outputs go through shared memory
-//            so that dst sees consecutive j across lanes, one output row at a
-//            time.
+// C2R 2-D transform of FftSize<F>::C2R_CH channels of one tile: rows and
+// columns [off, off + B) of the real result, times `scale`, go to dst. Each
+// channel has F lanes, q = h * F/2 + l, and every 1-D transform is split over
+// the two lanes (h = 0, 1) of one l by decimation in frequency (as in the
+// R2C, with conjugate twiddles):
+//   columns: lanes (h, l), l >= 1, inverse-transform column fx = l; for l = 0
+//            they transform columns 0 and F/2 (whose inverses are real) packed
+//            as one and leave both results in slot 0 (real part: column 0,
+//            imaginary part: column F/2);
+//   rows:    lanes (h, i), i < B/2, inverse-transform output rows off+i and
+//            off+i+B/2 packed as one complex row (each row's spectrum
+//            extended by conjugate symmetry); the outputs go through shared
+//            memory so that dst sees consecutive j across lanes, one output
+//            row at a time.
+// Input: GM, the spectra group-major [ldc/8][ntile][BINS][8] (tensor-core
+// contraction), else [BINS][ntile][ldc] (CUDA-core contraction).
 // Grid: x = column, y = channel group.
-template <int F, class Dst>
-__global__ void __launch_bounds__(32 * FftSize<F>::C2R_WARPS) k_fft_c2r(const float2* __restrict__ in, int nch,
-                                                                    int ldc, int ntile, int off, int B,
-                                                                    float scale, Dst dst) {
+template <int F, class Dst, bool GM>
+__global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2* __restrict__ in, int nch,
+                                                                  int ldc, int ntile, int off, int B,
+                                                                  float scale, Dst dst) {
     using Z = FftSize<F>;
     constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::C2R_CH;
     extern __shared__ float2 sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sub = lane / HF, l = lane % HF;
-    const int ch = warp * Z::CPW + sub;
+    const int ch = threadIdx.x / F, q = threadIdx.x % F;
+    const int h = q / HF, l = q % HF;
     const int tile = blockIdx.x, c0 = blockIdx.y * CH, c = c0 + ch;
     const auto view = dst.bind(tile);
-    // spectra of VG consecutive channels per bin (one thread reads them with
+    // spectra of 8 consecutive channels per bin (one thread reads them with
     // 16-byte loads), into [channel][bin]
-    constexpr int VG = CH < 8 ? CH : 8;
-    static_assert(VG % 4 == 0, "channel groups of 4 or 8");
-    for (int e = threadIdx.x; e < Z::BINS * (CH / VG); e += blockDim.x) {
-        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + VG * g;
-        float2 v[VG];
+    static_assert(CH % 8 == 0, "whole channel groups per block");
+    for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
+        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + 8 * g;
+        float2 v[8];
 #pragma unroll
-        for (int k = 0; k < VG; ++k) v[k] = make_float2(0.f, 0.f);
-        if (cg < ldc) {  // ldc is a multiple of VG (run_c2r checks)
-            const float4* q = reinterpret_cast<const float4*>(in + ((int64_t)bin * ntile + tile) * ldc + cg);
+        for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
+        if (cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
+            const float4* qq = reinterpret_cast<const float4*>(
+                GM ? in + (((int64_t)(cg >> 3) * ntile + tile) * Z::BINS + bin) * 8
+                   : in + ((int64_t)bin * ntile + tile) * ldc + cg);
 #pragma unroll
-            for (int k = 0; k < VG / 2; ++k) {
-                const float4 w = q[k];
+            for (int k = 0; k < 4; ++k) {
+                const float4 w = qq[k];
                 v[2 * k] = make_float2(w.x, w.y);
                 v[2 * k + 1] = make_float2(w.z, w.w);
             }
         }
 #pragma unroll
-        for (int k = 0; k < VG; ++k) sm[(size_t)(VG * g + k) * Z::BINS + bin] = v[k];
+        for (int k = 0; k < 8; ++k) sm[(size_t)(8 * g + k) * Z::BINS + bin] = v[k];
     }
     __syncthreads();
     float2* R = sm + (size_t)ch * Z::BINS;  // [F][H2]
+    float2 a[HF];
     {
-        float2 a[F];
-        if (l == 0) {
-#pragma unroll
-            for (int fy = 0; fy < F; ++fy) {
-                const float2 x0 = R[fy * H2], xh = R[fy * H2 + HF];
-                a[brev_c(fy, LOG)] = make_float2(x0.x - xh.y, x0.y + xh.x);
+        // column slot l at rows n and n + F/2 (slot 0: columns 0 and F/2 packed)
+        auto col = [&](int r) -> float2 {
+            if (l == 0) {
+                const float2 x0 = R[r * H2], xh = R[r * H2 + HF];
+                return make_float2(x0.x - xh.y, x0.y + xh.x);
             }
+            return R[r * H2 + l];
+        };
+        if (h == 0) {
+#pragma unroll
+            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = cadd(col(n), col(n + HF));
         } else {
 #pragma unroll
-            for (int fy = 0; fy < F; ++fy) a[brev_c(fy, LOG)] = R[fy * H2 + l];
+            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = twiddle<F, true>(csub(col(n), col(n + HF)), n);
         }
-        fft_reg<F, true>(a);
-#pragma unroll
-        for (int r = 0; r < F; ++r) R[r * H2 + l] = a[r];
     }
-    __syncwarp();
+    __syncthreads();  // every lane has read its column before the columns are rewritten
+    fft_reg<HF, true>(a);  // a[s] = column value at row 2s + h
+#pragma unroll
+    for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
+    __syncthreads();
     const int hb = B >> 1, ob = B + 1;  // row pairs; staged row stride
     float* O = reinterpret_cast<float*>(R);
-    {
-        float2 a[F];
-        if (l < hb) {
-            const float2* r1 = R + (off + l) * H2;
-            const float2* r2 = R + (off + l + hb) * H2;
-            const float2 p1 = r1[0], p2 = r2[0];  // (bin 0, bin F/2) of each row, both real
-            a[0] = make_float2(p1.x, p2.x);
-            a[brev_c(HF, LOG)] = make_float2(p1.y, p2.y);
-#pragma unroll
-            for (int k = 1; k < F; ++k) {
-                if (k == HF) continue;
-                float2 t1, t2;
-                if (k < HF) {
-                    t1 = r1[k];
-                    t2 = r2[k];
-                } else {
-                    t1 = r1[F - k];
-                    t2 = r2[F - k];
-                    t1.y = -t1.y;
-                    t2.y = -t2.y;
-                }
-                a[brev_c(k, LOG)] = make_float2(t1.x - t2.y, t1.y + t2.x);
+    if (l < hb) {
+        const float2* r1 = R + (off + l) * H2;
+        const float2* r2 = R + (off + l + hb) * H2;
+        // the packed row pair's spectrum Q[k] = R1[k] + i R2[k] over all F bins
+        auto Q = [&](int k) -> float2 {
+            if (k == 0) return make_float2(r1[0].x, r2[0].x);
+            if (k == HF) return make_float2(r1[0].y, r2[0].y);
+            float2 t1, t2;
+            if (k < HF) {
+                t1 = r1[k];
+                t2 = r2[k];
+            } else {
+                t1 = r1[F - k];
+                t2 = r2[F - k];
+                t1.y = -t1.y;
+                t2.y = -t2.y;
             }
-            fft_reg<F, true>(a);
-        }
-        __syncwarp();  // every lane has read its rows before R is reused for the outputs
-        if (l < hb) {
+            return make_float2(t1.x - t2.y, t1.y + t2.x);
+        };
+        if (h == 0) {
 #pragma unroll
-            for (int x = 0; x < F; ++x) {
-                const int j = x - off;
-                if (j >= 0 && j < B) {
-                    O[l * ob + j] = a[x].x * scale;
-                    O[(l + hb) * ob + j] = a[x].y * scale;
-                }
+            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = cadd(Q(n), Q(n + HF));
+        } else {
+#pragma unroll
+            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = twiddle<F, true>(csub(Q(n), Q(n + HF)), n);
+        }
+    }
+    __syncthreads();  // every lane has read its rows before R is reused for the outputs
+    if (l < hb) {
+        fft_reg<HF, true>(a);  // a[s] = row(off+l)[x] + i row(off+l+hb)[x], x = 2s + h
+#pragma unroll
+        for (int s2 = 0; s2 < HF; ++s2) {
+            const int j = 2 * s2 + h - off;
+            if (j >= 0 && j < B) {
+                O[l * ob + j] = a[s2].x * scale;
+                O[(l + hb) * ob + j] = a[s2].y * scale;
             }
         }
     }
-    __syncwarp();
+    __syncthreads();
     if (c < nch) {
-        // lanes take output columns j = l and l + F/2 (B < F) of one row at a time
+        // lane q takes output column j = q of one row at a time (B < F)
         const auto chn = view.chan(c);
-        const bool ok0 = l < B && view.col_ok(l), ok1 = l + HF < B && view.col_ok(l + HF);
+        const bool ok = q < B && view.col_ok(q);
         for (int i = 0; i < B; ++i) {
             const auto w = view.row(chn, i);
             if (!w.ok) break;  // the rows below are outside the grid as well
-            if (ok0) view.put(w, l, O[i * ob + l]);
-            if (ok1) view.put(w, l + HF, O[i * ob + l + HF]);
+            if (ok) view.put(w, q, O[i * ob + q]);
         }
     }
 }
@@ -964,7 +1015,7 @@ cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, Out out, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((ldc + FftSize<F>::R2C_CH - 1) / FftSize<F>::R2C_CH), (unsigned)ntile);
-    k_fft_r2c<F, Src, Out><<<grid, 32 * FftSize<F>::R2C_WARPS, smem, st>>>(src, nch, ldc, out);
+    k_fft_r2c<F, Src, Out><<<grid, FftSize<F>::THREADS, smem, st>>>(src, nch, ldc, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -990,17 +1041,26 @@ cudaError_t r2c_grouped(const FftPlan& p, Src src, int nch, int ldc, int ntile,
     return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
 }
 
-template <int F, class Dst>
-cudaError_t run_c2r(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
-                    cudaStream_t st) {
+template <int F, bool GM, class Dst>
+cudaError_t run_c2r_l(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
+                      cudaStream_t st) {
     if (ldc % 8 != 0) return cudaErrorInvalidValue;  // whole 8-channel groups per row
     const size_t smem = fft_smem<F>(false);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)ntile, (unsigned)((nch + FftSize<F>::C2R_CH - 1) / FftSize<F>::C2R_CH));
-    k_fft_c2r<F, Dst><<<grid, 32 * FftSize<F>::C2R_WARPS, smem, st>>>(in, nch, ldc, ntile, off, B, 1.0f / (F * F), dst);
+    k_fft_c2r<F, Dst, GM><<<grid, FftSize<F>::THREADS, smem, st>>>(in, nch, ldc, ntile, off, B,
+                                                                         1.0f / (F * F), dst);
     count_launch();
     return cudaGetLastError();
+}
+// gm: the spectra come group-major from the tensor-core contraction
+template <int F, class Dst>
+cudaError_t run_c2r(bool gm, const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
+                    cudaStream_t st) {
+    return gm ? run_c2r_l<F, true>(in, nch, ldc, ntile, off, B, dst, st)
+              : run_c2r_l<F, false>(in, nch, ldc, ntile, off, B, dst, st);
 }
 
 }  // namespace
@@ -1075,8 +1135,8 @@ cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
               (int64_t)g.S * L2, (int64_t)g.H * g.W};
-    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
 }
 
 cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* rcm,
@@ -1093,8 +1153,8 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
                (int64_t)g.C * L2, (int64_t)g.Nz * g.H * g.W};
-    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
-                     : run_c2r<32>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 static cudaError_t cm_copy(bool to, const float* src, const Geo& g, int planes, float* dst, cudaStream_t st) {
@@ -1168,8 +1228,8 @@ cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b,
     e = b.cg ? cgemm_forward(b.cg, ncol, st) : contract_fwd_all(p, g, b.Wf, b.Xh, b.Yh, ncol, st);
     if (e != cudaSuccess) return e;
     TabHvDst dst{fr, colf, col0, g.N, p.B, eps};
-    return p.F == 64 ? run_c2r<64>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
 }
 
 cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
@@ -1181,8 +1241,8 @@ cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b
     e = b.cg ? cgemm_adjoint(b.cg, ncol, st) : contract_adj_all(p, g, b.Wf, b.Yh, b.Xh, ncol, st);
     if (e != cudaSuccess) return e;
     TabVolDst dst{fr, colf, col0, g.N, g.S, p.B};
-    return p.F == 64 ? run_c2r<64>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
-                     : run_c2r<32>(b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 // one item per thread (no grid-stride tail), one flux partial per block

@@ -75,7 +75,7 @@ struct CgArgs {
     int nkb;           // k-blocks of 64 per unit
     int nrows;         // valid rows (S or C)
     int ld;            // row length of the output (Sf or Cf)
-    float2* out;       // [bins][ntile][ld]
+    float2* out;       // [ld/8][ncol][bins][8] (group-major)
     int* err;
     const int* lo_slot;  // adaptive lo planes: [bins][nkbc] compact slot, 0 = dropped
     int nkbc;            // 64-channel blocks of the PSF spectra
@@ -319,11 +319,14 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                     tmem_ld16(tb + N + g * 16, im);
                     tmem_wait_ld();
                     if (grow < a.nrows) {
-                        float2* o = a.out + ((int64_t)bin * a.ncol + col0) * a.ld + grow;
+                        // group-major output [ld/8][ncol][bins][8]: the inverse
+                        // transform reads a column's bins of 8 rows as one run
+                        float2* o = a.out + (((int64_t)(grow >> 3) * a.ncol + col0) * a.nbins + bin) * 8 +
+                                    (grow & 7);
 #pragma unroll
                         for (int t = 0; t < 16; ++t) {
                             if (col0 + t < a.ncol) {
-                                float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.ld);
+                                float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.nbins * 8);
                                 const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
                                 if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
                                 else red_add_v2(dst, vr, vi);
