@@ -94,6 +94,19 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[N]) {
     fft_stage<N, 2, INV>(a);
 }
 
+// Barrier of the F lanes of one channel of a transform block: a named
+// barrier (id 1 + ch) over the channel's two warps when F = 64, the warp
+// itself when F = 32; the channels of a block go through their phases
+// independently.
+template <int F>
+__device__ __forceinline__ void chan_sync(int ch) {
+    if constexpr (F >= 64) {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + ch), "r"(F) : "memory");
+    } else {
+        __syncwarp();
+    }
+}
+
 // v * exp(-+2 pi i n / F) for 0 <= n < F/2 (the decimation-in-frequency
 // twiddle; INV: conjugate), a constant-bank operand when n is a constant
 template <int F, bool INV>
@@ -259,94 +272,93 @@ struct OutPlanesG {
 // decimation in frequency: lane h = 0 transforms u[n] = x[n] + x[n + F/2] and
 // obtains the even outputs X[2r], lane h = 1 transforms
 // u[n] = (x[n] - x[n + F/2]) exp(-2 pi i n / F) and obtains the odd ones
-// X[2r + 1]; both read their inputs from shared memory. An F/2-point
-// transform in registers per lane keeps the block at 512 threads.
-//   load:    lane q loads column q of every patch row (coalesced across lanes,
-//            all loads issued before the stores); patch rows in shared memory
-//            (row stride F+1);
+// X[2r + 1]. The sums and differences are formed by the lanes that produce
+// the values (so a lane reads only the F/2 values it transforms), and an
+// F/2-point transform in registers per lane keeps the block at 512 threads.
+//   load:    lane (h, l) loads columns l and l + F/2 of the patch rows
+//            [h F/2, h F/2 + F/2) (coalesced across lanes) and stores their
+//            sum and difference, Sx[r][l] and Dx[r][l];
 //   rows:    lanes (h, l) transform rows l and l + F/2 packed as one complex
-//            row z = p_l + i p_{l+F/2} and separate the two half spectra (X[k]
-//            and X[F-k] have the same parity, so each lane holds both); the
-//            real bins fx = 0 and F/2 of a row go to slot 0 as one complex
-//            value (bin 0 real part, bin F/2 real part);
-//   columns: lanes (h, l) transform column slot l, for l = 0 the packed real
-//            columns 0 and F/2, which they separate afterwards.
+//            row z = p_l + i p_{l+F/2} (from Sx, or from Dx with the twiddle)
+//            and separate the two half spectra (X[k] and X[F-k] have the same
+//            parity, so each lane holds both); the real bins fx = 0 and F/2
+//            of a row go to slot 0 as one complex value (bin 0 real part,
+//            bin F/2 real part). For the columns they store, per bin, the
+//            sum of rows l and l + F/2 in row l and their difference times
+//            exp(-2 pi i l / F) in row l + F/2;
+//   columns: lanes (h, l) transform column slot l (rows [h F/2, h F/2 + F/2)
+//            hold their inputs), for l = 0 the packed real columns 0 and F/2,
+//            which they separate afterwards.
 // The half spectra stay in shared memory [channel][fy or row][fx], in place.
 // Grid: x = channel group (fastest, so blocks running together fill adjacent
 // parts of the same output rows), y = column.
 template <int F, class Src, class Out>
 __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
     using Z = FftSize<F>;
-    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH, PS = F + 1;
+    constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH, PS = HF + 1;
     extern __shared__ float2 sm[];
     const int ch = threadIdx.x / F, q = threadIdx.x % F;
     const int h = q / HF, l = q % HF;
     const int tile = blockIdx.y, c0 = blockIdx.x * CH, c = c0 + ch;
     const auto view = src.bind(tile);
-    float2* R = sm + (size_t)ch * Z::BINS;          // [F][H2]
-    float* Pm = reinterpret_cast<float*>(R);        // [F][PS] real patch (same space)
+    float2* R = sm + (size_t)ch * Z::BINS;          // [F][H2] half spectra
+    float* Sx = reinterpret_cast<float*>(R);        // [F][PS] row-half sums (same space)
+    float* Dx = Sx + F * PS;                        // [F][PS] row-half differences
     const bool on = c < nch;
+    const float2 wl = c_tw[l * (64 / F)];           // exp(-2 pi i l / F), this lane's row twiddle
     {
-        const bool okx = on && view.col_ok(q);
-        constexpr int RB = F < 32 ? F : 32;  // rows per batch of loads in flight
+        const bool ok0 = on && view.col_ok(l), ok1 = on && view.col_ok(l + HF);
+        float t0[HF], t1[HF];
 #pragma unroll
-        for (int r0 = 0; r0 < F; r0 += RB) {
-            float t[RB];
+        for (int r = 0; r < HF; ++r) {
+            const SrcRow w = view.row(on ? c : 0, h * HF + r);
+            t0[r] = (ok0 && w.ok) ? view.at(w, l) : 0.f;
+            t1[r] = (ok1 && w.ok) ? view.at(w, l + HF) : 0.f;
+        }
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const SrcRow w = view.row(on ? c : 0, r0 + r);
-                t[r] = (okx && w.ok) ? view.at(w, q) : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < RB; ++r) Pm[(r0 + r) * PS + q] = t[r];
+        for (int r = 0; r < HF; ++r) {
+            Sx[(h * HF + r) * PS + l] = t0[r] + t1[r];
+            Dx[(h * HF + r) * PS + l] = t0[r] - t1[r];
         }
     }
-    __syncthreads();
+    chan_sync<F>(ch);
     float2 a[HF];
     if (h == 0) {
 #pragma unroll
-        for (int n = 0; n < HF; ++n) {
-            const float2 z0 = make_float2(Pm[l * PS + n], Pm[(l + HF) * PS + n]);
-            const float2 z1 = make_float2(Pm[l * PS + n + HF], Pm[(l + HF) * PS + n + HF]);
-            a[brev_c(n, LOG - 1)] = cadd(z0, z1);
-        }
+        for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = make_float2(Sx[l * PS + n], Sx[(l + HF) * PS + n]);
     } else {
 #pragma unroll
-        for (int n = 0; n < HF; ++n) {
-            const float2 z0 = make_float2(Pm[l * PS + n], Pm[(l + HF) * PS + n]);
-            const float2 z1 = make_float2(Pm[l * PS + n + HF], Pm[(l + HF) * PS + n + HF]);
-            a[brev_c(n, LOG - 1)] = twiddle<F, false>(csub(z0, z1), n);
-        }
+        for (int n = 0; n < HF; ++n)
+            a[brev_c(n, LOG - 1)] = twiddle<F, false>(make_float2(Dx[l * PS + n], Dx[(l + HF) * PS + n]), n);
     }
-    __syncthreads();  // the half spectra below overwrite the patch
+    chan_sync<F>(ch);  // the half spectra below overwrite the row halves
     fft_reg<HF, false>(a);  // a[r] = Z[2r + h]
+    // bin k of rows l (A) and l + HF (B): column inputs A + B and (A - B) w_l
+    auto put = [&](int k, float2 A, float2 B) {
+        R[l * H2 + k] = cadd(A, B);
+        const float2 d = csub(A, B);
+        R[(l + HF) * H2 + k] = make_float2(fmaf(d.x, wl.x, -d.y * wl.y), fmaf(d.x, wl.y, d.y * wl.x));
+    };
     if (h == 0) {
-        R[l * H2] = make_float2(a[0].x, a[HF / 2].x);
-        R[(l + HF) * H2] = make_float2(a[0].y, a[HF / 2].y);
+        put(0, make_float2(a[0].x, a[HF / 2].x), make_float2(a[0].y, a[HF / 2].y));
 #pragma unroll
         for (int r = 1; r < HF / 2; ++r) {
             const float2 z = a[r], m = a[HF - r];
-            R[l * H2 + 2 * r] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
-            R[(l + HF) * H2 + 2 * r] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+            put(2 * r, make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y)),
+                make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x)));
         }
     } else {
 #pragma unroll
         for (int r = 0; r < HF / 2; ++r) {
             const float2 z = a[r], m = a[HF - 1 - r];
-            R[l * H2 + 2 * r + 1] = make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y));
-            R[(l + HF) * H2 + 2 * r + 1] = make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x));
+            put(2 * r + 1, make_float2(0.5f * (z.x + m.x), 0.5f * (z.y - m.y)),
+                make_float2(0.5f * (z.y + m.y), 0.5f * (m.x - z.x)));
         }
     }
-    __syncthreads();
-    if (h == 0) {
+    chan_sync<F>(ch);
 #pragma unroll
-        for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = cadd(R[n * H2 + l], R[(n + HF) * H2 + l]);
-    } else {
-#pragma unroll
-        for (int n = 0; n < HF; ++n)
-            a[brev_c(n, LOG - 1)] = twiddle<F, false>(csub(R[n * H2 + l], R[(n + HF) * H2 + l]), n);
-    }
-    __syncthreads();  // every lane has read its column before the columns are rewritten
+    for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = R[(h * HF + n) * H2 + l];
+    chan_sync<F>(ch);  // every lane has read its column before the columns are rewritten
     fft_reg<HF, false>(a);  // a[s] = Y[2s + h]
     if (l == 0) {  // packed real columns 0 (real part) and F/2 (imaginary part); slot HF is free
 #pragma unroll
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_r2c(Src src, int
 #pragma unroll
         for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
     }
-    __syncthreads();
+    __syncthreads();  // the output loop reads every channel of the block
     // every bin of 8 consecutive channels at a time
     for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
         const int bin = e % Z::BINS, g = e / Z::BINS;
@@ -518,52 +530,61 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2
     const int tile = blockIdx.x, c0 = blockIdx.y * CH, c = c0 + ch;
     const auto view = dst.bind(tile);
     // spectra of 8 consecutive channels per bin (one thread reads them with
-    // 16-byte loads), into [channel][bin]
+    // 16-byte loads) for the bins (fy, fx) and (fy + F/2, fx), stored into
+    // [channel][bin] as the column transform's inputs: their sum in row fy and
+    // their difference times exp(2 pi i fy / F) in row fy + F/2
     static_assert(CH % 8 == 0, "whole channel groups per block");
-    for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
-        const int bin = e % Z::BINS, g = e / Z::BINS, cg = c0 + 8 * g;
-        float2 v[8];
+    for (int e = threadIdx.x; e < HF * H2 * (CH / 8); e += blockDim.x) {
+        const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + 8 * g;
+        const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
+        float2 v0[8], v1[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 8; ++k) v0[k] = v1[k] = make_float2(0.f, 0.f);
         if (cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
-            const float4* qq = reinterpret_cast<const float4*>(
-                GM ? in + (((int64_t)(cg >> 3) * ntile + tile) * Z::BINS + bin) * 8
-                   : in + ((int64_t)bin * ntile + tile) * ldc + cg);
+            const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8
+                                    : in + (int64_t)tile * ldc + cg;
+            const int64_t bstride = GM ? 8 : (int64_t)ntile * ldc;  // float2 between bins
+            const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
+            const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 w = qq[k];
-                v[2 * k] = make_float2(w.x, w.y);
-                v[2 * k + 1] = make_float2(w.z, w.w);
+                const float4 w0 = q0[k], w1 = q1[k];
+                v0[2 * k] = make_float2(w0.x, w0.y);
+                v0[2 * k + 1] = make_float2(w0.z, w0.w);
+                v1[2 * k] = make_float2(w1.x, w1.y);
+                v1[2 * k + 1] = make_float2(w1.z, w1.w);
             }
         }
+        const float2 w = c_tw[fy * (64 / F)];  // conjugated below
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sm[(size_t)(8 * g + k) * Z::BINS + bin] = v[k];
+        for (int k = 0; k < 8; ++k) {
+            float2* dst = sm + (size_t)(8 * g + k) * Z::BINS;
+            dst[b0] = cadd(v0[k], v1[k]);
+            const float2 d = csub(v0[k], v1[k]);
+            dst[b1] = make_float2(fmaf(d.x, w.x, d.y * w.y), fmaf(d.y, w.x, -d.x * w.y));
+        }
     }
     __syncthreads();
     float2* R = sm + (size_t)ch * Z::BINS;  // [F][H2]
     float2 a[HF];
-    {
-        // column slot l at rows n and n + F/2 (slot 0: columns 0 and F/2 packed)
-        auto col = [&](int r) -> float2 {
-            if (l == 0) {
-                const float2 x0 = R[r * H2], xh = R[r * H2 + HF];
-                return make_float2(x0.x - xh.y, x0.y + xh.x);
-            }
-            return R[r * H2 + l];
-        };
-        if (h == 0) {
+    // column slot l, rows [h F/2, h F/2 + F/2) (slot 0: columns 0 and F/2 packed)
 #pragma unroll
-            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = cadd(col(n), col(n + HF));
+    for (int n = 0; n < HF; ++n) {
+        const int r = h * HF + n;
+        float2 y;
+        if (l == 0) {
+            const float2 x0 = R[r * H2], xh = R[r * H2 + HF];
+            y = make_float2(x0.x - xh.y, x0.y + xh.x);
         } else {
-#pragma unroll
-            for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = twiddle<F, true>(csub(col(n), col(n + HF)), n);
+            y = R[r * H2 + l];
         }
+        a[brev_c(n, LOG - 1)] = y;
     }
-    __syncthreads();  // every lane has read its column before the columns are rewritten
+    chan_sync<F>(ch);  // every lane has read its column before the columns are rewritten
     fft_reg<HF, true>(a);  // a[s] = column value at row 2s + h
 #pragma unroll
     for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
-    __syncthreads();
+    chan_sync<F>(ch);
     const int hb = B >> 1, ob = B + 1;  // row pairs; staged row stride
     float* O = reinterpret_cast<float*>(R);
     if (l < hb) {
@@ -593,7 +614,7 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2
             for (int n = 0; n < HF; ++n) a[brev_c(n, LOG - 1)] = twiddle<F, true>(csub(Q(n), Q(n + HF)), n);
         }
     }
-    __syncthreads();  // every lane has read its rows before R is reused for the outputs
+    chan_sync<F>(ch);  // every lane has read its rows before R is reused for the outputs
     if (l < hb) {
         fft_reg<HF, true>(a);  // a[s] = row(off+l)[x] + i row(off+l+hb)[x], x = 2s + h
 #pragma unroll
@@ -605,7 +626,7 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2
             }
         }
     }
-    __syncthreads();
+    chan_sync<F>(ch);
     if (c < nch) {
         // lane q takes output column j = q of one row at a time (B < F)
         const auto chn = view.chan(c);

@@ -332,21 +332,21 @@ void complete_tick(lfd_server* s, PsfSet& ps) {
 #define TICK_CK(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess) {                                                          \
-            fail_set(s, ps, LFD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-            return;                                                                       \
-        }                                                                                 \
+        if (e_ != cudaSuccess) return std::string(#call) + ": " + cudaGetErrorString(e_); \
     } while (0)
 
-void enqueue_tick(lfd_server* s, PsfSet& ps) {
+// Issues the work of one tick of a set (its lists already swapped in):
+// results out, the column table, new frames' inputs, the projections, the
+// updates and metrics, the histories to the host and the tick's event.
+// Touches only the set's own buffers and the device buffers of its frames in
+// flight, which no client call reads, so it runs without the server's lock.
+// Returns "" or what failed.
+std::string launch_tick(lfd_server* s, PsfSet& ps) {
     cudaGetLastError();  // the launch checks below read the thread's last error
     const lfd_options& o = s->opt.opt;
     const int mf = s->opt.max_frames_per_set;
     cudaStream_t st = ps.st;
     const Geo& gs = ps.gmax;
-    ps.ran_fin.swap(ps.finishing);
-    ps.ran_iter = ps.iter;
-    ps.ran_new.swap(ps.fresh);
 
     // 1. results out (stack order), straight into v_out or through xcm
     for (Job* j : ps.ran_fin) {
@@ -359,10 +359,7 @@ void enqueue_tick(lfd_server* s, PsfSet& ps) {
     }
 
     // column table: iterating frames first, then the new ones
-    if ((int)(ps.ran_iter.size() + ps.ran_new.size()) > mf) {
-        fail_set(s, ps, LFD_EINTERNAL, "more frames in a tick than max_frames_per_set");
-        return;
-    }
+    if ((int)(ps.ran_iter.size() + ps.ran_new.size()) > mf) return "more frames in a tick than max_frames_per_set";
     int nfr = 0, col = 0, iter_cols = 0;
     for (int pass = 0; pass < 2; ++pass) {
         for (Job* j : pass == 0 ? ps.ran_iter : ps.ran_new) {
@@ -445,9 +442,27 @@ void enqueue_tick(lfd_server* s, PsfSet& ps) {
                                 cudaMemcpyDeviceToHost, st));
     }
     TICK_CK(cudaEventRecord(ps.ev, st));
+    ps.tick_cols = iter_cols;
+    return std::string();
+}
+
+// Starts a tick of the set: swaps its lists in under the lock, issues the
+// launches with the lock released (client threads may submit, poll and
+// cancel meanwhile), then takes the lock back for the bookkeeping.
+void enqueue_tick(lfd_server* s, PsfSet& ps, std::unique_lock<std::mutex>& lk) {
+    ps.ran_fin.swap(ps.finishing);
+    ps.ran_iter = ps.iter;
+    ps.ran_new.swap(ps.fresh);
+    lk.unlock();
+    const std::string why = launch_tick(s, ps);
+    lk.lock();
+    if (!why.empty()) {
+        fail_set(s, ps, why.rfind("more frames", 0) == 0 ? LFD_EINTERNAL : LFD_ECUDA, why);
+        return;
+    }
     ps.busy = true;
     ++s->stats.ticks;
-    s->stats.columns += iter_cols;
+    s->stats.columns += ps.tick_cols;
 }
 
 void admit(lfd_server* s) {
@@ -503,12 +518,12 @@ void scheduler(lfd_server* s) {
             }
         if (s->arena.base) admit(s);
         bool any_work = false;
-        for (auto& up : s->sets) {
-            PsfSet& ps = *up;
+        for (size_t si = 0; si < s->sets.size(); ++si) {  // (sets are fixed once requests arrive)
+            PsfSet& ps = *s->sets[si];
             const bool work = !ps.iter.empty() || !ps.fresh.empty() || !ps.finishing.empty();
             any_work = any_work || work || ps.busy;
             if (!ps.busy && work) {
-                enqueue_tick(s, ps);
+                enqueue_tick(s, ps, lk);
                 progressed = true;
             }
         }
