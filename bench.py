@@ -684,8 +684,8 @@ def measure_batch(args, rank, world, local, precisions=("bf16x3", "bf16", "fp32"
     results = {}
     for prec in precisions:
         opt = lfd.lfd_default_options(precision=prec, variant="fft", max_frames=nf)
-        best, tune_ms = lfd.lfd_autotune(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
-        opt.fft_size = best
+        tune_ms, _ = lfd.lfd_autotune_options(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+        best, cols = opt.fft_size, opt.contraction_cols
         ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
         v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
         lfd.lfd_rl_iterate_batch(ctx, nf, y_d, v, 1)   # warm-up
@@ -705,9 +705,25 @@ def measure_batch(args, rank, world, local, precisions=("bf16x3", "bf16", "fp32"
         results[prec] = {"frames_per_s": aggregate(nf, world, secs), "seconds": secs,
                          "iterations_run": ran, "iters_done": done,
                          "frame_iterations_per_s": aggregate(nf * ran, world, secs),
-                         "fft_size": best, "autotune_ms_per_iteration": tune_ms,
+                         "fft_size": best, "contraction_cols": cols or "widest needed",
+                         "autotune_ms_per_iteration": tune_ms,
                          "gpu_launches": lfd.lfd_launch_count() - l0, "clocks": clk.summary()}
         lfd.lfd_destroy(ctx)
+        if prec == precisions[0]:
+            # the same run with one launch per stage instead of a CUDA-graph
+            # replay per iteration: what the launches cost between the kernels
+            opt.use_graph = 0
+            ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+            v.fill_(1.0)
+            lfd.lfd_rl_iterate_batch(ctx, nf, y_d, v, 1)
+            v.fill_(1.0)
+            torch.cuda.synchronize()
+            a.record(stream)
+            lfd.lfd_rl_iterate_batch(ctx, nf, y_d, v, cap, True, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            results[prec]["plain_launches_seconds"] = a.elapsed_time(b) / 1e3
+            lfd.lfd_destroy(ctx)
         del v
         torch.cuda.empty_cache()
     if "fp32" in results:

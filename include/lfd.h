@@ -102,6 +102,12 @@ typedef struct {
                              reaches tau x the largest of all spectra; a dropped
                              lo part is below 2^-9 tau of that largest value.
                              0 keeps every lo plane; default 2^-10; [0, 1)       */
+    int contraction_cols; /* LFD_FFT on the tensor cores: the widest column chunk of
+                             one contraction pass (16, 32 or 64 columns = frames x
+                             tiles; every chunk streams the PSF spectra once); 0
+                             (default) the widest the frames need, up to 64.
+                             Wider chunks stream the spectra fewer times with
+                             fewer stages in flight (see lfd_autotune_options) */
 } lfd_options;
 
 /* How the two projections are computed (same results up to rounding). */
@@ -183,9 +189,11 @@ lfd_status lfd_rl_iterate_batch(lfd_ctx* ctx, int nframes, const float* y, float
                                 double* entropy_hist, double* flux_hist, void* cuda_stream);
 
 /* Picks the fastest LFD_FFT transform size for this PSF, sensor shape and
- * opt->max_frames by measurement: for each feasible size a context is created,
- * one RL iteration of max_frames frames of a constant image is run to warm up
- * and two more are timed with CUDA events; the contexts are destroyed again.
+ * opt->max_frames by measurement (lfd_autotune_options, with the contraction's
+ * column chunk opt->contraction_cols kept fixed): for each feasible size a
+ * context is created, one RL iteration of max_frames frames of a constant
+ * image is run to warm up and two more are timed with CUDA events; the
+ * contexts are destroyed again.
  *   opt          options of the context to tune (variant must be LFD_FFT)
  *   best_size    (out) 32 or 64, to pass as opt->fft_size to lfd_create
  *   ms_per_iter  (out, may be NULL) measured time of one batched iteration of
@@ -195,6 +203,24 @@ lfd_status lfd_rl_iterate_batch(lfd_ctx* ctx, int nframes, const float* y, float
 lfd_status lfd_autotune(const float* psf, int P, int Nnum, int Nz, int H, int W,
                         const lfd_options* opt, void* cuda_stream, int* best_size,
                         float* ms_per_iter);
+
+/* Picks the LFD_FFT tiles for this PSF, sensor shape and opt->max_frames by
+ * measurement: the transform size (fft_size 32 or 64) and the contraction's
+ * column chunk (contraction_cols 16, 32 or 64, the chunks wider than the
+ * frames' columns need left out) on the tensor cores. For each feasible pair
+ * a context is created, one batched RL iteration of a constant image warms
+ * it up and two more are timed with CUDA events. The winner is written into
+ * *opt (fft_size, contraction_cols; the other fields are kept), ready for
+ * lfd_create, and cached for the process: a later call with the same PSF
+ * (pointer and a sample of its values), shape, frames, precision and lo-plane
+ * threshold returns it without timing (*cached = 1).
+ *   opt          in: options of the context to tune (variant LFD_FFT); out: the choice
+ *   ms_per_iter  (out, may be NULL) measured time of one batched iteration of the winner
+ *   cached       (out, may be NULL) 1 when the result came from the cache
+ * Errors: LFD_EINVAL, LFD_EUNSUPPORTED (no pair fits), and those of lfd_create.
+ * Allocates and frees device memory; synchronises the stream. */
+lfd_status lfd_autotune_options(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                                lfd_options* opt, void* cuda_stream, float* ms_per_iter, int* cached);
 
 /* DCT entropy (Eq. 12 over the region of Eq. 6) of the z-maximum projection of
  * the volume v [Nz][H][W] (host or device); result in *entropy (host).

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "lfd_internal.h"
@@ -333,6 +334,9 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (opt.max_frames < 1 || opt.max_frames > 4096) return LFD_EINVAL;
     if (opt.fft_size != 0 && opt.fft_size != 32 && opt.fft_size != 64) return LFD_EINVAL;
     if (!(opt.spectra_lo_tau >= 0.f && opt.spectra_lo_tau < 1.f)) return LFD_EINVAL;
+    if (opt.contraction_cols != 0 && opt.contraction_cols != 16 && opt.contraction_cols != 32 &&
+        opt.contraction_cols != 64)
+        return LFD_EINVAL;
     if (opt.max_frames > 1 && opt.variant != LFD_FFT) return LFD_EUNSUPPORTED;
     if (opt.precision == LFD_TF32 && opt.variant != LFD_DIRECT) return LFD_EUNSUPPORTED;
     int XS = opt.XS, YS = opt.YS;
@@ -498,6 +502,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
             cb.bins = fplan.bins;
             cb.ntile = fplan.ntile;
             cb.ncolp = (ctx->mf * fplan.ntile + 15) / 16 * 16;
+            cb.max_cols = ctx->opt.contraction_cols;
             cb.S = g.S;
             cb.C = g.C;
             cb.Sw = fplan.Sw;
@@ -1218,58 +1223,164 @@ lfd_status lfd_quality(lfd_ctx* ctx, const float* v, double* entropy, void* cuda
     return LFD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// one batched RL iteration of opt's context, timed with CUDA events (ms), or
+// a status other than LFD_OK
+lfd_status time_tiles(const float* psf, int P, int Nnum, int Nz, int H, int W, const lfd_options& o,
+                      cudaStream_t st, float* ms_out) {
+    const int nf = o.max_frames;
+    const int64_t nimg = (int64_t)nf * H * W, nvol = (int64_t)nf * Nz * H * W;
+    lfd_ctx* ctx = nullptr;
+    lfd_status s = lfd_create(psf, P, Nnum, Nz, H, W, &o, st, &ctx);
+    if (s != LFD_OK) return s;
+    float* y = nullptr;
+    float* v = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = -1.f;
+    bool ok = cudaMalloc(&y, nimg * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&v, nvol * sizeof(float)) == cudaSuccess &&
+              cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    ok = ok && launch_fill(y, nimg, 10.f, st) == cudaSuccess && launch_fill(v, nvol, 1.f, st) == cudaSuccess;
+    ok = ok && lfd_rl_iterate_batch(ctx, nf, y, v, 1, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK;
+    ok = ok && cudaEventRecord(a, st) == cudaSuccess &&
+         lfd_rl_iterate_batch(ctx, nf, y, v, 2, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK &&
+         cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+         cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (y) cudaFree(y);
+    if (v) cudaFree(v);
+    lfd_destroy(ctx);
+    if (!ok) {
+        cudaGetLastError();
+        return LFD_ECUDA;
+    }
+    *ms_out = 0.5f * ms;
+    return LFD_OK;
+}
+
+// the fastest (fft_size, contraction_cols) of the candidates
+lfd_status tune_tiles(const float* psf, int P, int Nnum, int Nz, int H, int W, const lfd_options& base,
+                      cudaStream_t st, bool tune_cols, int* bestF, int* bestCols, float* best_ms) {
+    Geo g;
+    std::string why;
+    if (!make_geo(P, Nnum, Nz, H, W, &g, &why)) return LFD_EINVAL;
+    const int products = base.precision == LFD_BF16X3 ? 3 : base.precision == LFD_BF16 ? 2 : 0;
+    float best = 0.f;
+    int bF = 0, bC = 0;
+    lfd_status last = LFD_EUNSUPPORTED;
+    for (int F : {32, 64}) {
+        FftPlan plan{};
+        if (!fft_plan_for(g, &plan, F, base.max_frames, products)) continue;
+        const int need = std::min(64, (base.max_frames * plan.ntile + 15) / 16 * 16);
+        std::vector<int> cols;
+        if (!tune_cols || products == 0) cols.push_back(base.contraction_cols);
+        else
+            for (int c : {16, 32, 64})
+                if (c <= need) cols.push_back(c);
+        for (int c : cols) {
+            lfd_options o = base;
+            o.fft_size = F;
+            o.contraction_cols = c;
+            o.use_graph = 1;
+            float ms = 0.f;
+            const lfd_status s = time_tiles(psf, P, Nnum, Nz, H, W, o, st, &ms);
+            if (s != LFD_OK) {
+                if (s != LFD_EUNSUPPORTED) last = s;
+                continue;
+            }
+            if (bF == 0 || ms < best) {
+                best = ms;
+                bF = F;
+                bC = c;
+            }
+        }
+    }
+    if (bF == 0) return last;
+    *bestF = bF;
+    *bestCols = bC;
+    *best_ms = best;
+    return LFD_OK;
+}
+
+struct TuneResult {
+    int F, cols;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneResult> g_tune_cache;
+
+// cache key: the PSF (address and 16 of its values spread over the array),
+// the shape, the frames and the options that change the tiles' cost
+bool tune_key(const float* psf, int P, int Nnum, int Nz, int H, int W, const lfd_options& o, std::string* key) {
+    const int64_t count = (int64_t)Nz * Nnum * Nnum * P * P;
+    uint32_t sample[16];
+    for (int k = 0; k < 16; ++k) {
+        float x = 0.f;
+        if (cudaMemcpy(&x, psf + count * k / 16, sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        std::memcpy(&sample[k], &x, sizeof(x));
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%d|%p|%d|%d|%d|%d|%d|%d|%d|%a|", dev, (const void*)psf, P, Nnum, Nz, H, W,
+                  o.max_frames, o.precision, (double)o.spectra_lo_tau);
+    *key = buf;
+    for (uint32_t v : sample) *key += std::to_string(v) + ",";
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 lfd_status lfd_autotune(const float* psf, int P, int Nnum, int Nz, int H, int W,
                         const lfd_options* opt, void* cuda_stream, int* best_size,
                         float* ms_per_iter) {
     if (!psf || !opt || !best_size || opt->variant != LFD_FFT) return LFD_EINVAL;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int nf = opt->max_frames;
-    const int64_t nimg = (int64_t)nf * H * W, nvol = (int64_t)nf * Nz * H * W;
-    float best = 0.f;
-    int bestF = 0;
-    lfd_status last = LFD_EUNSUPPORTED;
-    for (int F : {32, 64}) {
-        lfd_options o = *opt;
-        o.fft_size = F;
-        o.use_graph = 1;
-        lfd_ctx* ctx = nullptr;
-        lfd_status s = lfd_create(psf, P, Nnum, Nz, H, W, &o, cuda_stream, &ctx);
-        if (s != LFD_OK) {
-            if (s != LFD_EUNSUPPORTED) last = s;
-            continue;
-        }
-        float* y = nullptr;
-        float* v = nullptr;
-        cudaEvent_t a = nullptr, b = nullptr;
-        float ms = -1.f;
-        bool ok = cudaMalloc(&y, nimg * sizeof(float)) == cudaSuccess &&
-                  cudaMalloc(&v, nvol * sizeof(float)) == cudaSuccess &&
-                  cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
-        ok = ok && launch_fill(y, nimg, 10.f, st) == cudaSuccess && launch_fill(v, nvol, 1.f, st) == cudaSuccess;
-        ok = ok && lfd_rl_iterate_batch(ctx, nf, y, v, 1, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK;
-        ok = ok && cudaEventRecord(a, st) == cudaSuccess &&
-             lfd_rl_iterate_batch(ctx, nf, y, v, 2, 0, nullptr, nullptr, nullptr, nullptr, st) == LFD_OK &&
-             cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
-             cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
-        if (y) cudaFree(y);
-        if (v) cudaFree(v);
-        lfd_destroy(ctx);
-        if (!ok) {
-            cudaGetLastError();
-            last = LFD_ECUDA;
-            continue;
-        }
-        ms *= 0.5f;
-        if (bestF == 0 || ms < best) {
-            best = ms;
-            bestF = F;
+    int F = 0, cols = 0;
+    float ms = 0.f;
+    const lfd_status s = tune_tiles(psf, P, Nnum, Nz, H, W, *opt, (cudaStream_t)cuda_stream, false, &F, &cols, &ms);
+    if (s != LFD_OK) return s;
+    *best_size = F;
+    if (ms_per_iter) *ms_per_iter = ms;
+    return LFD_OK;
+}
+
+lfd_status lfd_autotune_options(const float* psf, int P, int Nnum, int Nz, int H, int W,
+                                lfd_options* opt, void* cuda_stream, float* ms_per_iter, int* cached) {
+    if (!psf || !opt || opt->variant != LFD_FFT || opt->max_frames < 1) return LFD_EINVAL;
+    if (cached) *cached = 0;
+    std::string key;
+    const bool keyed = tune_key(psf, P, Nnum, Nz, H, W, *opt, &key);
+    if (keyed) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            opt->fft_size = it->second.F;
+            opt->contraction_cols = it->second.cols;
+            if (ms_per_iter) *ms_per_iter = it->second.ms;
+            if (cached) *cached = 1;
+            return LFD_OK;
         }
     }
-    if (bestF == 0) return last;
-    *best_size = bestF;
-    if (ms_per_iter) *ms_per_iter = best;
+    int F = 0, cols = 0;
+    float ms = 0.f;
+    const lfd_status s = tune_tiles(psf, P, Nnum, Nz, H, W, *opt, (cudaStream_t)cuda_stream, true, &F, &cols, &ms);
+    if (s != LFD_OK) return s;
+    opt->fft_size = F;
+    opt->contraction_cols = cols;
+    if (ms_per_iter) *ms_per_iter = ms;
+    if (keyed) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = TuneResult{F, cols, ms};
+    }
     return LFD_OK;
 }
 

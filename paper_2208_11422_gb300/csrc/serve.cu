@@ -607,6 +607,7 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
         cb.bins = p.bins;
         cb.ntile = p.ntile;
         cb.ncolp = ncolp;
+        cb.max_cols = o.contraction_cols;
         cb.S = g.S;
         cb.C = g.C;
         cb.Sw = p.Sw;
@@ -675,6 +676,9 @@ lfd_status lfd_server_create(const lfd_server_options* opt_in, lfd_server** out)
     *out = nullptr;
     lfd_server_options o;
     if (opt_in) o = *opt_in; else lfd_server_default_options(&o);
+    if (o.opt.contraction_cols != 0 && o.opt.contraction_cols != 16 && o.opt.contraction_cols != 32 &&
+        o.opt.contraction_cols != 64)
+        return LFD_EINVAL;
     if (o.opt.precision != LFD_FP32 && o.opt.precision != LFD_BF16 && o.opt.precision != LFD_BF16X3)
         return LFD_EINVAL;
     if (!(o.opt.eps >= 0.f)) return LFD_EINVAL;

@@ -566,7 +566,8 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     if (e != cudaSuccess) return e;
     if ((e = cudaMemset(s->err, 0, sizeof(int))) != cudaSuccess) return e;
     s->nwidths = 1;
-    while (s->nwidths < 3 && 16 * kNg[s->nwidths] <= b.ncolp) ++s->nwidths;
+    const int widest = b.max_cols > 0 ? b.max_cols : 64;
+    while (s->nwidths < 3 && 16 * kNg[s->nwidths] <= b.ncolp && 16 * kNg[s->nwidths] <= widest) ++s->nwidths;
     s->mode = b.lo.slot ? MODE_ADAPTIVE : (b.W[1] && b.W[3]) ? MODE_SPLIT : MODE_BF16;
     const int nslot = (int)b.lo.kept + 1;
     for (int i = 0; i < 4; ++i) {

@@ -32,6 +32,7 @@ struct CgemmBuffers {
     float2* Yout;             // [Sf/8][ncol][bins][8] forward output (group-major)
     float2* Xout;             // [Cf/8][ncol][bins][8] adjoint output (group-major)
     LoPlanes lo;              // adaptive lo planes (slot null otherwise)
+    int max_cols;             // widest column chunk (16, 32 or 64); 0: up to 64
 };
 
 // Builds the adaptive lo planes from the full planes b.W[0..3] ([bins][S][Cw]);

@@ -46,6 +46,7 @@ class lfd_options(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("fft_size", ctypes.c_int),
         ("spectra_lo_tau", ctypes.c_float),
+        ("contraction_cols", ctypes.c_int),
     ]
 
 
@@ -110,6 +111,8 @@ _SIGS = {
     "lfd_quality": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
     "lfd_autotune": (_I, [_VP, _I, _I, _I, _I, _I, ctypes.POINTER(lfd_options), _VP,
                           ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "lfd_autotune_options": (_I, [_VP, _I, _I, _I, _I, _I, ctypes.POINTER(lfd_options), _VP,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
     "lfd_quality_mip_static": (_I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
     "lfd_quality_mip": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
     "lfd_split_load": (_I, [_VP, _VP, _VP]),
@@ -326,6 +329,18 @@ def lfd_autotune(psf, P: int, Nnum: int, Nz: int, H: int, W: int, opt: lfd_optio
     if st != LFD_OK:
         raise LfdError(st, "lfd_autotune failed: %s" % lfd_status_string(st))
     return best.value, ms.value
+
+
+def lfd_autotune_options(psf, P: int, Nnum: int, Nz: int, H: int, W: int, opt: lfd_options, stream=None):
+    """Tunes opt.fft_size and opt.contraction_cols in place; returns
+    (ms per batched iteration of the winner, whether it came from the cache)."""
+    ms = ctypes.c_float(0)
+    cached = _I(0)
+    st = load().lfd_autotune_options(_ptr(psf), P, Nnum, Nz, H, W, ctypes.byref(opt), _stream(stream),
+                                     ctypes.byref(ms), ctypes.byref(cached))
+    if st != LFD_OK:
+        raise LfdError(st, "lfd_autotune_options failed: %s" % lfd_status_string(st))
+    return ms.value, bool(cached.value)
 
 
 def lfd_destroy(ctx):

@@ -70,6 +70,9 @@ def test_create_rejects_null_psf_and_bad_options(lib):
     assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
                           ctypes.byref(out)) == lfd.LFD_EINVAL
     assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, None, None, None) == lfd.LFD_EINVAL
+    o = lfd.lfd_default_options(variant="fft", contraction_cols=48)   # 16, 32 or 64
+    assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
+                          ctypes.byref(out)) == lfd.LFD_EINVAL
     o = lfd.lfd_default_options(precision="tf32", variant="fft")   # TF32 is a direct-GEMM mode
     assert lib.lfd_create(psf.ctypes.data, 25, 5, 5, 75, 75, ctypes.byref(o), None,
                           ctypes.byref(out)) == lfd.LFD_EUNSUPPORTED
@@ -115,7 +118,8 @@ def test_predict_stop_matches_oracle():
 
 
 STRUCTS = {
-    "lfd_options": ["precision", "eps", "dML_um", "XS", "l2_over_region", "fft_size"],
+    "lfd_options": ["precision", "eps", "dML_um", "XS", "l2_over_region", "fft_size", "spectra_lo_tau",
+                    "contraction_cols"],
     "lfd_server_options": ["opt", "arena_bytes", "max_frames_per_set", "max_iter"],
     "lfd_request": ["set_id", "H", "y", "v_out", "max_iter", "entropy_hist"],
     "lfd_result": ["status", "predicted", "queue_us", "latency_us"],

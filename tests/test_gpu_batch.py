@@ -231,3 +231,66 @@ def test_autotune_picks_the_faster_fft_size_and_its_context_matches_oracle():
         assert pred[0] == int(d["predicted"])
     finally:
         lfd.lfd_destroy(ctx)
+
+
+def test_autotune_options_tunes_fft_size_and_column_chunk_and_caches_the_choice():
+    """lfd_autotune_options on the mid-size frame with 8 frames (72 columns at
+    F = 32, so the contraction's 16-, 32- and 64-column chunks all apply):
+    the pair it writes into the options is the fastest within noise of the
+    pairs timed here directly, a second call returns it from the cache, and a
+    context made with those options reproduces the stored FP64 oracle run."""
+    import os
+    import time
+    import torch
+    from paper_2208_11422_gb300 import lfd
+    g = synth.CONFIGS[1]
+    psf = synth.make_psf(1)
+    dev = torch.device("cuda:0")
+    psf_d = torch.from_numpy(psf).to(dev)
+    nf = 8
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "lf_mid_615px_31z_psf165.npz"))
+    y = (d["y_counts"].astype(np.float64) + float(d["background"])).astype(np.float32)
+    ys = torch.from_numpy(np.stack([y] * nf)).to(dev)
+    opt = lfd.lfd_default_options(precision="bf16x3", variant="fft", max_frames=nf)
+    ms, cached = lfd.lfd_autotune_options(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+    assert not cached
+    assert opt.fft_size in (32, 64) and opt.contraction_cols in (16, 32, 64)
+    t0 = time.perf_counter()
+    opt2 = lfd.lfd_default_options(precision="bf16x3", variant="fft", max_frames=nf)
+    ms2, cached2 = lfd.lfd_autotune_options(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt2)
+    t_cached = time.perf_counter() - t0
+    assert cached2 and (opt2.fft_size, opt2.contraction_cols) == (opt.fft_size, opt.contraction_cols)
+    assert ms2 == ms and t_cached < 1.0
+    direct = {}
+    for F, cols in ((32, 16), (32, 32), (32, 64), (64, 16)):
+        o = lfd.lfd_default_options(precision="bf16x3", variant="fft", max_frames=nf, fft_size=F,
+                                    contraction_cols=cols)
+        ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, o)
+        try:
+            v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+            lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, 1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, 3)
+            b.record()
+            torch.cuda.synchronize()
+            direct[(F, cols)] = a.elapsed_time(b) / 3
+        finally:
+            lfd.lfd_destroy(ctx)
+    print("autotune_options: F=%d, %d columns at %.2f ms/iteration; timed directly %s"
+          % (opt.fft_size, opt.contraction_cols, ms, direct))
+    assert ms <= 1.15 * min(direct.values())
+    ctx = lfd.lfd_create(psf_d, g.P, g.nnum, g.nz, g.H, g.W, opt)
+    try:
+        assert lfd.lfd_get_fft_plan(ctx)["F"] == opt.fft_size
+        v = torch.ones((nf, g.nz, g.H, g.W), device=dev)
+        done, pred, ent, _ = lfd.lfd_rl_iterate_batch(ctx, nf, ys, v, int(d["n_iter"]))
+        vox = d["sample_vox"]
+        v0 = v[0].cpu().numpy()
+        e = rel_l2(v0[vox[:, 0], vox[:, 1], vox[:, 2]], d["v_last"])
+        assert e <= TOL_RL["bf16x3"]
+        assert pred[0] == int(d["predicted"])
+    finally:
+        lfd.lfd_destroy(ctx)
