@@ -299,21 +299,16 @@ def fft_plan_numbers(g, plan):
 
 # DRAM bytes (read + write) per launch from one ncu capture, by (workload,
 # precision, kernel); each entry names its summary under profiles/ and is
-# removed when that kernel changes.
+# removed when that kernel changes. The volume transforms' traffic grows in
+# proportion to the channels C, so their 4-depth capture is scaled by
+# 11475 / 900; the contractions' does not (the share of kept lo tiles and the
+# transformed volume's re-reads depend on the depths), so they have no entry.
 NCU_TRAFFIC = {
-    ("lf_large_2025px_51z_psf345", "bf16x3", "forward contraction"):
-        (41.024e9 + 0.188e9, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
-    ("lf_large_2025px_51z_psf345", "bf16x3", "backward contraction"):
-        (33.181e9 + 3.093e9, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
-        ((0.0789e9 + 0.1840e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        ((0.080609e9 + 0.180679e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
-        ((0.2466e9 + 0.0485e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        ((0.244429e9 + 0.043105e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
-
-
-# dense tensor rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s)
-TF32_OVER_BF16 = 1.1 / 2.25
 
 
 def direct_tensor_roofline(g, prec, st_ms):
@@ -374,6 +369,8 @@ def fft_roofline(g, plan, prec, stage, peaks, peak_src, fp32_peak, smax, spectra
             continue
         gbs = w["bytes"] / (ms / 1e3) / 1e9
         e = {"ms": ms, "algorithmic_bytes": w["bytes"], "GBps": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+        t = NCU_TRAFFIC.get((g.name, prec, w["kernel"]))
+        e["traffic"] = t[0] if t else None
         if "flops" in w:
             tf = w["flops"] / (ms / 1e3) / 1e12
             e["TFLOPs"] = tf
