@@ -311,6 +311,10 @@ NCU_TRAFFIC = {
 }
 
 
+# dense tensor rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
 def direct_tensor_roofline(g, prec, st_ms):
     """Tensor-pipe fraction of the direct (implicit GEMM) projections: the
     algorithmic flops 2*H*W*Nz*P^2 per projection, and the executed ones (the

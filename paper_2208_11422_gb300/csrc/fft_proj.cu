@@ -890,37 +890,46 @@ __global__ void k_low_list(const float* __restrict__ x, int64_t n, const unsigne
 // ------------------------------------------------ layout and update kernels --
 // Stack-order planes <-> channel-major polyphase planes:
 //   img[z][Iy*N+ty][Ix*N+tx]  <->  cm[z*S + ty*N + tx][Iy][Ix]
-// (a volume has Nz planes, an image one). One block per (image row, plane):
-// the row goes through shared memory, so both the image row and the N
-// channel rows it feeds are read / written contiguously (the shared-memory
-// stride N is odd, so the accesses are free of bank conflicts).
-__global__ void k_to_cm(const float* __restrict__ img, Geo g, float* __restrict__ cm) {
-    extern __shared__ float row[];
-    const int y = blockIdx.x, z = blockIdx.y;
-    const int Iy = y / g.N, ty = y % g.N;
-    const float* src = img + ((int64_t)z * g.H + y) * g.W;
-    for (int x = threadIdx.x; x < g.W; x += blockDim.x) row[x] = src[x];
+// (a volume has Nz planes, an image one). One block per tile of kCmTile
+// lenslets of one lenslet row of one plane: the tile's N image rows go
+// through shared memory, so the image side is read / written in whole row
+// segments and every channel's segment (kCmTile lenslets, 128 bytes) in one
+// run (the shared-memory stride N is odd, so the channel reads are free of
+// bank conflicts). Grid: x = lenslet tile, y = lenslet row, z = plane.
+constexpr int kCmTile = 32;
+__global__ void __launch_bounds__(256) k_to_cm(const float* __restrict__ img, Geo g, float* __restrict__ cm) {
+    extern __shared__ float tile[];  // [N][kCmTile * N]
+    const int Ix0 = blockIdx.x * kCmTile, Iy = blockIdx.y, z = blockIdx.z;
+    const int nl = min(kCmTile, g.Lx - Ix0), wpx = nl * g.N, ld = kCmTile * g.N;
+    const float* src = img + ((int64_t)z * g.H + (int64_t)Iy * g.N) * g.W + (int64_t)Ix0 * g.N;
+    for (int e = threadIdx.x; e < g.N * wpx; e += blockDim.x) {
+        const int ty = e / wpx, xx = e % wpx;
+        tile[ty * ld + xx] = src[(int64_t)ty * g.W + xx];
+    }
     __syncthreads();
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
-    float* dst = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
-    for (int k = threadIdx.x; k < g.W; k += blockDim.x) {
-        const int tx = k / g.Lx, Ix = k % g.Lx;
-        dst[tx * L2 + Ix] = row[Ix * g.N + tx];
+    float* dst = cm + (int64_t)z * g.S * L2 + (int64_t)Iy * g.Lx + Ix0;
+    for (int e = threadIdx.x; e < g.S * nl; e += blockDim.x) {
+        const int t = e / nl, i = e % nl, ty = t / g.N, tx = t % g.N;
+        dst[t * L2 + i] = tile[ty * ld + i * g.N + tx];
     }
 }
-__global__ void k_from_cm(const float* __restrict__ cm, Geo g, float* __restrict__ img) {
-    extern __shared__ float row[];
-    const int y = blockIdx.x, z = blockIdx.y;
-    const int Iy = y / g.N, ty = y % g.N;
+__global__ void __launch_bounds__(256) k_from_cm(const float* __restrict__ cm, Geo g, float* __restrict__ img) {
+    extern __shared__ float tile[];  // [N][kCmTile * N]
+    const int Ix0 = blockIdx.x * kCmTile, Iy = blockIdx.y, z = blockIdx.z;
+    const int nl = min(kCmTile, g.Lx - Ix0), wpx = nl * g.N, ld = kCmTile * g.N;
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
-    const float* src = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
-    for (int k = threadIdx.x; k < g.W; k += blockDim.x) {
-        const int tx = k / g.Lx, Ix = k % g.Lx;
-        row[Ix * g.N + tx] = src[tx * L2 + Ix];
+    const float* src = cm + (int64_t)z * g.S * L2 + (int64_t)Iy * g.Lx + Ix0;
+    for (int e = threadIdx.x; e < g.S * nl; e += blockDim.x) {
+        const int t = e / nl, i = e % nl, ty = t / g.N, tx = t % g.N;
+        tile[ty * ld + i * g.N + tx] = src[t * L2 + i];
     }
     __syncthreads();
-    float* dst = img + ((int64_t)z * g.H + y) * g.W;
-    for (int x = threadIdx.x; x < g.W; x += blockDim.x) dst[x] = row[x];
+    float* dst = img + ((int64_t)z * g.H + (int64_t)Iy * g.N) * g.W + (int64_t)Ix0 * g.N;
+    for (int e = threadIdx.x; e < g.N * wpx; e += blockDim.x) {
+        const int ty = e / wpx, xx = e % wpx;
+        dst[(int64_t)ty * g.W + xx] = tile[ty * ld + xx];
+    }
 }
 __global__ void k_fill_cm(float* __restrict__ p, int64_t n, float val) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -1179,13 +1188,8 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
 }
 
 static cudaError_t cm_copy(bool to, const float* src, const Geo& g, int planes, float* dst, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)g.W;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(to ? k_to_cm : k_from_cm,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((unsigned)g.H, (unsigned)planes);
+    const size_t smem = sizeof(float) * (size_t)g.N * kCmTile * g.N;  // at most 28.8 KB (Nnum 15)
+    dim3 grid((unsigned)((g.Lx + kCmTile - 1) / kCmTile), (unsigned)g.Ly, (unsigned)planes);
     if (to)
         k_to_cm<<<grid, 256, smem, st>>>(src, g, dst);
     else
