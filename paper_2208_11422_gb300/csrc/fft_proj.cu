@@ -40,9 +40,14 @@ struct FftSize {
     static constexpr int HF = F / 2;           // points of each lane's 1-D transform (F/2)
     static constexpr int H2 = F / 2 + 1;       // half-spectrum columns
     static constexpr int BINS = F * H2;
-    static constexpr int THREADS = 512;        // per transform block
-    static constexpr int R2C_CH = THREADS / F; // channels per block: F lanes each
+    // per transform block: at F = 64, 4 channels in 256 threads and two
+    // blocks per SM (each 68 KB of half spectra), so that one block's loads
+    // overlap the other's transforms; at F = 32, 16 channels in 512 threads
+    static constexpr int THREADS = F == 64 ? 256 : 512;
+    static constexpr int MINB = 512 / THREADS;  // blocks per SM (launch bounds)
+    static constexpr int R2C_CH = THREADS / F;  // channels per block: F lanes each
     static constexpr int C2R_CH = THREADS / F;
+    static constexpr int GCH = R2C_CH < 8 ? R2C_CH : 8;  // channels per output / input group item
 };
 
 __device__ __forceinline__ int brev_c(int i, int log) {
@@ -101,7 +106,19 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[N]) {
 template <int F>
 __device__ __forceinline__ void chan_sync(int ch) {
     if constexpr (F >= 64) {
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + ch), "r"(F) : "memory");
+        // immediate barrier ids (one per channel of the block), so that the
+        // block holds only the barriers it uses
+        static_assert(FftSize<F>::THREADS / F <= 8, "one named barrier per channel");
+        switch (ch) {
+            case 0: asm volatile("bar.sync 1, %0;" ::"n"(F) : "memory"); break;
+            case 1: asm volatile("bar.sync 2, %0;" ::"n"(F) : "memory"); break;
+            case 2: asm volatile("bar.sync 3, %0;" ::"n"(F) : "memory"); break;
+            case 3: asm volatile("bar.sync 4, %0;" ::"n"(F) : "memory"); break;
+            case 4: asm volatile("bar.sync 5, %0;" ::"n"(F) : "memory"); break;
+            case 5: asm volatile("bar.sync 6, %0;" ::"n"(F) : "memory"); break;
+            case 6: asm volatile("bar.sync 7, %0;" ::"n"(F) : "memory"); break;
+            default: asm volatile("bar.sync 8, %0;" ::"n"(F) : "memory"); break;
+        }
     } else {
         __syncwarp();
     }
@@ -216,9 +233,29 @@ __device__ __forceinline__ void split8(const float2 (&v)[8], uint32_t (&h)[4][4]
     }
 }
 
+__device__ __forceinline__ void split4(const float2 (&v)[4], uint32_t (&h)[4][2]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float2 a = v[2 * k], b = v[2 * k + 1];
+        const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+        const float2 rb = __bfloat1622float2(rh), ib = __bfloat1622float2(ih);
+        const __nv_bfloat162 rl = __floats2bfloat162_rn(a.x - rb.x, b.x - rb.y);
+        const __nv_bfloat162 il = __floats2bfloat162_rn(a.y - ib.x, b.y - ib.y);
+        h[0][k] = *reinterpret_cast<const uint32_t*>(&rh);
+        h[1][k] = *reinterpret_cast<const uint32_t*>(&rl);
+        h[2][k] = *reinterpret_cast<const uint32_t*>(&ih);
+        h[3][k] = *reinterpret_cast<const uint32_t*>(&il);
+    }
+}
+
 struct OutC64 {
     float2* p;
     int ntile, ld;
+    __device__ void put4(int bin, int tile, int c0, const float2 (&v)[4]) const {
+        float4* q = reinterpret_cast<float4*>(p + ((int64_t)bin * ntile + tile) * ld + c0);
+        q[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        q[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    }
     __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
         float4* q = reinterpret_cast<float4*>(p + ((int64_t)bin * ntile + tile) * ld + c0);
         const int n4 = ld - c0 >= 8 ? 4 : 2;
@@ -231,6 +268,14 @@ struct OutC64 {
 struct OutPlanes {
     __nv_bfloat16* p[4];
     int ntile, ld;
+    __device__ void put4(int bin, int tile, int c0, const float2 (&v)[4]) const {
+        const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
+        uint32_t h[4][2];
+        split4(v, h);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (p[q]) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
+    }
     __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
         const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
         uint32_t h[4][4];
@@ -255,6 +300,13 @@ struct OutPlanes {
 struct OutPlanesG {
     __nv_bfloat16* p[4];
     int ncolp, bins;  // columns per group, bins per column
+    __device__ void put4(int bin, int col, int c0, const float2 (&v)[4]) const {
+        const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8 + (c0 & 7);
+        uint32_t h[4][2];
+        split4(v, h);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
+    }
     __device__ void put8(int bin, int col, int c0, const float2 (&v)[8]) const {
         const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8;
         uint32_t h[4][4];
@@ -293,7 +345,7 @@ struct OutPlanesG {
 // Grid: x = channel group (fastest, so blocks running together fill adjacent
 // parts of the same output rows), y = column.
 template <int F, class Src, class Out>
-__global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
+__global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_r2c(Src src, int nch, int ldc, Out out) {
     using Z = FftSize<F>;
     constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH, PS = HF + 1;
     extern __shared__ float2 sm[];
@@ -373,14 +425,16 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_r2c(Src src, int
         for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
     }
     __syncthreads();  // the output loop reads every channel of the block
-    // every bin of 8 consecutive channels at a time
-    for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
+    // every bin of GCH (8, or the block's 4) consecutive channels at a time
+    constexpr int GCH = Z::GCH;
+    for (int e = threadIdx.x; e < Z::BINS * (CH / GCH); e += blockDim.x) {
         const int bin = e % Z::BINS, g = e / Z::BINS;
-        if (c0 + 8 * g >= ldc) continue;
-        float2 v[8];
+        if (c0 + GCH * g >= ldc) continue;
+        float2 v[GCH];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = sm[(size_t)(8 * g + k) * Z::BINS + bin];
-        out.put8(bin, tile, c0 + 8 * g, v);
+        for (int k = 0; k < GCH; ++k) v[k] = sm[(size_t)(GCH * g + k) * Z::BINS + bin];
+        if constexpr (GCH == 8) out.put8(bin, tile, c0 + 8 * g, v);
+        else out.put4(bin, tile, c0 + 4 * g, v);
     }
 }
 
@@ -519,7 +573,7 @@ struct TabVolDst {
 // contraction), else [BINS][ntile][ldc] (CUDA-core contraction).
 // Grid: x = column, y = channel group.
 template <int F, class Dst, bool GM>
-__global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2* __restrict__ in, int nch,
+__global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_c2r(const float2* __restrict__ in, int nch,
                                                                   int ldc, int ntile, int off, int B,
                                                                   float scale, Dst dst) {
     using Z = FftSize<F>;
@@ -529,25 +583,27 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2
     const int h = q / HF, l = q % HF;
     const int tile = blockIdx.x, c0 = blockIdx.y * CH, c = c0 + ch;
     const auto view = dst.bind(tile);
-    // spectra of 8 consecutive channels per bin (one thread reads them with
-    // 16-byte loads) for the bins (fy, fx) and (fy + F/2, fx), stored into
-    // [channel][bin] as the column transform's inputs: their sum in row fy and
-    // their difference times exp(2 pi i fy / F) in row fy + F/2
-    static_assert(CH % 8 == 0, "whole channel groups per block");
-    for (int e = threadIdx.x; e < HF * H2 * (CH / 8); e += blockDim.x) {
-        const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + 8 * g;
+    // spectra of GCH (8, or the block's 4) consecutive channels per bin (one
+    // thread reads them with 16-byte loads) for the bins (fy, fx) and
+    // (fy + F/2, fx), stored into [channel][bin] as the column transform's
+    // inputs: their sum in row fy and their difference times exp(2 pi i fy / F)
+    // in row fy + F/2
+    constexpr int GCH = Z::GCH;
+    static_assert(CH % GCH == 0 && 8 % GCH == 0, "whole channel groups per block");
+    for (int e = threadIdx.x; e < HF * H2 * (CH / GCH); e += blockDim.x) {
+        const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + GCH * g;
         const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
-        float2 v0[8], v1[8];
+        float2 v0[GCH], v1[GCH];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v0[k] = v1[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < GCH; ++k) v0[k] = v1[k] = make_float2(0.f, 0.f);
         if (cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
-            const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8
+            const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
                                     : in + (int64_t)tile * ldc + cg;
             const int64_t bstride = GM ? 8 : (int64_t)ntile * ldc;  // float2 between bins
             const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
             const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < GCH / 2; ++k) {
                 const float4 w0 = q0[k], w1 = q1[k];
                 v0[2 * k] = make_float2(w0.x, w0.y);
                 v0[2 * k + 1] = make_float2(w0.z, w0.w);
@@ -557,8 +613,8 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, 1) k_fft_c2r(const float2
         }
         const float2 w = c_tw[fy * (64 / F)];  // conjugated below
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            float2* dst = sm + (size_t)(8 * g + k) * Z::BINS;
+        for (int k = 0; k < GCH; ++k) {
+            float2* dst = sm + (size_t)(GCH * g + k) * Z::BINS;
             dst[b0] = cadd(v0[k], v1[k]);
             const float2 d = csub(v0[k], v1[k]);
             dst[b1] = make_float2(fmaf(d.x, w.x, d.y * w.y), fmaf(d.y, w.x, -d.x * w.y));

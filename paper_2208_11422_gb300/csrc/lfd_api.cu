@@ -221,6 +221,11 @@ void free_all(lfd_ctx* ctx) {
         delete ctx->lo;
         ctx->lo = nullptr;
     }
+    if (ctx->wide) {
+        cgemm_free_wide(ctx->wide);
+        delete ctx->wide;
+        ctx->wide = nullptr;
+    }
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
     if (ctx->host_pinned_slots) cudaFreeHost(ctx->host_pinned_slots);
@@ -532,6 +537,14 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
                 cb.lo = *ctx->lo;
                 ctx->spectra_bytes = plane_bytes * 2 + 2 * (ctx->lo->kept + 1) * (int64_t)g.S * 64 *
                                                            (int64_t)sizeof(__nv_bfloat16);
+                if (ctx->mf == 1 && fplan.ntile <= 16 && g.S <= 256) {
+                    // single frames: the forward's wide units read their own copy
+                    // of the spectra (the same bytes per projection)
+                    ctx->wide = new (std::nothrow) WidePlanes();
+                    if (!ctx->wide) return bail(LFD_ENOMEM);
+                    CREATE_CK(cgemm_build_wide(cb, *ctx->lo, st, ctx->wide, &ctx->device_bytes));
+                    cb.wide = *ctx->wide;
+                }
             }
             std::string why2;
             cudaError_t ce = cgemm_init(cb, ctx->sm_count, &ctx->cg, &why2);

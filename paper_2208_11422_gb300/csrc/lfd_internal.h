@@ -77,6 +77,7 @@ struct StageTimes {
 
 struct ExactPlan;  // exact.h
 struct LoPlanes;   // tc_cgemm.h
+struct WidePlanes; // tc_cgemm.h
 
 }  // namespace lfd
 
@@ -155,6 +156,7 @@ struct lfd_ctx {
     float* rimg = nullptr;       // ratio image [H][W] (FFT variant)
     lfd::ExactPlan* exact = nullptr;  // voxels backprojected exactly (FFT variant)
     lfd::LoPlanes* lo = nullptr;      // adaptive lo planes of the PSF spectra (split BF16)
+    lfd::WidePlanes* wide = nullptr;  // the forward's wide-unit copy of the adaptive spectra
     int64_t spectra_bytes = 0;        // PSF spectra planes the contractions stream
     int64_t n_low = 0;
     // depth split (lfd_split_*): iterate buffer holding the current iterate

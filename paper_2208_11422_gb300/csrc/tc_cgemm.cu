@@ -348,6 +348,280 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                      "r"(kTmemCols));
 }
 
+// Wide forward units (adaptive lo planes, single chunks of up to 16 columns,
+// S <= 256). A unit is (bin pair p = bins 2p and 2p + 1, chunk q) and covers
+// both row tiles of both bins, so each 32-byte sector of the data planes (8
+// channels of two neighbouring bins) is fetched by one unit only, and the data
+// of a k-block feeds all four (bin, row tile) accumulator pairs. A k-block is
+// 16 channels (one MMA K step). A stage holds per bin the (bin, k-block) group
+// of the wide PSF copy, hi and (where the bin's 64-channel block keeps it) lo,
+// each one bulk copy of 64 S bytes laid out [row tile][plane][group][rows][8],
+// and the bin's four data planes side by side as the N = 64 columns of one B
+// operand, [group][plane][column][8] (TMA boxes of one channel group). Each
+// PSF part then takes two MMAs per (bin, row tile):
+//   P += Wr [Xr_hi | Xr_lo | Xi_hi | Xi_lo],   Q += Wi [Xr_hi | Xr_lo | Xi_hi | Xi_lo]
+// (Wr, Wi the hi part, and the lo part where kept), and the epilogue forms
+//   re = P[0:16] + P[16:32] - Q[32:48] - Q[48:64],
+//   im = P[32:48] + P[48:64] + Q[0:16] + Q[16:32].
+// (The lo x lo products of kept tiles are included.) The A descriptors of row
+// tile m step over its rows_m rows per channel group; an MMA reads 128 rows,
+// and the rows past rows_m (beyond the tile's phases, read from the next piece
+// or the group's spare bytes) only reach output rows that are not written.
+constexpr int kWideThreads = 192;
+constexpr int kWideGroup = 16384;  // bytes reserved per (bin, hi / lo) group: 64 x 256
+constexpr int kWideB = 2048;       // B of one bin: 2 groups x 4 planes x 16 columns x 16 B
+constexpr int kWideStage = 4 * kWideGroup + 2 * kWideB;  // 68 KB
+constexpr int kWideStages = 3;
+constexpr int kWideSmem = kWideStages * kWideStage + 1024 + 256;
+constexpr int kWideChain = 256;       // k-blocks per accumulation chain
+constexpr uint32_t kWideTmem = 512;   // 4 (bin, row tile) x (P, Q) x 64 columns, one buffer
+static_assert(kWideSmem <= 232448, "wide stage ring exceeds the shared memory of a block");
+
+struct WideArgs {
+    int npairs;         // bin pairs (bins / 2)
+    int nchunk;         // chunks of 16 columns
+    int ncol;           // output columns of this launch
+    int nkb;            // k-blocks of 16 channels per bin
+    int S;              // phases (output rows), <= 256
+    int mtiles;         // row tiles of 128 (1 or 2)
+    int nbins;
+    int nkbc;           // 64-channel blocks per bin (lo slot table row length)
+    const uint8_t* hi;  // wide hi groups: 64 S bytes per (bin, k-block)
+    const uint8_t* lo;  // wide lo groups: 64 S bytes per (slot, k-block of the slot)
+    const int* lo_slot; // [bins][nkbc], 0 = dropped
+    float2* out;        // [Sf/8][ncol][bins][8] (group-major)
+    int* err;
+};
+
+__global__ void __launch_bounds__(kWideThreads, 1)
+k_tc_cgemm_wide(const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
+                const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
+                const WideArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t* smem = smem_raw + (sbase - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kWideStages * kWideStage);
+    uint64_t* empty = full + kWideStages;
+    uint64_t* acc_full = empty + kWideStages;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* mma_done = acc_empty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    volatile int* stage_lo = reinterpret_cast<volatile int*>(tmem_slot + 3);  // [kWideStages]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = a.npairs * a.nchunk;
+    const uint32_t grp = 64u * (uint32_t)a.S;  // bytes of one (bin, k-block) group
+    const int rows0 = a.S < 128 ? a.S : 128, rows1 = a.S - rows0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWideStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 128);
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        *consumed_ctr = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kWideTmem));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------- copy producer --
+            const CUtensorMap* B[4] = {&b0, &b1, &b2, &b3};
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            // the bins' lo slots of a 64-channel block, read one block ahead so
+            // that the table lookup overlaps the ring's waits
+            auto slots = [&](int u_, int blk, int& s0, int& s1) {
+                s0 = s1 = 0;
+                if (u_ >= n_units) return;
+                const int* ls = a.lo_slot + (int64_t)(2 * (u_ / a.nchunk)) * a.nkbc + blk;
+                s0 = ls[0];
+                s1 = ls[a.nkbc];
+            };
+            int nx0, nx1;
+            slots(blockIdx.x, 0, nx0, nx1);
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const int p = u / a.nchunk, q = u % a.nchunk;
+                int sl0 = 0, sl1 = 0;
+                for (int kb = 0; kb < a.nkb; ++kb) {
+                    if ((kb & 3) == 0) {
+                        sl0 = nx0;
+                        sl1 = nx1;
+                        if (kb + 4 < a.nkb) slots(u, (kb >> 2) + 1, nx0, nx1);
+                        else slots(u + gridDim.x, 0, nx0, nx1);
+                    }
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    stage_lo[stage] = (sl0 ? 1 : 0) | (sl1 ? 2 : 0);
+                    mbar_expect_tx(&full[stage], 2 * grp + (sl0 ? grp : 0u) + (sl1 ? grp : 0u) + 2 * kWideB);
+                    const uint32_t sA = sbase + stage * kWideStage, sB = sA + 4 * kWideGroup;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int bin = 2 * p + j, sl = j ? sl1 : sl0;
+                        bulk_g2s(sA + j * kWideGroup, a.hi + ((int64_t)bin * a.nkb + kb) * grp, grp, &full[stage]);
+                        if (sl)
+                            bulk_g2s(sA + (2 + j) * kWideGroup, a.lo + ((int64_t)sl * 4 + (kb & 3)) * grp, grp,
+                                     &full[stage]);
+#pragma unroll
+                        for (int g = 0; g < 2; ++g)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)  // 8 channels x 1 bin x 16 columns of one group
+                                tma_4d(sB + j * kWideB + g * 1024 + i * 256, B[i], 0, bin, q * 16, kb * 2 + g,
+                                       &full[stage]);
+                    }
+                    ++issued;
+                    if (++stage == kWideStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok)
+                for (int i = *consumed_ctr; i < issued; ++i)
+                    mbar_wait_drain(&full[i % kWideStages], (uint32_t)((i / kWideStages) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer --
+            const uint32_t id = idesc_bf16(128, 64, false, false, false);
+            int stage = 0, consumed = 0, ci = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                for (int c0 = 0; c0 < a.nkb && ok; c0 += kWideChain, ++ci) {
+                    const int c1 = min(a.nkb, c0 + kWideChain);
+                    if (ci >= 1 && !mbar_wait(acc_empty, (uint32_t)((ci - 1) & 1), abort_flag, a.err, 12)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = c0; kb < c1 && ok; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sA = sbase + stage * kWideStage, sB = sA + 4 * kWideGroup;
+                        const int lo = stage_lo[stage];
+                        const uint32_t acc0 = kb == c0 ? 0u : 1u;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            // B: 64 rows (plane x 16 + column) of 16 channels; groups 1 KB apart
+                            const uint64_t bd = sdesc_noswz(sB + j * kWideB, 1024, 128);
+                            const bool jlo = (lo >> j) & 1;
+                            for (int m = 0; m < a.mtiles; ++m) {
+                                const uint32_t rows = m ? rows1 : rows0, lbo = rows * 16;
+                                const uint32_t off = m ? 4u * rows0 * 16 : 0u;
+                                const uint32_t hA = sA + j * kWideGroup + off, lA = sA + (2 + j) * kWideGroup + off;
+                                const uint32_t dP = tmem + (j * 2 + m) * 128, dQ = dP + 64;
+                                umma_bf16(dP, sdesc_noswz(hA, lbo, 128), bd, id, acc0);
+                                umma_bf16(dQ, sdesc_noswz(hA + 2 * lbo, lbo, 128), bd, id, acc0);
+                                if (jlo) {
+                                    umma_bf16(dP, sdesc_noswz(lA, lbo, 128), bd, id, 1u);
+                                    umma_bf16(dQ, sdesc_noswz(lA + 2 * lbo, lbo, 128), bd, id, 1u);
+                                }
+                            }
+                        }
+                        umma_commit(&empty[stage]);
+                        *consumed_ctr = ++consumed;
+                        if (++stage == kWideStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (ok) umma_commit(acc_full);
+                }
+            }
+            umma_commit(mma_done);
+            mbar_wait_drain(mma_done, 0);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int lg = warp & 3;
+        const int row = lg * 32 + lane;
+        int ci = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int p = u / a.nchunk, q = u % a.nchunk, col0 = q * 16;
+            for (int c0 = 0; c0 < a.nkb; c0 += kWideChain, ++ci) {
+                if (!mbar_wait(acc_full, (uint32_t)(ci & 1), abort_flag, a.err, 14)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16);
+                for (int j = 0; j < 2; ++j) {
+                    for (int m = 0; m < a.mtiles; ++m) {
+                        const uint32_t tP = tb + (j * 2 + m) * 128, tQ = tP + 64;
+                        float re[16], im[16];
+                        {
+                            uint32_t x0[16], x1[16], x2[16], x3[16];
+                            tmem_ld16(tP, x0);
+                            tmem_ld16(tP + 16, x1);
+                            tmem_ld16(tQ + 32, x2);
+                            tmem_ld16(tQ + 48, x3);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                re[t] = (__uint_as_float(x0[t]) + __uint_as_float(x1[t])) -
+                                        (__uint_as_float(x2[t]) + __uint_as_float(x3[t]));
+                            tmem_ld16(tP + 32, x0);
+                            tmem_ld16(tP + 48, x1);
+                            tmem_ld16(tQ, x2);
+                            tmem_ld16(tQ + 16, x3);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                im[t] = (__uint_as_float(x0[t]) + __uint_as_float(x1[t])) +
+                                        (__uint_as_float(x2[t]) + __uint_as_float(x3[t]));
+                        }
+                        const int grow = m * 128 + row;
+                        if (grow < a.S) {
+                            float2* o = a.out + (((int64_t)(grow >> 3) * a.ncol + col0) * a.nbins + 2 * p + j) * 8 +
+                                        (grow & 7);
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                if (col0 + t < a.ncol) {
+                                    float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.nbins * 8);
+                                    if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(re[t], im[t]);
+                                    else red_add_v2(dst, re[t], im[t]);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(acc_empty);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWideTmem));
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -375,15 +649,15 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
 }
 
 // grouped column planes [groups][ncolp][bins][8]: the box 8 channels x 1 bin x
-// ncb columns x 8 groups lands densely (no swizzle) as [group][column][8], the
-// K-major core-matrix layout the B descriptor of the kernel describes
+// ncb columns x gbox groups lands densely (no swizzle) as [group][column][8],
+// the K-major core-matrix layout the B descriptors of the kernels describe
 bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp,
-                  uint32_t ncb) {
+                  uint32_t ncb, uint32_t gbox = 8) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[4] = {8, bins, ncolp, groups};
     const cuuint64_t str[3] = {16, 16 * bins, 16 * bins * ncolp};
-    const cuuint32_t box[4] = {8, 1, ncb, 8};
+    const cuuint32_t box[4] = {8, 1, ncb, gbox};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, str, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -396,7 +670,10 @@ constexpr int kNg[3] = {1, 2, 4};
 struct CgState {
     CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (see the modes)
     CUtensorMap fb[3][4], ab[3][4];  // per chunk width
+    CUtensorMap fw[4];               // data planes, boxes of one group (wide forward units)
     CgArgs fwd, adj;
+    WideArgs wide;
+    bool use_wide = false;
     int sm_count = 0, ncolp = 16, nwidths = 1;
     int mode = MODE_SPLIT;
     int* err = nullptr;
@@ -427,6 +704,15 @@ cudaError_t launch_mode(int ng, const CUtensorMap* A, const CUtensorMap* B, cons
 template <bool ADJ>
 cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     if (ncol < 1 || ncol > s->ncolp) return cudaErrorInvalidValue;
+    if (!ADJ && s->use_wide && ncol <= 16) {  // one chunk: the wide units stream the spectra once
+        WideArgs w = s->wide;
+        w.ncol = ncol;
+        w.nchunk = 1;
+        const int grid = std::min(w.npairs * w.nchunk, s->sm_count);
+        k_tc_cgemm_wide<<<grid, kWideThreads, kWideSmem, st>>>(s->fw[0], s->fw[1], s->fw[2], s->fw[3], w);
+        count_launch();
+        return cudaGetLastError();
+    }
     CgArgs a = ADJ ? s->adj : s->fwd;
     a.ncol = ncol;
     // the narrowest chunk that covers all columns, else the widest available
@@ -550,6 +836,79 @@ cudaError_t cgemm_compact_lo(const CgemmBuffers& b, float tau, cudaStream_t st, 
     return e;
 }
 
+namespace {
+
+// byte offset of piece (m, plane, g) inside a (bin, k-block) group of the
+// wide layout: tile 0's four pieces of rows0 rows, then tile 1's of rows1
+__host__ __device__ __forceinline__ int64_t wide_piece(int m, int plane, int g, int rows0, int rows1) {
+    return m == 0 ? (int64_t)(plane * 2 + g) * rows0 * 16
+                  : (int64_t)4 * rows0 * 16 + (int64_t)(plane * 2 + g) * rows1 * 16;
+}
+
+// one block per (bin, k-block): 16-byte pieces of the hi planes
+__global__ void k_wide_hi(const __nv_bfloat16* __restrict__ re, const __nv_bfloat16* __restrict__ im, int S,
+                          int Cw, int nkb16, __nv_bfloat16* __restrict__ dst) {
+    const int bin = blockIdx.x / nkb16, kb = blockIdx.x % nkb16;
+    const int rows0 = S < 128 ? S : 128, rows1 = S - rows0;
+    uint8_t* d = reinterpret_cast<uint8_t*>(dst) + (int64_t)blockIdx.x * 64 * S;
+    for (int e = threadIdx.x; e < 4 * S; e += blockDim.x) {
+        const int s = e % S, pg = e / S, plane = pg >> 1, g = pg & 1;
+        const int m = s >> 7, r = s & 127, c = kb * 16 + g * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (c < Cw) v = *reinterpret_cast<const uint4*>((plane ? im : re) + ((int64_t)bin * S + s) * Cw + c);
+        *reinterpret_cast<uint4*>(d + wide_piece(m, plane, g, rows0, rows1) + (int64_t)r * 16) = v;
+    }
+}
+
+// one block per (slot, k-block of the slot's 64 channels): the compact lo planes
+__global__ void k_wide_lo(const __nv_bfloat16* __restrict__ re, const __nv_bfloat16* __restrict__ im, int S,
+                          __nv_bfloat16* __restrict__ dst) {
+    const int slot = 1 + blockIdx.x / 4, q = blockIdx.x % 4;
+    const int rows0 = S < 128 ? S : 128, rows1 = S - rows0;
+    uint8_t* d = reinterpret_cast<uint8_t*>(dst) + ((int64_t)slot * 4 + q) * 64 * S;
+    for (int e = threadIdx.x; e < 4 * S; e += blockDim.x) {
+        const int s = e % S, pg = e / S, plane = pg >> 1, g = pg & 1;
+        const int m = s >> 7, r = s & 127, c = q * 16 + g * 8;
+        const uint4 v = *reinterpret_cast<const uint4*>((plane ? im : re) + ((int64_t)slot * S + s) * 64 + c);
+        *reinterpret_cast<uint4*>(d + wide_piece(m, plane, g, rows0, rows1) + (int64_t)r * 16) = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t cgemm_build_wide(const CgemmBuffers& b, const LoPlanes& lo, cudaStream_t st, WidePlanes* out,
+                             int64_t* bytes) {
+    *out = WidePlanes{};
+    if (b.S > 256 || !b.W[0] || !b.W[2] || !lo.slot || !lo.lo[0] || !lo.lo[1]) return cudaErrorInvalidValue;
+    const int nkb16 = (b.Cw + 15) / 16;
+    const size_t hi_bytes = (size_t)b.bins * nkb16 * 64 * b.S;
+    const size_t lo_bytes = (size_t)(lo.kept + 1) * 4 * 64 * b.S;
+    cudaError_t e = injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc((void**)&out->hi, hi_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&out->lo, lo_bytes);
+    if (e != cudaSuccess) {
+        cgemm_free_wide(out);
+        return e;
+    }
+    *bytes += (int64_t)(hi_bytes + lo_bytes);
+    out->nkb16 = nkb16;
+    k_wide_hi<<<(unsigned)((int64_t)b.bins * nkb16), 256, 0, st>>>(b.W[0], b.W[2], b.S, b.Cw, nkb16, out->hi);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && lo.kept > 0) {
+        k_wide_lo<<<(unsigned)(lo.kept * 4), 256, 0, st>>>(lo.lo[0], lo.lo[1], b.S, out->lo);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+void cgemm_free_wide(WidePlanes* p) {
+    if (p->hi) cudaFree(p->hi);
+    if (p->lo) cudaFree(p->lo);
+    *p = WidePlanes{};
+}
+
 void cgemm_free_lo(LoPlanes* p) {
     if (p->slot) cudaFree(p->slot);
     if (p->lo[0]) cudaFree(p->lo[0]);
@@ -610,6 +969,31 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.out = b.Xout;
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
+    if (s->mode == MODE_ADAPTIVE && b.wide.hi && b.S <= 256 && b.bins % 2 == 0) {
+        bool ok = true;
+        for (int i = 0; i < 4 && ok; ++i) ok = map4_grouped(&s->fw[i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16, 1);
+        if (!ok) {
+            if (why) *why = "cuTensorMapEncodeTiled failed for the wide units' data planes";
+            return cudaErrorInvalidValue;
+        }
+        WideArgs& w = s->wide;
+        w.npairs = b.bins / 2;
+        w.nchunk = 1;
+        w.ncol = 16;
+        w.nkb = b.wide.nkb16;
+        w.S = b.S;
+        w.mtiles = (b.S + 127) / 128;
+        w.nbins = b.bins;
+        w.nkbc = b.lo.nkbc;
+        w.hi = reinterpret_cast<const uint8_t*>(b.wide.hi);
+        w.lo = reinterpret_cast<const uint8_t*>(b.wide.lo);
+        w.lo_slot = b.lo.slot;
+        w.out = b.Yout;
+        w.err = s->err;
+        cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
+        if (e != cudaSuccess) return e;
+        s->use_wide = true;
+    }
     switch (s->mode) {
         case MODE_BF16: return set_smem<MODE_BF16>();
         case MODE_ADAPTIVE: return set_smem<MODE_ADAPTIVE>();

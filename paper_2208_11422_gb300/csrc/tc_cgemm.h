@@ -17,6 +17,21 @@ struct LoPlanes {
     int64_t kept = 0, tiles = 0;
 };
 
+// The forward's copy of the adaptive PSF spectra in the order its wide units
+// read them (cgemm_build_wide): per bin and k-block of 16 channels, for row
+// tile m (rows [128 m, 128 m + rows_m) of the S phases), plane (real, imag)
+// and channel group g (8 channels), the rows_m x 16 bytes of the canonical
+// K-major core-matrix layout [g][row][8], valid rows only:
+//   hi[bin][kb16][m][plane][g][rows_m][8]   (64 S bytes per bin and k-block)
+//   lo[slot][kb16 % 4][m][plane][g][rows_m][8] for the slots of LoPlanes
+// (a 64-channel block is four k-blocks). One unit of the wide forward kernel
+// covers both bins of a 32-byte sector of the data planes and both row tiles.
+struct WidePlanes {
+    __nv_bfloat16* hi = nullptr;
+    __nv_bfloat16* lo = nullptr;
+    int nkb16 = 0;              // k-blocks of 16 channels per bin
+};
+
 // Operands are BF16 planes: [0] real hi, [1] real lo, [2] imag hi, [3] imag lo.
 // The PSF spectra: all four planes (split BF16), the two hi planes (W[1], W[3]
 // null: BF16 spectra), or the two hi planes and lo.slot != null (adaptive).
@@ -33,6 +48,7 @@ struct CgemmBuffers {
     float2* Xout;             // [Cf/8][ncol][bins][8] adjoint output (group-major)
     LoPlanes lo;              // adaptive lo planes (slot null otherwise)
     int max_cols;             // widest column chunk (16, 32 or 64); 0: up to 64
+    WidePlanes wide;          // the forward's wide-unit copy (hi null: not used)
 };
 
 // Builds the adaptive lo planes from the full planes b.W[0..3] ([bins][S][Cw]);
@@ -40,6 +56,13 @@ struct CgemmBuffers {
 // are added to *bytes.
 cudaError_t cgemm_compact_lo(const CgemmBuffers& b, float tau, cudaStream_t st, LoPlanes* out, int64_t* bytes);
 void cgemm_free_lo(LoPlanes* p);
+
+// Builds the wide-unit copy of the adaptive spectra from the hi planes b.W[0],
+// b.W[2] ([bins][S][Cw]) and the compact lo planes `lo`; S <= 256. Device
+// bytes allocated are added to *bytes.
+cudaError_t cgemm_build_wide(const CgemmBuffers& b, const LoPlanes& lo, cudaStream_t st, WidePlanes* out,
+                             int64_t* bytes);
+void cgemm_free_wide(WidePlanes* p);
 
 cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::string* why);
 // ncol = frames x tiles of this call (<= ncolp)
