@@ -292,23 +292,26 @@ struct OutPlanes {
     }
 };
 // The transformed volume / ratio for the tensor-core contraction, in groups of
-// 8 channels: plane[q][g][col][bin][8] (g = channel / 8). One transform block
-// writes, per plane, all bins of its 8 channels of one column as one
-// contiguous run; the contraction's TMA box (8 channels x 1 bin x 16 columns
-// x 8 groups) lands in shared memory as [group][column][8 channels], the
-// canonical K-major layout without swizzle (8 x 16-byte core matrices).
+// 8 channels with the four planes of a group side by side:
+// [g][plane q][col][bin][8] (g = channel / 8; p[q] points at plane q of group
+// 0, groups are 4 ncolp bins x 8 values apart). One transform block writes,
+// per plane, all bins of its channels of one column as one contiguous run;
+// the contraction's TMA box (8 channels x 1 bin x n columns x 4 planes of
+// each of its groups) lands in shared memory as [group][plane][column][8
+// channels]: the canonical K-major layout without swizzle (8 x 16-byte core
+// matrices) of one B operand whose N = 4n rows are the planes' columns.
 struct OutPlanesG {
     __nv_bfloat16* p[4];
     int ncolp, bins;  // columns per group, bins per column
     __device__ void put4(int bin, int col, int c0, const float2 (&v)[4]) const {
-        const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8 + (c0 & 7);
+        const int64_t o = (((int64_t)(c0 >> 3) * 4 * ncolp + col) * bins + bin) * 8 + (c0 & 7);
         uint32_t h[4][2];
         split4(v, h);
 #pragma unroll
         for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
     }
     __device__ void put8(int bin, int col, int c0, const float2 (&v)[8]) const {
-        const int64_t o = (((int64_t)(c0 >> 3) * ncolp + col) * bins + bin) * 8;
+        const int64_t o = (((int64_t)(c0 >> 3) * 4 * ncolp + col) * bins + bin) * 8;
         uint32_t h[4][4];
         split8(v, h);
 #pragma unroll

@@ -17,9 +17,10 @@ struct FftPlan {
 
 // Spectra buffers. FP32 contraction: Wf, Xh, Yh (complex64). Tensor-core
 // contraction (cg != null): BF16 planes (real hi, real lo, imag hi, imag lo)
-// Wp[4] [bins][S][Cw] (PSF), Xp[4] [Cw/8][ncolp][bins][8] (volume columns) and
-// Yp[4] [Sw/8][ncolp][bins][8] (ratio columns) as inputs, and Yh / Xh as the
-// contractions' complex64 outputs.
+// Wp[4] [bins][S][Cw] (PSF); the volume and ratio columns in one block each,
+// [Cw/8][4 planes][ncolp][bins][8] and [Sw/8][4 planes][ncolp][bins][8], with
+// Xp[q] / Yp[q] pointing at plane q of group 0 (only Xp[0] / Yp[0] are
+// allocations); and Yh / Xh as the contractions' complex64 outputs.
 struct FftBuffers {
     float2* Wf = nullptr;
     float2* Xh = nullptr;

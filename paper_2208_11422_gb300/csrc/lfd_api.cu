@@ -210,8 +210,7 @@ void free_all(lfd_ctx* ctx) {
                     ctx->coef, ctx->flux_part, ctx->hist, ctx->stage_vol, ctx->stage_img,
                     ctx->Wf, ctx->Xh, ctx->Yh, ctx->Vcm[0], ctx->Vcm[1], ctx->Rcm, ctx->Xcm,
                     ctx->invcm, ctx->ycm, ctx->psf_dev, ctx->rimg,
-                    ctx->Wp[0], ctx->Wp[1], ctx->Wp[2], ctx->Wp[3], ctx->Xp[0], ctx->Xp[1],
-                    ctx->Xp[2], ctx->Xp[3], ctx->Yp[0], ctx->Yp[1], ctx->Yp[2], ctx->Yp[3]};
+                    ctx->Wp[0], ctx->Wp[1], ctx->Wp[2], ctx->Wp[3], ctx->Xp[0], ctx->Yp[0]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     exact_plan_destroy(ctx->exact);
@@ -414,11 +413,15 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     if (fft) {
         const int ncol = mf * fplan.ntile, ncolp = (ncol + 15) / 16 * 16;
         if (fft_products(ctx)) {
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 4; ++i)
                 if (fft_products(ctx) == 3 || i % 2 == 0)  // BF16 spectra: hi planes only
                     CREATE_TRY(dalloc(ctx, &ctx->Wp[i], (int64_t)fplan.bins * g.S * fplan.Cw, false));
-                CREATE_TRY(dalloc(ctx, &ctx->Xp[i], (int64_t)fplan.bins * ncolp * fplan.Cw, true));
-                CREATE_TRY(dalloc(ctx, &ctx->Yp[i], (int64_t)fplan.bins * ncolp * fplan.Sw, true));
+            // the four data planes of each 8-channel group side by side (one block)
+            CREATE_TRY(dalloc(ctx, &ctx->Xp[0], 4 * (int64_t)fplan.bins * ncolp * fplan.Cw, true));
+            CREATE_TRY(dalloc(ctx, &ctx->Yp[0], 4 * (int64_t)fplan.bins * ncolp * fplan.Sw, true));
+            for (int i = 1; i < 4; ++i) {
+                ctx->Xp[i] = ctx->Xp[0] + (int64_t)i * ncolp * fplan.bins * 8;
+                ctx->Yp[i] = ctx->Yp[0] + (int64_t)i * ncolp * fplan.bins * 8;
             }
         } else {
             CREATE_TRY(dalloc(ctx, &ctx->Wf, (int64_t)fplan.bins * g.S * fplan.Cf, false));
@@ -514,11 +517,9 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
             cb.Cw = fplan.Cw;
             cb.Sf = fplan.Sf;
             cb.Cf = fplan.Cf;
-            for (int i = 0; i < 4; ++i) {
-                cb.W[i] = ctx->Wp[i];
-                cb.X[i] = ctx->Xp[i];
-                cb.Y[i] = ctx->Yp[i];
-            }
+            for (int i = 0; i < 4; ++i) cb.W[i] = ctx->Wp[i];
+            cb.X = ctx->Xp[0];
+            cb.Y = ctx->Yp[0];
             cb.Yout = ctx->Yh;
             cb.Xout = ctx->Xh;
             const int64_t plane_bytes = (int64_t)fplan.bins * g.S * fplan.Cw * (int64_t)sizeof(__nv_bfloat16);

@@ -582,11 +582,15 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
     FftBuffers& b = ps->fb;
     b.ncolp = ncolp;
     if (split) {
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 4; ++i)
             if (products == 3 || i % 2 == 0)  // BF16 spectra: hi planes only
                 ADD_CK(ps->dev(&b.Wp[i], (int64_t)p.bins * g.S * p.Cw));
-            ADD_CK(ps->dev(&b.Xp[i], (int64_t)p.bins * ncolp * p.Cw));
-            ADD_CK(ps->dev(&b.Yp[i], (int64_t)p.bins * ncolp * p.Sw));
+        // the four data planes of each 8-channel group side by side (one block)
+        ADD_CK(ps->dev(&b.Xp[0], 4 * (int64_t)p.bins * ncolp * p.Cw));
+        ADD_CK(ps->dev(&b.Yp[0], 4 * (int64_t)p.bins * ncolp * p.Sw));
+        for (int i = 1; i < 4; ++i) {
+            b.Xp[i] = b.Xp[0] + (int64_t)i * ncolp * p.bins * 8;
+            b.Yp[i] = b.Yp[0] + (int64_t)i * ncolp * p.bins * 8;
         }
     } else {
         ADD_CK(ps->dev(&b.Wf, (int64_t)p.bins * g.S * p.Cf));
@@ -614,11 +618,9 @@ lfd_status add_psf(lfd_server* s, const float* psf, int P, int N, int Nz, int ma
         cb.Cw = p.Cw;
         cb.Sf = p.Sf;
         cb.Cf = p.Cf;
-        for (int i = 0; i < 4; ++i) {
-            cb.W[i] = b.Wp[i];
-            cb.X[i] = b.Xp[i];
-            cb.Y[i] = b.Yp[i];
-        }
+        for (int i = 0; i < 4; ++i) cb.W[i] = b.Wp[i];
+        cb.X = b.Xp[0];
+        cb.Y = b.Yp[0];
         cb.Yout = b.Yh;
         cb.Xout = b.Xh;
         if (products == 3 && o.spectra_lo_tau > 0.f) {

@@ -5,29 +5,37 @@
 //   adjoint  Xh[bin][t][c] = sum_s  conj(Wf[bin][s][c]) Yh[bin][t][s]
 //
 // Every complex operand is held as four BF16 planes (real hi, real lo, imag
-// hi, imag lo; x = hi + lo) and every complex product becomes real MMAs:
-//   forward  re += Wr Xr - Wi Xi,   im += Wr Xi + Wi Xr
-//   adjoint  re += Wr Yr + Wi Yi,   im += Wr Yi - Wi Yr
-// each of them in three passes hi*hi + hi*lo + lo*hi (negation through the
-// instruction descriptor). With BF16 PSF spectra (no lo planes of Wf) the
-// passes are hi*hi + hi*lo: the PSF spectra are rounded once, the transformed
-// data still carry hi + lo, and the spectra stream is 4 bytes per complex
-// value instead of 8. With adaptive lo planes the PSF's lo planes are kept
-// only for the (bin, 64-channel block) tiles whose largest hi value reaches
-// tau x the largest of all spectra (compact planes [slot][S][64], slot 0 all
-// zeros); elsewhere the dropped lo part is below 2^-9 tau of the largest
-// value, and the k-block runs the two hi passes only. One block owns 128 output rows (phases s for the
-// forward, channels c for the adjoint) by a chunk of 16, 32 or 64 columns
-// (frame x tile) of one bin, so a spectra tile is loaded once for up to 64
-// columns; units are ordered bin-major so the blocks working on one bin share
-// its spectra in L2. Its K loop streams 64-wide blocks of all eight planes
+// hi, imag lo; x = hi + lo). The four data planes of a chunk of n columns are
+// the N = 4n columns of one B operand [Xr_hi | Xr_lo | Xi_hi | Xi_lo], so each
+// PSF plane takes one MMA per k-step: the real planes of Wf accumulate into P,
+// the imaginary ones into Q,
+//   P = (Wr_hi + Wr_lo) [Xr_hi | Xr_lo | Xi_hi | Xi_lo],   Q = (Wi_hi + Wi_lo) [ ... ],
+// and the epilogue forms
+//   forward  re = Wr Xr - Wi Xi = P_r - Q_i,   im = Wr Xi + Wi Xr = P_i + Q_r
+//   adjoint  re = Wr Yr + Wi Yi = P_r + Q_i,   im = Wr Yi - Wi Yr = P_i - Q_r
+// (P_r: the sum of P's Xr_hi and Xr_lo columns, and so on). With BF16 PSF
+// spectra (no lo planes of Wf) only the hi planes take part: the spectra are
+// rounded once, the transformed data still carry hi + lo, and the spectra
+// stream is 4 bytes per complex value instead of 8. With adaptive lo planes the
+// PSF's lo planes are kept only for the (bin, 64-channel block) tiles whose
+// largest hi value reaches tau x the largest of all spectra (compact planes
+// [slot][S][64], slot 0 all zeros); elsewhere the dropped lo part is below
+// 2^-9 tau of the largest value, and the k-block runs the hi MMAs only. One
+// block owns 128 output rows (phases s for the forward, channels c for the
+// adjoint) by a chunk of 16, 32 or 64 columns (frame x tile) of one bin, so a
+// spectra tile is loaded once for up to 64 columns; units are ordered
+// bin-major so the blocks working on one bin share its spectra in L2. Its K
+// loop streams 64-wide blocks of the PSF planes and the chunk's data planes
 // through a TMA ring (3 stages for 16 columns, 2 for wider chunks). The
-// accumulators (real and imaginary, one chunk of columns each) alternate
-// between two TMEM buffers so the drain of one chunk overlaps the next; chains
-// are cut every 64 k-blocks (1536 MMA steps) and added into the FP32 output at
-// L2 (the same rounding control as the direct projections). The spectra (all
-// of Wf) are read once per projection while the columns fit one chunk: the
-// kernel is bound by HBM bandwidth.
+// accumulators (P and Q of one chunk) alternate between two TMEM buffers (one
+// buffer of all 512 columns for 64-column chunks), so the drain of one chunk
+// overlaps the next; chains are cut every 64 k-blocks and added into the FP32
+// output at L2 (the same rounding control as the direct projections). An MMA
+// of N = 16 columns costs about as much of the tensor pipe (its A operand read
+// from shared memory) as one of N = 64, so the four data planes side by side
+// take a quarter of the instructions of one MMA per plane pair. The spectra
+// (all of Wf) are read once per projection while the columns fit one chunk:
+// the kernels are bound by HBM bandwidth.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -53,17 +61,21 @@ constexpr int kChunkKb = 64;  // 64 k-blocks x 4 k-steps x 3 passes x 2 = 1536 M
 // compact lo planes (three products there, two elsewhere).
 constexpr int MODE_BF16 = 0, MODE_SPLIT = 1, MODE_ADAPTIVE = 2;
 
-// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4).
+// Shapes of a unit of NG groups of 16 columns (NG = 1, 2 or 4). The four
+// data planes of a chunk are the NB = 4 N columns of one B operand, and each
+// PSF plane takes one MMA per k-step into the accumulator P (real part of the
+// PSF) or Q (imaginary part), each NB columns wide.
 template <int NG, int MODE>
 struct Cg {
-    static constexpr int N = 16 * NG;                        // MMA N
+    static constexpr int N = 16 * NG;                        // columns of a chunk
+    static constexpr int NB = 4 * N;                         // MMA N
     static constexpr int NA = MODE == MODE_BF16 ? 2 : 4;     // PSF planes per stage
-    static constexpr int NP = MODE == MODE_BF16 ? 2 : 3;     // products per term (at most)
-    static constexpr int kPlaneB = N * 64 * 2;               // 2, 4 or 8 KB
+    static constexpr int kPlaneB = N * 64 * 2;               // one data plane of a stage: 2, 4 or 8 KB
     static constexpr int kStageBytes = NA * kPlaneA + 4 * kPlaneB;
     static constexpr int kStages = (232448 - 1280) / kStageBytes < 6 ? (232448 - 1280) / kStageBytes : 6;
     static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
-    static constexpr uint32_t kTmemCols = 64 * NG;           // 2 buffers x (real, imag) x N
+    static constexpr int kBufs = 2 * 2 * NB <= 512 ? 2 : 1;  // accumulator buffers of (P, Q)
+    static constexpr uint32_t kTmemCols = kBufs * 2 * NB;    // 256 or 512
     static_assert(kStages >= 2 && kSmemBytes <= 232448, "stage ring exceeds the shared memory of a block");
 };
 
@@ -85,12 +97,10 @@ template <bool ADJ, int NG, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
            const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
-           const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
-           const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
-           const CgArgs a) {
+           const __grid_constant__ CUtensorMap bm, const CgArgs a) {
     using G = Cg<NG, MODE>;
     constexpr int kStages = G::kStages, kStageBytes = G::kStageBytes;
-    constexpr int kPlaneB = G::kPlaneB, N = G::N, NA = G::NA;
+    constexpr int N = G::N, NB = G::NB, NA = G::NA, kBufs = G::kBufs;
     constexpr uint32_t kTmemCols = G::kTmemCols;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -138,7 +148,6 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
         if (lane == 0) {
             // ------------------------------------------------- TMA producer --
             const CUtensorMap* A[4] = {&a0, &a1, &a2, &a3};
-            const CUtensorMap* B[4] = {&b0, &b1, &b2, &b3};
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -201,9 +210,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                             tma_3d(sA + i * kPlaneA, A[i], kb * 64, mt * 128, bin, &full[stage]);
                         }
                     }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)  // 8 channels x 1 bin x N columns x 8 groups: [group][column][8]
-                        tma_4d(sB + i * kPlaneB, B[i], 0, bin, q * N, kb * 8, &full[stage]);
+                    // 8 channels x 1 bin x N columns x (8 groups x 4 planes): [group][plane][column][8]
+                    tma_4d(sB, &bm, 0, bin, q * N, kb * 32, &full[stage]);
                     ++issued;
                     if (++stage == kStages) {
                         stage = 0;
@@ -218,22 +226,21 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer --
-            const uint32_t id_p = idesc_bf16(128, N, false, ADJ, false);
-            const uint32_t id_n = idesc_bf16(128, N, false, ADJ, true);
+            const uint32_t id = idesc_bf16(128, NB, false, ADJ, false);
             int stage = 0, consumed = 0, ci = 0;
             uint32_t phase = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 for (int c0 = 0; c0 < a.nkb && ok; c0 += kChunkKb, ++ci) {
                     const int c1 = min(a.nkb, c0 + kChunkKb);
-                    const int buf = ci & 1;
-                    if (ci >= 2 &&
-                        !mbar_wait(&acc_empty[buf], (uint32_t)(((ci - 2) >> 1) & 1), abort_flag, a.err, 12)) {
+                    const int buf = ci % kBufs;
+                    if (ci >= kBufs && !mbar_wait(&acc_empty[buf], (uint32_t)(((ci - kBufs) / kBufs) & 1),
+                                                  abort_flag, a.err, 12)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dR = tmem + buf * 2 * N, dI = dR + N;
+                    const uint32_t dP = tmem + buf * 2 * NB, dQ = dP + NB;
                     bool first = true;
                     for (int kb = c0; kb < c1 && ok; ++kb) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) {
@@ -242,40 +249,25 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         }
                         tc_fence_after();
                         const uint32_t sA = sbase + stage * kStageBytes, sB = sA + NA * kPlaneA;
-                        const int np = MODE == MODE_ADAPTIVE && !stage_lo[stage] ? 2 : G::NP;
+                        const bool lo = MODE == MODE_SPLIT || (MODE == MODE_ADAPTIVE && stage_lo[stage]);
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
-                            // B planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo; A planes
-                            // the same (four planes), or 0 real hi, 1 imag hi
-                            uint64_t ad[NA], bd[4];
+                            // A planes: 0 real hi, 1 real lo, 2 imag hi, 3 imag lo (four
+                            // planes), or 0 real hi, 1 imag hi
+                            uint64_t ad[NA];
 #pragma unroll
                             for (int i = 0; i < NA; ++i)
                                 ad[i] = ADJ ? sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024)
                                             : sdesc(sA + i * kPlaneA + ks * 32, 16, 1024);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)  // K = 16 per MMA: groups 2ks, 2ks+1 (N x 16 B
-                                                         // apart); 8-column core matrices 128 B apart
-                                bd[i] = sdesc_noswz(sB + i * kPlaneB + ks * 2 * N * 16, N * 16, 128);
-#pragma unroll
-                            for (int p = 0; p < G::NP; ++p) {
-                                if (p >= np) break;
-                                // four planes: (hi, hi), (hi, lo), (lo, hi); two: (hi, hi), (hi, lo)
-                                constexpr bool four = NA == 4;
-                                const int ia = (four && p == 2) ? 1 : 0;
-                                const int ib = p == 1 ? 1 : 0;
-                                const uint64_t wr = ad[ia], wi = ad[four ? 2 + ia : 1];
-                                const uint32_t acc0 = (first && ks == 0 && p == 0) ? 0u : 1u;
-                                if (!ADJ) {
-                                    umma_bf16(dR, wr, bd[ib], id_p, acc0);          // + Wr Xr
-                                    umma_bf16(dR, wi, bd[2 + ib], id_n, 1u);        // - Wi Xi
-                                    umma_bf16(dI, wr, bd[2 + ib], id_p, acc0);      // + Wr Xi
-                                    umma_bf16(dI, wi, bd[ib], id_p, 1u);            // + Wi Xr
-                                } else {
-                                    umma_bf16(dR, wr, bd[ib], id_p, acc0);          // + Wr Yr
-                                    umma_bf16(dR, wi, bd[2 + ib], id_p, 1u);        // + Wi Yi
-                                    umma_bf16(dI, wr, bd[2 + ib], id_p, acc0);      // + Wr Yi
-                                    umma_bf16(dI, wi, bd[ib], id_n, 1u);            // - Wi Yr
-                                }
+                            // B: groups 2ks, 2ks + 1 (4N x 16 B apart), rows plane x N + column
+                            const uint64_t bd = sdesc_noswz(sB + ks * 2 * NB * 16, NB * 16, 128);
+                            const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+                            constexpr bool four = NA == 4;
+                            umma_bf16(dP, ad[0], bd, id, acc0);            // P += Wr_hi [Xr | Xi]
+                            umma_bf16(dQ, ad[four ? 2 : 1], bd, id, acc0); // Q += Wi_hi [Xr | Xi]
+                            if (four && lo) {
+                                umma_bf16(dP, ad[1], bd, id, 1u);          // P += Wr_lo [Xr | Xi]
+                                umma_bf16(dQ, ad[3], bd, id, 1u);          // Q += Wi_lo [Xr | Xi]
                             }
                         }
                         first = false;
@@ -303,21 +295,45 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
             const int q = rem / a.mtiles, mt = rem % a.mtiles;
             const int grow = mt * 128 + row;
             for (int c0 = 0; c0 < a.nkb; c0 += kChunkKb, ++ci) {
-                const int buf = ci & 1;
-                if (!mbar_wait(&acc_full[buf], (uint32_t)((ci >> 1) & 1), abort_flag, a.err, 14)) {
+                const int buf = ci % kBufs;
+                if (!mbar_wait(&acc_full[buf], (uint32_t)((ci / kBufs) & 1), abort_flag, a.err, 14)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16) + buf * 2 * N;
+                const uint32_t tb = tmem + ((uint32_t)(lg * 32) << 16) + buf * 2 * NB;
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     const int col0 = q * N + g * 16;
                     if (col0 >= a.ncol) break;
-                    uint32_t re[16], im[16];
-                    tmem_ld16(tb + g * 16, re);
-                    tmem_ld16(tb + N + g * 16, im);
-                    tmem_wait_ld();
+                    // P, Q columns plane x N + column: planes 0 real hi, 1 real lo, 2 imag hi, 3 imag lo
+                    const uint32_t tP = tb + g * 16, tQ = tP + NB;
+                    float re[16], im[16];
+                    {
+                        uint32_t x0[16], x1[16], x2[16], x3[16];
+                        tmem_ld16(tP, x0);
+                        tmem_ld16(tP + N, x1);
+                        tmem_ld16(tQ + 2 * N, x2);
+                        tmem_ld16(tQ + 3 * N, x3);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {  // forward Wr Xr - Wi Xi, adjoint Wr Yr + Wi Yi
+                            const float pr = __uint_as_float(x0[t]) + __uint_as_float(x1[t]);
+                            const float qi = __uint_as_float(x2[t]) + __uint_as_float(x3[t]);
+                            re[t] = ADJ ? pr + qi : pr - qi;
+                        }
+                        tmem_ld16(tP + 2 * N, x0);
+                        tmem_ld16(tP + 3 * N, x1);
+                        tmem_ld16(tQ, x2);
+                        tmem_ld16(tQ + N, x3);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {  // forward Wr Xi + Wi Xr, adjoint Wr Yi - Wi Yr
+                            const float pi = __uint_as_float(x0[t]) + __uint_as_float(x1[t]);
+                            const float qr = __uint_as_float(x2[t]) + __uint_as_float(x3[t]);
+                            im[t] = ADJ ? pi - qr : pi + qr;
+                        }
+                    }
                     if (grow < a.nrows) {
                         // group-major output [ld/8][ncol][bins][8]: the inverse
                         // transform reads a column's bins of 8 rows as one run
@@ -327,9 +343,8 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         for (int t = 0; t < 16; ++t) {
                             if (col0 + t < a.ncol) {
                                 float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.nbins * 8);
-                                const float vr = __uint_as_float(re[t]), vi = __uint_as_float(im[t]);
-                                if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(vr, vi);
-                                else red_add_v2(dst, vr, vi);
+                                if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(re[t], im[t]);
+                                else red_add_v2(dst, re[t], im[t]);
                             }
                         }
                     }
@@ -357,7 +372,7 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
 // of the wide PSF copy, hi and (where the bin's 64-channel block keeps it) lo,
 // each one bulk copy of 64 S bytes laid out [row tile][plane][group][rows][8],
 // and the bin's four data planes side by side as the N = 64 columns of one B
-// operand, [group][plane][column][8] (TMA boxes of one channel group). Each
+// operand, [group][plane][column][8] (one TMA box per bin). Each
 // PSF part then takes two MMAs per (bin, row tile):
 //   P += Wr [Xr_hi | Xr_lo | Xi_hi | Xi_lo],   Q += Wi [Xr_hi | Xr_lo | Xi_hi | Xi_lo]
 // (Wr, Wi the hi part, and the lo part where kept), and the epilogue forms
@@ -394,9 +409,7 @@ struct WideArgs {
 };
 
 __global__ void __launch_bounds__(kWideThreads, 1)
-k_tc_cgemm_wide(const __grid_constant__ CUtensorMap b0, const __grid_constant__ CUtensorMap b1,
-                const __grid_constant__ CUtensorMap b2, const __grid_constant__ CUtensorMap b3,
-                const WideArgs a) {
+k_tc_cgemm_wide(const __grid_constant__ CUtensorMap bm, const WideArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -442,7 +455,6 @@ k_tc_cgemm_wide(const __grid_constant__ CUtensorMap b0, const __grid_constant__ 
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------- copy producer --
-            const CUtensorMap* B[4] = {&b0, &b1, &b2, &b3};
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -481,12 +493,8 @@ k_tc_cgemm_wide(const __grid_constant__ CUtensorMap b0, const __grid_constant__ 
                         if (sl)
                             bulk_g2s(sA + (2 + j) * kWideGroup, a.lo + ((int64_t)sl * 4 + (kb & 3)) * grp, grp,
                                      &full[stage]);
-#pragma unroll
-                        for (int g = 0; g < 2; ++g)
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)  // 8 channels x 1 bin x 16 columns of one group
-                                tma_4d(sB + j * kWideB + g * 1024 + i * 256, B[i], 0, bin, q * 16, kb * 2 + g,
-                                       &full[stage]);
+                        // 8 channels x 1 bin x 16 columns x (2 groups x 4 planes)
+                        tma_4d(sB + j * kWideB, &bm, 0, bin, q * 16, kb * 8, &full[stage]);
                     }
                     ++issued;
                     if (++stage == kWideStages) {
@@ -648,9 +656,10 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// grouped column planes [groups][ncolp][bins][8]: the box 8 channels x 1 bin x
-// ncb columns x gbox groups lands densely (no swizzle) as [group][column][8],
-// the K-major core-matrix layout the B descriptors of the kernels describe
+// grouped column planes [rows][ncolp][bins][8] (rows: channel group x 4 +
+// plane): the box 8 channels x 1 bin x ncb columns x gbox rows lands densely
+// (no swizzle) as [group][plane][column][8], the K-major core-matrix layout of
+// the B operands the kernels describe (N = 4 ncb rows: plane x ncb + column)
 bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp,
                   uint32_t ncb, uint32_t gbox = 8) {
     auto fn = encode_fn();
@@ -669,8 +678,8 @@ constexpr int kNg[3] = {1, 2, 4};
 
 struct CgState {
     CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (see the modes)
-    CUtensorMap fb[3][4], ab[3][4];  // per chunk width
-    CUtensorMap fw[4];               // data planes, boxes of one group (wide forward units)
+    CUtensorMap fb[3], ab[3];        // data planes per chunk width
+    CUtensorMap fw;                  // data planes, boxes of 2 groups (wide forward units)
     CgArgs fwd, adj;
     WideArgs wide;
     bool use_wide = false;
@@ -685,8 +694,7 @@ cudaError_t launch_width(const CUtensorMap* A, const CUtensorMap* B, CgArgs a, i
     using G = Cg<NG, MODE>;
     a.nchunk = (a.ncol + G::N - 1) / G::N;
     const int grid = std::min(a.nbins * a.nchunk * a.mtiles, sm_count);
-    k_tc_cgemm<ADJ, NG, MODE><<<grid, kThreads, G::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], B[0], B[1],
-                                                                     B[2], B[3], a);
+    k_tc_cgemm<ADJ, NG, MODE><<<grid, kThreads, G::kSmemBytes, st>>>(A[0], A[1], A[2], A[3], *B, a);
     count_launch();
     return cudaGetLastError();
 }
@@ -709,7 +717,7 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
         w.ncol = ncol;
         w.nchunk = 1;
         const int grid = std::min(w.npairs * w.nchunk, s->sm_count);
-        k_tc_cgemm_wide<<<grid, kWideThreads, kWideSmem, st>>>(s->fw[0], s->fw[1], s->fw[2], s->fw[3], w);
+        k_tc_cgemm_wide<<<grid, kWideThreads, kWideSmem, st>>>(s->fw, w);
         count_launch();
         return cudaGetLastError();
     }
@@ -720,7 +728,7 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     int j = 0;
     while (j + 1 < s->nwidths && kNg[j] < ncg) ++j;
     const CUtensorMap* A = ADJ ? s->aa : s->fa;
-    const CUtensorMap* B = ADJ ? s->ab[j] : s->fb[j];
+    const CUtensorMap* B = ADJ ? &s->ab[j] : &s->fb[j];
     switch (s->mode) {
         case MODE_BF16: return launch_mode<ADJ, MODE_BF16>(kNg[j], A, B, a, s->sm_count, st);
         case MODE_ADAPTIVE: return launch_mode<ADJ, MODE_ADAPTIVE>(kNg[j], A, B, a, s->sm_count, st);
@@ -940,11 +948,15 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
             ok = w && map3(&s->fa[i], w, b.Cw, b.S, b.bins, 64, 128) &&
                  map3(&s->aa[i], w, b.Cw, b.S, b.bins, 64, 64);
         }
-        for (int j = 0; j < s->nwidths && ok; ++j)
-            ok = map4_grouped(&s->fb[j][i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16 * kNg[j]) &&
-                 map4_grouped(&s->ab[j][i], b.Y[i], b.Sw / 8, b.bins, b.ncolp, 16 * kNg[j]);
         if (!ok) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the spectra planes";
+            return cudaErrorInvalidValue;
+        }
+    }
+    for (int j = 0; j < s->nwidths; ++j) {  // rows of the data maps: group x 4 + plane
+        if (!map4_grouped(&s->fb[j], b.X, 4 * (b.Cw / 8), b.bins, b.ncolp, 16 * kNg[j], 32) ||
+            !map4_grouped(&s->ab[j], b.Y, 4 * (b.Sw / 8), b.bins, b.ncolp, 16 * kNg[j], 32)) {
+            if (why) *why = "cuTensorMapEncodeTiled failed for the data planes";
             return cudaErrorInvalidValue;
         }
     }
@@ -970,9 +982,7 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
     if (s->mode == MODE_ADAPTIVE && b.wide.hi && b.S <= 256 && b.bins % 2 == 0) {
-        bool ok = true;
-        for (int i = 0; i < 4 && ok; ++i) ok = map4_grouped(&s->fw[i], b.X[i], b.Cw / 8, b.bins, b.ncolp, 16, 1);
-        if (!ok) {
+        if (!map4_grouped(&s->fw, b.X, 4 * (b.Cw / 8), b.bins, b.ncolp, 16, 8)) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the wide units' data planes";
             return cudaErrorInvalidValue;
         }

@@ -42,8 +42,8 @@ struct CgemmBuffers {
     int Sw, Cw;               // plane row lengths (multiples of 8)
     int Sf, Cf;               // FP32 complex output row lengths
     const __nv_bfloat16* W[4];  // [bins][S][Cw] PSF spectra
-    const __nv_bfloat16* X[4];  // [Cw/8][ncolp][bins][8] volume spectra (forward input)
-    const __nv_bfloat16* Y[4];  // [Sw/8][ncolp][bins][8] ratio spectra (adjoint input)
+    const __nv_bfloat16* X;   // [Cw/8][4 planes][ncolp][bins][8] volume spectra (forward input)
+    const __nv_bfloat16* Y;   // [Sw/8][4 planes][ncolp][bins][8] ratio spectra (adjoint input)
     float2* Yout;             // [Sf/8][ncol][bins][8] forward output (group-major)
     float2* Xout;             // [Cf/8][ncol][bins][8] adjoint output (group-major)
     LoPlanes lo;              // adaptive lo planes (slot null otherwise)
