@@ -1174,7 +1174,10 @@ bool fft_plan_for(const Geo& g, FftPlan* p, int force_F, int frames, int tc_prod
         q.bins = F * (F / 2 + 1);
         q.Cf = (g.C + 7) & ~7;
         q.Sf = (g.S + 7) & ~7;
-        q.Cw = (g.C + 7) & ~7;
+        // BF16 plane rows in whole 256-byte blocks: the contractions' PSF tiles
+        // (64 or 128 channels of a row) then never share an L2 line with their
+        // neighbours
+        q.Cw = (g.C + 127) & ~127;
         q.Sw = (g.S + 7) & ~7;
         // complex64, split BF16 (4 planes) or BF16 (2 planes)
         const double spectra = (double)q.bins * g.S * q.Cf * (tc_products == 2 ? 4.0 : 8.0);

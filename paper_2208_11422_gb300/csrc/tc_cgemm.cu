@@ -630,6 +630,257 @@ k_tc_cgemm_wide(const __grid_constant__ CUtensorMap bm, const WideArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWideTmem));
 }
 
+// Adjoint units with the data resident (single chunks of up to 16 columns,
+// Sw <= 256). The ratio spectra of one bin are 4 k-blocks x 8 KB; a block owns
+// a contiguous range of (bin, row tile) units in bin-major order, keeps the
+// current bin's data planes in shared memory (loaded once per bin, about 14
+// bins per block at the large frame), and streams only the PSF planes through
+// its ring. Otherwise as k_tc_cgemm<ADJ = true, NG = 1>. Waits 15 and 16 are
+// the data region's (free for reload, loaded).
+constexpr int kResB = 4 * 8192;  // resident data: 4 k-blocks x (8 groups x 4 planes x 16 columns x 16 B)
+template <int MODE>
+struct CgR {
+    static constexpr int NA = MODE == MODE_BF16 ? 2 : 4;
+    static constexpr int kStageBytes = NA * kPlaneA;
+    static constexpr int kStages =
+        (232448 - 1280 - kResB) / kStageBytes < 6 ? (232448 - 1280 - kResB) / kStageBytes : 6;
+    static constexpr int kSmemBytes = kStages * kStageBytes + kResB + 1024 + 256;
+    static_assert(kStages >= 2 && kSmemBytes <= 232448, "stage ring exceeds the shared memory of a block");
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_cgemm_adjr(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
+                const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap a3,
+                const __grid_constant__ CUtensorMap bm, const CgArgs a) {
+    using G = CgR<MODE>;
+    constexpr int kStages = G::kStages, kStageBytes = G::kStageBytes, NA = G::NA;
+    constexpr int N = 16, NB = 64;
+    constexpr uint32_t kTmemCols = 256;  // 2 buffers x (P, Q) x 64 columns
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t* smem = smem_raw + (sbase - raw);
+    const uint32_t sBres = sbase + kStages * kStageBytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + kResB);
+    uint64_t* empty = full + kStages;
+    uint64_t* acc_full = empty + kStages;   // [2]
+    uint64_t* acc_empty = acc_full + 2;     // [2]
+    uint64_t* b_full = acc_empty + 2;
+    uint64_t* b_empty = b_full + 1;
+    uint64_t* mma_done = b_empty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* consumed_ctr = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    volatile int* b_seen = reinterpret_cast<volatile int*>(tmem_slot + 3);
+    volatile int* stage_lo = reinterpret_cast<volatile int*>(tmem_slot + 4);  // [kStages]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_units = (int64_t)a.nbins * a.mtiles;
+    const int64_t u0 = (int64_t)blockIdx.x * n_units / gridDim.x;
+    const int64_t u1 = (int64_t)(blockIdx.x + 1) * n_units / gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(b_full, 1);
+        mbar_init(b_empty, 1);
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        *consumed_ctr = 0;
+        *b_seen = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------- TMA producer --
+            const CUtensorMap* A[4] = {&a0, &a1, &a2, &a3};
+            int stage = 0, issued = 0, nb = 0, cur_bin = -1;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t u = u0; u < u1 && ok; ++u) {
+                const int bin = (int)(u / a.mtiles), mt = (int)(u % a.mtiles);
+                if (bin != cur_bin) {  // the bin's data planes, once the previous bin's MMAs are done
+                    if (nb > 0 && !mbar_wait(b_empty, (uint32_t)((nb - 1) & 1), abort_flag, a.err, 15)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_full, a.nkb * 8192);
+                    for (int kb = 0; kb < a.nkb; ++kb)  // 8 channels x 1 bin x 16 columns x (8 groups x 4 planes)
+                        tma_4d(sBres + kb * 8192, &bm, 0, bin, 0, kb * 32, b_full);
+                    ++nb;
+                    cur_bin = bin;
+                }
+                int lo0 = 0, lo1 = 0;  // the tile's two 64-channel atoms
+                if (MODE == MODE_ADAPTIVE) {
+                    const int* ls = a.lo_slot + (int64_t)bin * a.nkbc;
+                    lo0 = 2 * mt < a.nkbc ? ls[2 * mt] : 0;
+                    lo1 = 2 * mt + 1 < a.nkbc ? ls[2 * mt + 1] : 0;
+                }
+                const bool lo = MODE == MODE_SPLIT || (MODE == MODE_ADAPTIVE && (lo0 | lo1) != 0);
+                for (int kb = 0; kb < a.nkb && ok; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    if (MODE == MODE_ADAPTIVE) stage_lo[stage] = lo ? 1 : 0;
+                    mbar_expect_tx(&full[stage], lo || MODE == MODE_BF16 ? kStageBytes : kStageBytes - 2 * kPlaneA);
+                    const uint32_t sA = sbase + stage * kStageBytes;
+#pragma unroll
+                    for (int i = 0; i < NA; ++i) {
+                        if (MODE == MODE_ADAPTIVE && (i & 1)) {  // compact lo plane [slot][S][64]
+                            if (!lo) continue;
+                            tma_3d(sA + i * kPlaneA, A[i], 0, kb * 64, lo0, &full[stage]);
+                            tma_3d(sA + i * kPlaneA + 8192, A[i], 0, kb * 64, lo1, &full[stage]);
+                        } else {  // MN-major: two 64-channel atoms of 64 phases
+                            tma_3d(sA + i * kPlaneA, A[i], mt * 128, kb * 64, bin, &full[stage]);
+                            tma_3d(sA + i * kPlaneA + 8192, A[i], mt * 128 + 64, kb * 64, bin, &full[stage]);
+                        }
+                    }
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                for (int i = *consumed_ctr; i < issued; ++i)
+                    mbar_wait_drain(&full[i % kStages], (uint32_t)((i / kStages) & 1));
+                if (nb > *b_seen) mbar_wait_drain(b_full, (uint32_t)((nb - 1) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer --
+            const uint32_t id = idesc_bf16(128, NB, false, true, false);
+            int stage = 0, consumed = 0, ci = 0, nb = 0, cur_bin = -1;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t u = u0; u < u1 && ok; ++u, ++ci) {
+                const int bin = (int)(u / a.mtiles);
+                if (bin != cur_bin) {
+                    if (!mbar_wait(b_full, (uint32_t)(nb & 1), abort_flag, a.err, 16)) {
+                        ok = false;
+                        break;
+                    }
+                    *b_seen = ++nb;
+                    cur_bin = bin;
+                }
+                const int buf = ci & 1;
+                if (ci >= 2 &&
+                    !mbar_wait(&acc_empty[buf], (uint32_t)(((ci - 2) >> 1) & 1), abort_flag, a.err, 12)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dP = tmem + buf * 2 * NB, dQ = dP + NB;
+                for (int kb = 0; kb < a.nkb && ok; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sA = sbase + stage * kStageBytes;
+                    const bool lo = MODE == MODE_SPLIT || (MODE == MODE_ADAPTIVE && stage_lo[stage]);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        uint64_t ad[NA];
+#pragma unroll
+                        for (int i = 0; i < NA; ++i) ad[i] = sdesc(sA + i * kPlaneA + ks * 2048, 8192, 1024);
+                        const uint64_t bd = sdesc_noswz(sBres + kb * 8192 + ks * 2 * NB * 16, NB * 16, 128);
+                        const uint32_t acc0 = (kb == 0 && ks == 0) ? 0u : 1u;
+                        constexpr bool four = NA == 4;
+                        umma_bf16(dP, ad[0], bd, id, acc0);             // P += Wr_hi [Yr | Yi]
+                        umma_bf16(dQ, ad[four ? 2 : 1], bd, id, acc0);  // Q += Wi_hi [Yr | Yi]
+                        if (four && lo) {
+                            umma_bf16(dP, ad[1], bd, id, 1u);
+                            umma_bf16(dQ, ad[3], bd, id, 1u);
+                        }
+                    }
+                    umma_commit(&empty[stage]);
+                    *consumed_ctr = ++consumed;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&acc_full[buf]);
+                if (u + 1 == u1 || (int)((u + 1) / a.mtiles) != bin) umma_commit(b_empty);  // data free
+            }
+            umma_commit(mma_done);
+            mbar_wait_drain(mma_done, 0);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int lg = warp & 3;
+        const int row = lg * 32 + lane;
+        int ci = 0;
+        for (int64_t u = u0; u < u1; ++u, ++ci) {
+            const int bin = (int)(u / a.mtiles), mt = (int)(u % a.mtiles);
+            const int grow = mt * 128 + row;
+            const int buf = ci & 1;
+            if (!mbar_wait(&acc_full[buf], (uint32_t)((ci >> 1) & 1), abort_flag, a.err, 14)) break;
+            tc_fence_after();
+            const uint32_t tP = tmem + ((uint32_t)(lg * 32) << 16) + buf * 2 * NB, tQ = tP + NB;
+            float re[16], im[16];
+            {
+                uint32_t x0[16], x1[16], x2[16], x3[16];
+                tmem_ld16(tP, x0);
+                tmem_ld16(tP + N, x1);
+                tmem_ld16(tQ + 2 * N, x2);
+                tmem_ld16(tQ + 3 * N, x3);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 16; ++t)  // Wr Yr + Wi Yi
+                    re[t] = (__uint_as_float(x0[t]) + __uint_as_float(x1[t])) +
+                            (__uint_as_float(x2[t]) + __uint_as_float(x3[t]));
+                tmem_ld16(tP + 2 * N, x0);
+                tmem_ld16(tP + 3 * N, x1);
+                tmem_ld16(tQ, x2);
+                tmem_ld16(tQ + N, x3);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 16; ++t)  // Wr Yi - Wi Yr
+                    im[t] = (__uint_as_float(x0[t]) + __uint_as_float(x1[t])) -
+                            (__uint_as_float(x2[t]) + __uint_as_float(x3[t]));
+            }
+            if (grow < a.nrows) {
+                float2* o = a.out + ((int64_t)(grow >> 3) * a.ncol * a.nbins + bin) * 8 + (grow & 7);
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    if (t < a.ncol) o[(int64_t)t * a.nbins * 8] = make_float2(re[t], im[t]);
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -683,6 +934,7 @@ struct CgState {
     CgArgs fwd, adj;
     WideArgs wide;
     bool use_wide = false;
+    bool use_adjr = false;  // adjoint with resident data for chunks of <= 16 columns
     int sm_count = 0, ncolp = 16, nwidths = 1;
     int mode = MODE_SPLIT;
     int* err = nullptr;
@@ -723,6 +975,26 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     }
     CgArgs a = ADJ ? s->adj : s->fwd;
     a.ncol = ncol;
+    if (ADJ && s->use_adjr && ncol <= 16) {
+        a.nchunk = 1;
+        const int grid = (int)std::min<int64_t>((int64_t)a.nbins * a.mtiles, s->sm_count);
+        const CUtensorMap* A = s->aa;
+        switch (s->mode) {
+            case MODE_BF16:
+                k_tc_cgemm_adjr<MODE_BF16><<<grid, kThreads, CgR<MODE_BF16>::kSmemBytes, st>>>(
+                    A[0], A[1], A[2], A[3], s->ab[0], a);
+                break;
+            case MODE_ADAPTIVE:
+                k_tc_cgemm_adjr<MODE_ADAPTIVE><<<grid, kThreads, CgR<MODE_ADAPTIVE>::kSmemBytes, st>>>(
+                    A[0], A[1], A[2], A[3], s->ab[0], a);
+                break;
+            default:
+                k_tc_cgemm_adjr<MODE_SPLIT><<<grid, kThreads, CgR<MODE_SPLIT>::kSmemBytes, st>>>(
+                    A[0], A[1], A[2], A[3], s->ab[0], a);
+        }
+        count_launch();
+        return cudaGetLastError();
+    }
     // the narrowest chunk that covers all columns, else the widest available
     const int ncg = (ncol + 15) / 16;
     int j = 0;
@@ -742,6 +1014,7 @@ cudaError_t set_smem() {
     auto one = [&](auto kern, int bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     };
+    one(k_tc_cgemm_adjr<MODE>, CgR<MODE>::kSmemBytes);
     one(k_tc_cgemm<false, 1, MODE>, Cg<1, MODE>::kSmemBytes);
     one(k_tc_cgemm<true, 1, MODE>, Cg<1, MODE>::kSmemBytes);
     one(k_tc_cgemm<false, 2, MODE>, Cg<2, MODE>::kSmemBytes);
@@ -981,6 +1254,7 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     g.out = b.Xout;
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
+    s->use_adjr = g.nkb <= kResB / 8192;
     if (s->mode == MODE_ADAPTIVE && b.wide.hi && b.S <= 256 && b.bins % 2 == 0) {
         if (!map4_grouped(&s->fw, b.X, 4 * (b.Cw / 8), b.bins, b.ncolp, 16, 8)) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the wide units' data planes";

@@ -68,7 +68,7 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
 // ncol = frames x tiles of this call (<= ncolp)
 cudaError_t cgemm_forward(void* state, int ncol, cudaStream_t st);
 cudaError_t cgemm_adjoint(void* state, int ncol, cudaStream_t st);
-int cgemm_error(void* state);  // 0, or the code of a wait that gave up (11-14)
+int cgemm_error(void* state);  // 0, or the code of a wait that gave up (11-16)
 void cgemm_destroy(void* state);
 
 }  // namespace lfd
