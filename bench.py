@@ -304,10 +304,13 @@ def fft_plan_numbers(g, plan):
 # 11475 / 900; the contractions' does not (the share of kept lo tiles and the
 # transformed volume's re-reads depend on the depths), so they have no entry.
 NCU_TRAFFIC = {
+    # 4-depth case (C = 900 channels, 1024 transformed); reads scale with the
+    # channels read (C for the volume, Cf = 904 for the spectra), writes with
+    # the channels written (Cw = 1024 for the planes, C for the volume)
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
-        ((0.080609e9 + 0.180679e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        (74.571e6 * 11475 / 900 + 214.35e6 * 11520 / 1024, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
     ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
-        ((0.244429e9 + 0.043105e9) * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
+        (244.45e6 * 11480 / 904 + 45.85e6 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
 
 

@@ -40,6 +40,10 @@ constexpr int kMinLong = 8;
 constexpr int kShortVpw = kMinLong - 1;
 constexpr int kNsMax = 16;               // PSF rows up to 512 taps (ns = ceil(P / 32) <= 16)
 constexpr int kLongFill = 8, kShortFill = 16;  // image-row floats per thread
+// PSF rows per pass between barriers (long pieces): two measured 0.696 against
+// 0.685 ms at the large frame (128 instead of 72 registers, 16 instead of 28
+// warps per SM)
+constexpr int kLongRps = 1;
 constexpr int kLongSpan = 32 * kLongWarps * kLongFill, kShortSpan = 32 * kShortFill;
 
 struct ExactRun {
@@ -58,9 +62,10 @@ __device__ __forceinline__ void piece_sync() {
 
 // One piece of a run with WARPS warps, VPW voxel slots per warp, NS =
 // ceil(P / 32) chunks of a PSF row per lane, and image-row segments of up to
-// 32 WARPS FILL floats. The next PSF row and image row are loaded into
-// registers while the current one is summed.
-template <int NS, int WARPS, int VPW, int FILL>
+// 32 WARPS FILL floats, RPS PSF rows (and image rows) per pass between two
+// block barriers. The next pass's PSF rows and image rows are loaded into
+// registers while the current ones are summed.
+template <int NS, int WARPS, int VPW, int FILL, int RPS>
 __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ pos,
                             const int64_t* __restrict__ out, const float* __restrict__ rimg,
                             const float* __restrict__ rimgT, const float* __restrict__ psf,
@@ -87,39 +92,52 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
 #pragma unroll
     for (int k = 0; k < VPW; ++k) acc[k] = 0.f;
 
-    float nxt[FILL], knx[NS];
-    auto fetch = [&](int mi) {  // image row and PSF row mi into registers
-        const float* row = img + (int64_t)(ip - c0 + mi) * Ww;
+    float nxt[RPS][FILL], knx[RPS][NS];
+    auto fetch = [&](int m) {  // image rows and PSF rows m .. m + RPS - 1 into registers
 #pragma unroll
-        for (int u = 0; u < FILL; ++u) {
-            const int e = threadIdx.x + u * T, col = j0 + e;
-            nxt[u] = (e < span && col >= 0 && col < Ww) ? row[col] : 0.f;
-        }
+        for (int r = 0; r < RPS; ++r) {
+            const int mi = m + r;
+            const bool in = mi < mi1;
+            const float* row = img + (int64_t)(ip - c0 + (in ? mi : m)) * Ww;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int mj = lane + 32 * s;
-            knx[s] = mj < P ? K[(int64_t)mi * P + mj] : 0.f;
+            for (int u = 0; u < FILL; ++u) {
+                const int e = threadIdx.x + u * T, col = j0 + e;
+                nxt[r][u] = (in && e < span && col >= 0 && col < Ww) ? row[col] : 0.f;
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int mj = lane + 32 * s;
+                knx[r][s] = (in && mj < P) ? K[(int64_t)mi * P + mj] : 0.f;
+            }
         }
     };
     if (mi0 < mi1) fetch(mi0);
-    for (int mi = mi0; mi < mi1; ++mi) {
-        piece_sync<WARPS>();  // the previous row's products are done
+    for (int mi = mi0; mi < mi1; mi += RPS) {
+        piece_sync<WARPS>();  // the previous pass's products are done
 #pragma unroll
-        for (int u = 0; u < FILL; ++u) {
-            const int e = threadIdx.x + u * T;
-            if (e < span) rs[e] = nxt[u];
-        }
-        float kr[NS];
+        for (int r = 0; r < RPS; ++r)
 #pragma unroll
-        for (int s = 0; s < NS; ++s) kr[s] = knx[s];
+            for (int u = 0; u < FILL; ++u) {
+                const int e = threadIdx.x + u * T;
+                if (e < span) rs[r * span + e] = nxt[r][u];
+            }
+        float kr[RPS][NS];
+#pragma unroll
+        for (int r = 0; r < RPS; ++r)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) kr[r][s] = knx[r][s];
         piece_sync<WARPS>();
-        if (mi + 1 < mi1) fetch(mi + 1);
+        if (mi + RPS < mi1) fetch(mi + RPS);
 #pragma unroll
-        for (int k = 0; k < VPW; ++k) {
-            if (warp + WARPS * k < R.count) {
-                const float* q = rs + off[k] + lane;
+        for (int r = 0; r < RPS; ++r) {
+            if (mi + r >= mi1) break;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) acc[k] = fmaf(q[32 * s], kr[s], acc[k]);
+            for (int k = 0; k < VPW; ++k) {
+                if (warp + WARPS * k < R.count) {
+                    const float* q = rs + r * span + off[k] + lane;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) acc[k] = fmaf(q[32 * s], kr[r][s], acc[k]);
+                }
             }
         }
     }
@@ -134,7 +152,7 @@ __device__ void exact_piece(const ExactRun& R, int f, const int* __restrict__ po
 }
 
 // pieces sorted by cost; block b of the grid takes pieces b, b + gridDim.x, ...
-template <int NS, int WARPS, int VPW, int FILL>
+template <int NS, int WARPS, int VPW, int FILL, int RPS>
 __global__ void __launch_bounds__(32 * WARPS) k_exact_runs(const ExactRun* __restrict__ runs, int nruns,
                                                            const int* __restrict__ pos,
                                                            const int64_t* __restrict__ out,
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_exact_runs(const ExactRun* __res
     extern __shared__ float rs[];
     for (int b = blockIdx.x; b < nruns; b += gridDim.x) {
         const ExactRun R = runs[b];
-        exact_piece<NS, WARPS, VPW, FILL>(R, blockIdx.y, pos, out, rimg, rimgT, psf, psfT, g, xcm, rs);
+        exact_piece<NS, WARPS, VPW, FILL, RPS>(R, blockIdx.y, pos, out, rimg, rimgT, psf, psfT, g, xcm, rs);
         piece_sync<WARPS>();  // rs is reused by the next piece
     }
 }
@@ -154,12 +172,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_exact_runs(const ExactRun* __res
 using RunsKernel = void (*)(const ExactRun*, int, const int*, const int64_t*, const float*, const float*,
                             const float*, const float*, Geo, float*);
 
-template <int NS, int WARPS, int VPW, int FILL>
+template <int NS, int WARPS, int VPW, int FILL, int RPS>
 RunsKernel runs_kernel_n(int ns) {
     if constexpr (NS > kNsMax) {
         return nullptr;
     } else {
-        return ns == NS ? k_exact_runs<NS, WARPS, VPW, FILL> : runs_kernel_n<NS + 1, WARPS, VPW, FILL>(ns);
+        return ns == NS ? k_exact_runs<NS, WARPS, VPW, FILL, RPS> : runs_kernel_n<NS + 1, WARPS, VPW, FILL, RPS>(ns);
     }
 }
 
@@ -396,9 +414,9 @@ cudaError_t exact_plan_create(const int64_t* low, int64_t n, const Geo& g, const
             (e = cudaMemcpyAsync(p->out, outs.data(), sizeof(int64_t) * outs.size(), cudaMemcpyHostToDevice,
                                  st)) != cudaSuccess)
             return fail("upload");
-        p->kern_long = runs_kernel_n<1, kLongWarps, kLongVpw, kLongFill>(ns);
-        p->kern_short = runs_kernel_n<1, 1, kShortVpw, kShortFill>(ns);
-        if ((p->nlong && (e = slots_for(p->kern_long, 32 * kLongWarps, sizeof(float) * p->span_long,
+        p->kern_long = runs_kernel_n<1, kLongWarps, kLongVpw, kLongFill, kLongRps>(ns);
+        p->kern_short = runs_kernel_n<1, 1, kShortVpw, kShortFill, 1>(ns);
+        if ((p->nlong && (e = slots_for(p->kern_long, 32 * kLongWarps, sizeof(float) * kLongRps * p->span_long,
                                         &p->slots_long)) != cudaSuccess) ||
             (p->nshort && (e = slots_for(p->kern_short, 32, sizeof(float) * p->span_short,
                                          &p->slots_short)) != cudaSuccess))
@@ -448,7 +466,8 @@ cudaError_t exact_bwd(ExactPlan* p, int nf, const float* rimg, float* xcm, cudaS
     }
     if (p->nlong) {
         const int gx = std::min(p->nlong, std::max(1, p->slots_long / nf));
-        p->kern_long<<<dim3((unsigned)gx, (unsigned)nf), 32 * kLongWarps, sizeof(float) * p->span_long, st>>>(
+        p->kern_long<<<dim3((unsigned)gx, (unsigned)nf), 32 * kLongWarps, sizeof(float) * kLongRps * p->span_long,
+                       st>>>(
             p->runs, p->nlong, p->pos, p->out, rimg, p->rimgT, p->psf, p->psfT, g, xcm);
         count_launch();
         cudaError_t e = cudaGetLastError();

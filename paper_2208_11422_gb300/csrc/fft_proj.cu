@@ -40,14 +40,18 @@ struct FftSize {
     static constexpr int HF = F / 2;           // points of each lane's 1-D transform (F/2)
     static constexpr int H2 = F / 2 + 1;       // half-spectrum columns
     static constexpr int BINS = F * H2;
-    // per transform block: at F = 64, 4 channels in 256 threads and two
-    // blocks per SM (each 68 KB of half spectra), so that one block's loads
-    // overlap the other's transforms; at F = 32, 16 channels in 512 threads
-    static constexpr int THREADS = F == 64 ? 256 : 512;
-    static constexpr int MINB = 512 / THREADS;  // blocks per SM (launch bounds)
-    static constexpr int R2C_CH = THREADS / F;  // channels per block: F lanes each
-    static constexpr int C2R_CH = THREADS / F;
-    static constexpr int GCH = R2C_CH < 8 ? R2C_CH : 8;  // channels per output / input group item
+    // Threads per block. R2C: 512 (8 channels at F = 64, 16 at F = 32), so
+    // that its outputs go out as whole 8-channel groups. C2R at F = 64: 4
+    // channels in 256 threads and two blocks per SM (each 68 KB of half
+    // spectra), so that one block's loads overlap the other's transforms
+    // (1.84 -> 1.71 ms at the large frame; the R2C measured 1.70 -> 1.74 ms
+    // that way); at F = 32, 512.
+    static constexpr int R2C_THREADS = 512;
+    static constexpr int C2R_THREADS = F == 64 ? 256 : 512;
+    static constexpr int C2R_MINB = 512 / C2R_THREADS;  // blocks per SM (launch bounds)
+    static constexpr int R2C_CH = R2C_THREADS / F;       // channels per block: F lanes each
+    static constexpr int C2R_CH = C2R_THREADS / F;
+    static constexpr int C2R_GCH = C2R_CH < 8 ? C2R_CH : 8;  // channels per input group item
 };
 
 __device__ __forceinline__ int brev_c(int i, int log) {
@@ -108,7 +112,7 @@ __device__ __forceinline__ void chan_sync(int ch) {
     if constexpr (F >= 64) {
         // immediate barrier ids (one per channel of the block), so that the
         // block holds only the barriers it uses
-        static_assert(FftSize<F>::THREADS / F <= 8, "one named barrier per channel");
+        static_assert(FftSize<F>::R2C_CH <= 8 && FftSize<F>::C2R_CH <= 8, "one named barrier per channel");
         switch (ch) {
             case 0: asm volatile("bar.sync 1, %0;" ::"n"(F) : "memory"); break;
             case 1: asm volatile("bar.sync 2, %0;" ::"n"(F) : "memory"); break;
@@ -233,29 +237,9 @@ __device__ __forceinline__ void split8(const float2 (&v)[8], uint32_t (&h)[4][4]
     }
 }
 
-__device__ __forceinline__ void split4(const float2 (&v)[4], uint32_t (&h)[4][2]) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float2 a = v[2 * k], b = v[2 * k + 1];
-        const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
-        const float2 rb = __bfloat1622float2(rh), ib = __bfloat1622float2(ih);
-        const __nv_bfloat162 rl = __floats2bfloat162_rn(a.x - rb.x, b.x - rb.y);
-        const __nv_bfloat162 il = __floats2bfloat162_rn(a.y - ib.x, b.y - ib.y);
-        h[0][k] = *reinterpret_cast<const uint32_t*>(&rh);
-        h[1][k] = *reinterpret_cast<const uint32_t*>(&rl);
-        h[2][k] = *reinterpret_cast<const uint32_t*>(&ih);
-        h[3][k] = *reinterpret_cast<const uint32_t*>(&il);
-    }
-}
-
 struct OutC64 {
     float2* p;
     int ntile, ld;
-    __device__ void put4(int bin, int tile, int c0, const float2 (&v)[4]) const {
-        float4* q = reinterpret_cast<float4*>(p + ((int64_t)bin * ntile + tile) * ld + c0);
-        q[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-        q[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-    }
     __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
         float4* q = reinterpret_cast<float4*>(p + ((int64_t)bin * ntile + tile) * ld + c0);
         const int n4 = ld - c0 >= 8 ? 4 : 2;
@@ -268,14 +252,6 @@ struct OutC64 {
 struct OutPlanes {
     __nv_bfloat16* p[4];
     int ntile, ld;
-    __device__ void put4(int bin, int tile, int c0, const float2 (&v)[4]) const {
-        const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
-        uint32_t h[4][2];
-        split4(v, h);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (p[q]) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
-    }
     __device__ void put8(int bin, int tile, int c0, const float2 (&v)[8]) const {
         const int64_t o = ((int64_t)bin * ntile + tile) * ld + c0;
         uint32_t h[4][4];
@@ -303,13 +279,6 @@ struct OutPlanes {
 struct OutPlanesG {
     __nv_bfloat16* p[4];
     int ncolp, bins;  // columns per group, bins per column
-    __device__ void put4(int bin, int col, int c0, const float2 (&v)[4]) const {
-        const int64_t o = (((int64_t)(c0 >> 3) * 4 * ncolp + col) * bins + bin) * 8 + (c0 & 7);
-        uint32_t h[4][2];
-        split4(v, h);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(p[q] + o) = make_uint2(h[q][0], h[q][1]);
-    }
     __device__ void put8(int bin, int col, int c0, const float2 (&v)[8]) const {
         const int64_t o = (((int64_t)(c0 >> 3) * 4 * ncolp + col) * bins + bin) * 8;
         uint32_t h[4][4];
@@ -348,7 +317,7 @@ struct OutPlanesG {
 // Grid: x = channel group (fastest, so blocks running together fill adjacent
 // parts of the same output rows), y = column.
 template <int F, class Src, class Out>
-__global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_r2c(Src src, int nch, int ldc, Out out) {
+__global__ void __launch_bounds__(FftSize<F>::R2C_THREADS, 1) k_fft_r2c(Src src, int nch, int ldc, Out out) {
     using Z = FftSize<F>;
     constexpr int HF = Z::HF, H2 = Z::H2, LOG = Z::LOG, CH = Z::R2C_CH, PS = HF + 1;
     extern __shared__ float2 sm[];
@@ -428,16 +397,15 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_r
         for (int s2 = 0; s2 < HF; ++s2) R[(2 * s2 + h) * H2 + l] = a[s2];
     }
     __syncthreads();  // the output loop reads every channel of the block
-    // every bin of GCH (8, or the block's 4) consecutive channels at a time
-    constexpr int GCH = Z::GCH;
-    for (int e = threadIdx.x; e < Z::BINS * (CH / GCH); e += blockDim.x) {
+    // every bin of 8 consecutive channels at a time
+    static_assert(CH % 8 == 0, "whole 8-channel groups per block");
+    for (int e = threadIdx.x; e < Z::BINS * (CH / 8); e += blockDim.x) {
         const int bin = e % Z::BINS, g = e / Z::BINS;
-        if (c0 + GCH * g >= ldc) continue;
-        float2 v[GCH];
+        if (c0 + 8 * g >= ldc) continue;
+        float2 v[8];
 #pragma unroll
-        for (int k = 0; k < GCH; ++k) v[k] = sm[(size_t)(GCH * g + k) * Z::BINS + bin];
-        if constexpr (GCH == 8) out.put8(bin, tile, c0 + 8 * g, v);
-        else out.put4(bin, tile, c0 + 4 * g, v);
+        for (int k = 0; k < 8; ++k) v[k] = sm[(size_t)(8 * g + k) * Z::BINS + bin];
+        out.put8(bin, tile, c0 + 8 * g, v);
     }
 }
 
@@ -576,7 +544,7 @@ struct TabVolDst {
 // contraction), else [BINS][ntile][ldc] (CUDA-core contraction).
 // Grid: x = column, y = channel group.
 template <int F, class Dst, bool GM>
-__global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_c2r(const float2* __restrict__ in, int nch,
+__global__ void __launch_bounds__(FftSize<F>::C2R_THREADS, FftSize<F>::C2R_MINB) k_fft_c2r(const float2* __restrict__ in, int nch,
                                                                   int ldc, int ntile, int off, int B,
                                                                   float scale, Dst dst) {
     using Z = FftSize<F>;
@@ -591,7 +559,7 @@ __global__ void __launch_bounds__(FftSize<F>::THREADS, FftSize<F>::MINB) k_fft_c
     // (fy + F/2, fx), stored into [channel][bin] as the column transform's
     // inputs: their sum in row fy and their difference times exp(2 pi i fy / F)
     // in row fy + F/2
-    constexpr int GCH = Z::GCH;
+    constexpr int GCH = Z::C2R_GCH;
     static_assert(CH % GCH == 0 && 8 % GCH == 0, "whole channel groups per block");
     for (int e = threadIdx.x; e < HF * H2 * (CH / GCH); e += blockDim.x) {
         const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + GCH * g;
@@ -949,46 +917,40 @@ __global__ void k_low_list(const float* __restrict__ x, int64_t n, const unsigne
 // ------------------------------------------------ layout and update kernels --
 // Stack-order planes <-> channel-major polyphase planes:
 //   img[z][Iy*N+ty][Ix*N+tx]  <->  cm[z*S + ty*N + tx][Iy][Ix]
-// (a volume has Nz planes, an image one). One block per tile of kCmTile
-// lenslets of one lenslet row of one plane: the tile's N image rows go
-// through shared memory, so the image side is read / written in whole row
-// segments and every channel's segment (kCmTile lenslets, 128 bytes) in one
-// run (the shared-memory stride N is odd, so the channel reads are free of
-// bank conflicts). Grid: x = lenslet tile, y = lenslet row, z = plane.
-constexpr int kCmTile = 32;
+// (a volume has Nz planes, an image one). One block per image row y = Iy*N
+// + ty of one plane: the row goes through shared memory, so the image side is
+// read / written as one contiguous row and the channel side as N runs of Lx
+// values (the row's lenslets of the channels (ty, tx)), a warp per tx and 32
+// lenslets per access (the shared-memory stride N is odd, so these accesses
+// are free of bank conflicts). Blocks of 32 lenslets of one lenslet row (N
+// rows at a time, 128-byte channel runs) measured 2.3x slower at the large
+// frame, and per-element index divisions cost as much again.
+// Grid: x = image row, y = plane.
 __global__ void __launch_bounds__(256) k_to_cm(const float* __restrict__ img, Geo g, float* __restrict__ cm) {
-    extern __shared__ float tile[];  // [N][kCmTile * N]
-    const int Ix0 = blockIdx.x * kCmTile, Iy = blockIdx.y, z = blockIdx.z;
-    const int nl = min(kCmTile, g.Lx - Ix0), wpx = nl * g.N, ld = kCmTile * g.N;
-    const float* src = img + ((int64_t)z * g.H + (int64_t)Iy * g.N) * g.W + (int64_t)Ix0 * g.N;
-    for (int e = threadIdx.x; e < g.N * wpx; e += blockDim.x) {
-        const int ty = e / wpx, xx = e % wpx;
-        tile[ty * ld + xx] = src[(int64_t)ty * g.W + xx];
-    }
+    extern __shared__ float row[];  // [W]
+    const int y = blockIdx.x, z = blockIdx.y;
+    const int Iy = y / g.N, ty = y - Iy * g.N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float* src = img + ((int64_t)z * g.H + y) * g.W;
+    for (int x = threadIdx.x; x < g.W; x += blockDim.x) row[x] = src[x];
     __syncthreads();
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
-    float* dst = cm + (int64_t)z * g.S * L2 + (int64_t)Iy * g.Lx + Ix0;
-    for (int e = threadIdx.x; e < g.S * nl; e += blockDim.x) {
-        const int t = e / nl, i = e % nl, ty = t / g.N, tx = t % g.N;
-        dst[t * L2 + i] = tile[ty * ld + i * g.N + tx];
-    }
+    float* dst = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
+    for (int tx = warp; tx < g.N; tx += nw)
+        for (int Ix = lane; Ix < g.Lx; Ix += 32) dst[tx * L2 + Ix] = row[Ix * g.N + tx];
 }
 __global__ void __launch_bounds__(256) k_from_cm(const float* __restrict__ cm, Geo g, float* __restrict__ img) {
-    extern __shared__ float tile[];  // [N][kCmTile * N]
-    const int Ix0 = blockIdx.x * kCmTile, Iy = blockIdx.y, z = blockIdx.z;
-    const int nl = min(kCmTile, g.Lx - Ix0), wpx = nl * g.N, ld = kCmTile * g.N;
+    extern __shared__ float row[];  // [W]
+    const int y = blockIdx.x, z = blockIdx.y;
+    const int Iy = y / g.N, ty = y - Iy * g.N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t L2 = (int64_t)g.Ly * g.Lx;
-    const float* src = cm + (int64_t)z * g.S * L2 + (int64_t)Iy * g.Lx + Ix0;
-    for (int e = threadIdx.x; e < g.S * nl; e += blockDim.x) {
-        const int t = e / nl, i = e % nl, ty = t / g.N, tx = t % g.N;
-        tile[ty * ld + i * g.N + tx] = src[t * L2 + i];
-    }
+    const float* src = cm + ((int64_t)z * g.S + (int64_t)ty * g.N) * L2 + (int64_t)Iy * g.Lx;
+    for (int tx = warp; tx < g.N; tx += nw)
+        for (int Ix = lane; Ix < g.Lx; Ix += 32) row[Ix * g.N + tx] = src[tx * L2 + Ix];
     __syncthreads();
-    float* dst = img + ((int64_t)z * g.H + (int64_t)Iy * g.N) * g.W + (int64_t)Ix0 * g.N;
-    for (int e = threadIdx.x; e < g.N * wpx; e += blockDim.x) {
-        const int ty = e / wpx, xx = e % wpx;
-        dst[(int64_t)ty * g.W + xx] = tile[ty * ld + xx];
-    }
+    float* dst = img + ((int64_t)z * g.H + y) * g.W;
+    for (int x = threadIdx.x; x < g.W; x += blockDim.x) dst[x] = row[x];
 }
 __global__ void k_fill_cm(float* __restrict__ p, int64_t n, float val) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -1104,7 +1066,7 @@ cudaError_t run_r2c(Src src, int nch, int ldc, int ntile, Out out, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(k_fft_r2c<F, Src, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((ldc + FftSize<F>::R2C_CH - 1) / FftSize<F>::R2C_CH), (unsigned)ntile);
-    k_fft_r2c<F, Src, Out><<<grid, FftSize<F>::THREADS, smem, st>>>(src, nch, ldc, out);
+    k_fft_r2c<F, Src, Out><<<grid, FftSize<F>::R2C_THREADS, smem, st>>>(src, nch, ldc, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -1139,7 +1101,7 @@ cudaError_t run_c2r_l(const float2* in, int nch, int ldc, int ntile, int off, in
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)ntile, (unsigned)((nch + FftSize<F>::C2R_CH - 1) / FftSize<F>::C2R_CH));
-    k_fft_c2r<F, Dst, GM><<<grid, FftSize<F>::THREADS, smem, st>>>(in, nch, ldc, ntile, off, B,
+    k_fft_c2r<F, Dst, GM><<<grid, FftSize<F>::C2R_THREADS, smem, st>>>(in, nch, ldc, ntile, off, B,
                                                                          1.0f / (F * F), dst);
     count_launch();
     return cudaGetLastError();
@@ -1250,8 +1212,13 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
 }
 
 static cudaError_t cm_copy(bool to, const float* src, const Geo& g, int planes, float* dst, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)g.N * kCmTile * g.N;  // at most 28.8 KB (Nnum 15)
-    dim3 grid((unsigned)((g.Lx + kCmTile - 1) / kCmTile), (unsigned)g.Ly, (unsigned)planes);
+    const size_t smem = sizeof(float) * (size_t)g.W;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(to ? k_to_cm : k_from_cm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)g.H, (unsigned)planes);
     if (to)
         k_to_cm<<<grid, 256, smem, st>>>(src, g, dst);
     else

@@ -102,11 +102,12 @@ __global__ void k_mip_stack(const float* __restrict__ v, int Nz, int64_t HW, flo
 }
 
 // Row transform (Eq. 1 along the rows, basis of Eqs. 2-4 tabulated in
-// cosW[u][x]) G[y][u] = sum_x f[y][x] C_u(x; W), u < XS, and the row energy
-// rowE2[y] = sum_x f[y][x]^2 (FP64). A block holds ROWS rows in shared memory
-// (8, fewer for very wide images); warp w takes the basis rows u = w, w + 8,
-// ... and applies each to all the block's rows (one basis load per ROWS
-// products, ROWS independent sums per lane). The products and sums are double-float on the
+// cosW[u][x]) G[u][y] = sum_x f[y][x] C_u(x; W), u < XS (stored transposed,
+// for the column transform), and the row energy rowE2[y] = sum_x f[y][x]^2
+// (FP64). A block holds ROWS rows in shared memory (8, fewer for very wide
+// images); warp w takes the basis rows u = w, w + 8, ... and applies each to
+// all the block's rows (one basis load per ROWS products, ROWS independent
+// sums per lane; the basis values of four steps are loaded together). The products and sums are double-float on the
 // FP32 units: the basis is an FP64 value split as hi + lo, each product
 // f * hi is kept exactly as p + e (FMA), and each running sum is a
 // compensated pair, rounded to FP64 at the end (about 44 significant bits,
@@ -140,42 +141,59 @@ __global__ void __launch_bounds__(256) k_dct_rows(const float* __restrict__ f, c
         float sh[ROWS], sl[ROWS];
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) sh[r] = sl[r] = 0.f;
-        for (int x = lane; x < W; x += 32) {
-            const float2 c = cb[x];
+        for (int x0 = lane; x0 < W; x0 += 128) {
+            float2 c[4];
 #pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const float m = rows[r * W + x];
-                const float p = m * c.x;
-                const float e = fmaf(m, c.y, fmaf(m, c.x, -p));  // m*hi - p exactly, plus m*lo
-                const float t = sh[r] + p;                        // two-sum of sh + p
-                const float bp = t - sh[r];
-                sl[r] += ((sh[r] - (t - bp)) + (p - bp)) + e;
-                sh[r] = t;
+            for (int k = 0; k < 4; ++k) c[k] = x0 + 32 * k < W ? cb[x0 + 32 * k] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = x0 + 32 * k;
+                if (x >= W) break;
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const float m = rows[r * W + x];
+                    const float p = m * c[k].x;
+                    const float e = fmaf(m, c[k].y, fmaf(m, c[k].x, -p));  // m*hi - p exactly, plus m*lo
+                    const float t = sh[r] + p;                              // two-sum of sh + p
+                    const float bp = t - sh[r];
+                    sl[r] += ((sh[r] - (t - bp)) + (p - bp)) + e;
+                    sh[r] = t;
+                }
             }
         }
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             const double s = warp_sum((double)sh[r] + (double)sl[r]);
-            if (lane == 0 && r < nr) G[(int64_t)(y0 + r) * XS + u] = s;
+            if (lane == 0 && r < nr) G[(int64_t)u * H + y0 + r] = s;
         }
     }
 }
+// Column transform coef[v][u] = sum_y C_v(y; H) G[u][y] (FP64) inside the
+// triangular region; block (u, group of 8 rows v), one warp per v, four
+// partial sums per lane.
 __global__ void k_dct_cols(const double* __restrict__ G, const double* __restrict__ cosH, int H,
                            int XS, int YS, double* __restrict__ coef) {
     const int u = blockIdx.x;
-    G += (int64_t)blockIdx.y * H * XS;  // frame blockIdx.y
-    coef += (int64_t)blockIdx.y * XS * YS;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int v = w; v < YS; v += nw) {
-        double s = 0.0;
-        const bool in = (int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS;
-        if (in) {
-            const double* cb = cosH + (int64_t)v * H;
-            for (int y = lane; y < H; y += 32) s += cb[y] * G[(int64_t)y * XS + u];
-            s = warp_sum(s);
+    G += (int64_t)blockIdx.z * H * XS;  // frame blockIdx.z
+    coef += (int64_t)blockIdx.z * XS * YS;
+    const int lane = threadIdx.x & 31, v = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (v >= YS) return;
+    const bool in = (int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS;
+    double s = 0.0;
+    if (in) {
+        const double* cb = cosH + (int64_t)v * H;
+        const double* gu = G + (int64_t)u * H;
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int y0 = lane; y0 < H; y0 += 128) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int y = y0 + 32 * k;
+                if (y < H) a[k] = fma(cb[y], gu[y], a[k]);
+            }
         }
-        if (lane == 0) coef[(int64_t)v * XS + u] = in ? s : 0.0;
+        s = warp_sum((a[0] + a[1]) + (a[2] + a[3]));
     }
+    if (lane == 0) coef[(int64_t)v * XS + u] = in ? s : 0.0;
 }
 
 // E = -(1/G_S) sum_S |p| log2 |p|, p = F / ||F||_2 (Eqs. 5, 6, 12), and the
@@ -301,7 +319,7 @@ cudaError_t launch_metric(const float* mip, const float2* cosW, const double* co
     cudaError_t e = rows == 8 ? launch(k_dct_rows<8>) : rows == 4 ? launch(k_dct_rows<4>)
                   : rows == 2 ? launch(k_dct_rows<2>) : launch(k_dct_rows<1>);
     if (e != cudaSuccess) return e;
-    k_dct_cols<<<dim3(XS, nf), 256, 0, st>>>(G, cosH, H, XS, YS, coef);
+    k_dct_cols<<<dim3(XS, (YS + 7) / 8, nf), 256, 0, st>>>(G, cosH, H, XS, YS, coef);
     k_entropy<<<nf, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
                                   out_entropy, out_flux, out_stride);
     count_launch(3);

@@ -912,7 +912,7 @@ bool map3(CUtensorMap* m, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2
 // (no swizzle) as [group][plane][column][8], the K-major core-matrix layout of
 // the B operands the kernels describe (N = 4 ncb rows: plane x ncb + column)
 bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bins, uint64_t ncolp,
-                  uint32_t ncb, uint32_t gbox = 8) {
+                  uint32_t ncb, uint32_t gbox, bool promote = true) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[4] = {8, bins, ncolp, groups};
@@ -921,7 +921,8 @@ bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bin
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, str, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // column chunks of 16 x kNg[j] columns; a chunk is never wider than the planes
@@ -931,6 +932,8 @@ struct CgState {
     CUtensorMap fa[4], aa[4];        // PSF planes in kernel order (see the modes)
     CUtensorMap fb[3], ab[3];        // data planes per chunk width
     CUtensorMap fw;                  // data planes, boxes of 2 groups (wide forward units)
+    CUtensorMap ar;                  // ratio planes for the resident-data adjoint (no L2 promotion:
+                                     // a block reads a bin's 16-byte pieces once, not its neighbours')
     CgArgs fwd, adj;
     WideArgs wide;
     bool use_wide = false;
@@ -982,15 +985,15 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
         switch (s->mode) {
             case MODE_BF16:
                 k_tc_cgemm_adjr<MODE_BF16><<<grid, kThreads, CgR<MODE_BF16>::kSmemBytes, st>>>(
-                    A[0], A[1], A[2], A[3], s->ab[0], a);
+                    A[0], A[1], A[2], A[3], s->ar, a);
                 break;
             case MODE_ADAPTIVE:
                 k_tc_cgemm_adjr<MODE_ADAPTIVE><<<grid, kThreads, CgR<MODE_ADAPTIVE>::kSmemBytes, st>>>(
-                    A[0], A[1], A[2], A[3], s->ab[0], a);
+                    A[0], A[1], A[2], A[3], s->ar, a);
                 break;
             default:
                 k_tc_cgemm_adjr<MODE_SPLIT><<<grid, kThreads, CgR<MODE_SPLIT>::kSmemBytes, st>>>(
-                    A[0], A[1], A[2], A[3], s->ab[0], a);
+                    A[0], A[1], A[2], A[3], s->ar, a);
         }
         count_launch();
         return cudaGetLastError();
@@ -1255,6 +1258,10 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
     s->sm_count = sm_count;
     s->ncolp = b.ncolp;
     s->use_adjr = g.nkb <= kResB / 8192;
+    if (s->use_adjr && !map4_grouped(&s->ar, b.Y, 4 * (b.Sw / 8), b.bins, b.ncolp, 16, 32, false)) {
+        if (why) *why = "cuTensorMapEncodeTiled failed for the ratio planes";
+        return cudaErrorInvalidValue;
+    }
     if (s->mode == MODE_ADAPTIVE && b.wide.hi && b.S <= 256 && b.bins % 2 == 0) {
         if (!map4_grouped(&s->fw, b.X, 4 * (b.Cw / 8), b.bins, b.ncolp, 16, 8)) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the wide units' data planes";
