@@ -500,26 +500,32 @@ def run_lfd(args, rank, world, local):
     # end to end through the C ABI, one iteration per call: every step uploads
     # the step's input (the light-field image y) from pinned host memory and
     # reads back its result (the entropy and flux of the new iterate); the
-    # volume is the iteration's state and stays in device memory
+    # volume is the iteration's state and stays in the context (lfd_rl_load
+    # before the first step and lfd_rl_store after the last are timed too)
     e2e = None
     e2e_rt = None
     if not args.no_e2e:
         y_h = torch.from_numpy(y).pin_memory()
         v.fill_(1.0)
-        lfd.lfd_rl_iterate(ctx, y_h, v, 1)   # warm the staging buffers
+        lfd.lfd_rl_load(ctx, v)
+        lfd.lfd_rl_step(ctx, y_h, 1)          # warm the staging buffers and graphs
         v.fill_(1.0)
         torch.cuda.synchronize()
         dist_barrier(world)
         t0 = time.perf_counter()
+        lfd.lfd_rl_load(ctx, v)
         for _ in range(steps):
-            _, _, ent_k, _ = lfd.lfd_rl_iterate(ctx, y_h, v, 1)
+            ent_k, flux_k = lfd.lfd_rl_step(ctx, y_h, 1)
+        lfd.lfd_rl_store(ctx, v)
+        torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         dist_barrier(world)
         t_e2e = dist_max(t_e2e, world, dev)
         e2e = {"value": aggregate(steps, world, t_e2e), "unit": "RL iterations/s",
                "h2d_bytes_per_step": int(y_h.numel() * 4), "d2h_bytes_per_step": 16,
-               "step": "lfd_rl_iterate(y in pinned host memory, v in device memory, n=1); "
-                       "reads back the iterate's entropy and flux"}
+               "step": "lfd_rl_step(y in pinned host memory, n=1) on the resident iterate; reads back "
+                       "the iterate's entropy and flux (lfd_rl_load of v^0 before the first step and "
+                       "lfd_rl_store of the result after the last inside the timed region)"}
         # the same with the whole volume through host memory every iteration
         v_h = torch.ones((g.nz, g.H, g.W)).pin_memory()
         lfd.lfd_rl_iterate(ctx, y_h, v_h, 1)

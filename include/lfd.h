@@ -170,6 +170,32 @@ lfd_status lfd_rl_iterate(lfd_ctx* ctx, const float* y, float* v, int n,
                           int stop_at_predicted, int* iters_done, int* predicted,
                           double* entropy_hist, double* flux_hist, void* cuda_stream);
 
+/* RL iterations on an iterate that stays in the context between calls, for a
+ * caller that steps the deconvolution itself (e.g. one iteration at a time,
+ * watching the entropy of Section 2.2 to decide when to stop): the volume is
+ * repacked into the context's layout once, not on every call as with
+ * lfd_rl_iterate.
+ *   lfd_rl_load(ctx, v)       resident iterate <- v [Nz][H][W] (host or device)
+ *   lfd_rl_step(ctx, y, n, entropy_hist, flux_hist)
+ *                             n >= 1 RL iterations (model above) of the resident
+ *                             iterate with the light-field image y [H][W] (host
+ *                             or device; read by this call only); entropy_hist
+ *                             and flux_hist (host arrays of n doubles, may be
+ *                             NULL) get E_k and sum(H^T1 * v^k) of each
+ *                             iteration. Synchronises the stream.
+ *   lfd_rl_store(ctx, v)      v [Nz][H][W] (host or device) <- the resident
+ *                             iterate; with a host v the stream is synchronised.
+ * The resident iterate is the one of the lfd_split_* calls: lfd_split_load and
+ * lfd_rl_load are interchangeable. lfd_forward, lfd_rl_iterate and
+ * lfd_rl_iterate_batch reuse its buffers (after them lfd_rl_load is needed
+ * again). Frame 0 of a context made for several frames.
+ * Errors: LFD_EINVAL (NULL arguments, n < 1, no iterate loaded), LFD_ECUDA,
+ * LFD_ETIMEDOUT (a tensor-core kernel gave up waiting). */
+lfd_status lfd_rl_load(lfd_ctx* ctx, const float* v, void* cuda_stream);
+lfd_status lfd_rl_step(lfd_ctx* ctx, const float* y, int n, double* entropy_hist, double* flux_hist,
+                       void* cuda_stream);
+lfd_status lfd_rl_store(lfd_ctx* ctx, float* v, void* cuda_stream);
+
 /* lfd_rl_iterate for nframes frames that share the context's PSF and sensor
  * shape (e.g. a time-lapse), all advanced together: every stage of an
  * iteration is one launch over all frames, and the iteration is replayed as a

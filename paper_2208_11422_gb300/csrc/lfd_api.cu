@@ -88,6 +88,9 @@ std::vector<double> dct_table(int n, int Z) {
 
 namespace {
 
+lfd_status rl_step(lfd_ctx* ctx, const float* y, int n, double* entropy_hist, double* flux_hist,
+                   cudaStream_t ust);
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -874,6 +877,28 @@ lfd_status lfd_split_store(lfd_ctx* ctx, float* v, int previous, void* cuda_stre
     return LFD_OK;
 }
 
+lfd_status lfd_rl_load(lfd_ctx* ctx, const float* v, void* cuda_stream) {
+    return lfd_split_load(ctx, v, cuda_stream);
+}
+
+lfd_status lfd_rl_store(lfd_ctx* ctx, float* v, void* cuda_stream) {
+    return lfd_split_store(ctx, v, 0, cuda_stream);
+}
+
+lfd_status lfd_rl_step(lfd_ctx* ctx, const float* y, int n, double* entropy_hist, double* flux_hist,
+                       void* cuda_stream) {
+    if (!ctx) return LFD_EINVAL;
+    if (!y || n < 1) {
+        ctx->err = "invalid argument (NULL image or n < 1)";
+        return LFD_EINVAL;
+    }
+    if (ctx->split_cur < 0) {
+        ctx->err = "no iterate loaded (lfd_rl_load)";
+        return LFD_EINVAL;
+    }
+    return rl_step(ctx, y, n, entropy_hist, flux_hist, (cudaStream_t)cuda_stream);
+}
+
 lfd_status lfd_quality_mip(lfd_ctx* ctx, const float* mip, double* entropy, void* cuda_stream) {
     if (!ctx) return LFD_EINVAL;
     if (!mip || !entropy) {
@@ -1188,6 +1213,75 @@ lfd_status rl_run(lfd_ctx* ctx, int nf, const float* y, float* v, int n, int sto
             for (int k = 0; k < n; ++k) flux_hist[(size_t)f * n + k] = k < ran_f[f] ? Ff[k] : NAN;
         if (iters_done) iters_done[f] = done[f];
         if (predicted) predicted[f] = lfd_predict_stop(Ef, ran_f[f]);
+    }
+    return LFD_OK;
+}
+
+// n iterations of the resident iterate (buffer ctx->split_cur, frame 0) with
+// the image y; leaves the result resident and the per-iteration entropy and
+// flux in the host arrays (may be null)
+lfd_status rl_step(lfd_ctx* ctx, const float* y, int n, double* entropy_hist, double* flux_hist,
+                   cudaStream_t ust) {
+    const Geo& g = ctx->g;
+    const bool prof = ctx->prof.on;
+    const bool graphs = ctx->opt.use_graph && !prof;
+    cudaStream_t st = ctx->wstream;
+    LFD_CK(cudaEventRecord(ctx->ev_in, ust));
+    LFD_CK(cudaStreamWaitEvent(st, ctx->ev_in, 0));
+    if ((int64_t)n > (int64_t)ctx->host_hist_n * ctx->mf || !ctx->host_hist) {
+        if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+        ctx->host_hist = nullptr;
+        LFD_CK(cudaMallocHost((void**)&ctx->host_hist, 2 * sizeof(double) * (size_t)n * ctx->mf));
+        ctx->host_hist_n = n;
+    }
+    double* hE = ctx->host_hist;
+    double* hF = ctx->host_hist + n;
+    const float* yd = y;
+    if (!is_device_ptr(y)) {
+        LFD_TRY(ensure_stage(ctx, false));
+        LFD_CK(cudaMemcpyAsync(ctx->stage_img, y, (int64_t)g.H * g.W * sizeof(float), cudaMemcpyHostToDevice,
+                               st));
+        yd = ctx->stage_img;
+    }
+    if (ctx->fft)
+        LFD_CK(launch_poly_image_cm(yd, g, ctx->ycm, st));
+    else
+        LFD_CK(launch_poly_image(yd, g, ctx->ypoly, 0, nullptr, nullptr, st));
+    if (graphs) LFD_TRY(ensure_graphs(ctx, 1));
+    int cur = ctx->split_cur;
+    for (int k = 0; k < n; ++k) {
+        if (graphs) {
+            LFD_CK(cudaGraphLaunch(ctx->graph[cur], st));
+            count_launch(ctx->graph_launches);
+        } else {
+            LFD_TRY(iter_body(ctx, 1, cur, st, nullptr));
+        }
+        LFD_CK(cudaMemcpyAsync(hE + k, ctx->hist, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LFD_CK(cudaMemcpyAsync(hF + k, ctx->hist + ctx->mf, sizeof(double), cudaMemcpyDeviceToHost, st));
+        cur ^= 1;
+    }
+    ctx->split_cur = cur;
+    ctx->split_prev = 1;
+    LFD_CK(cudaEventRecord(ctx->ev_out, st));
+    LFD_CK(cudaStreamWaitEvent(ust, ctx->ev_out, 0));
+    LFD_CK(cudaStreamSynchronize(st));
+    if (ctx->cg) {
+        const int te = cgemm_error(ctx->cg);
+        if (te != 0) {
+            ctx->err = "tensor-core contraction gave up waiting (code " + std::to_string(te) + ")";
+            return LFD_ETIMEDOUT;
+        }
+    }
+    if (uses_tc(ctx)) {
+        const int te = tc_error(ctx);
+        if (te != 0) {
+            ctx->err = "tensor-core kernel gave up waiting (code " + std::to_string(te) + ")";
+            return LFD_ETIMEDOUT;
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        if (entropy_hist) entropy_hist[k] = hE[k];
+        if (flux_hist) flux_hist[k] = hF[k];
     }
     return LFD_OK;
 }

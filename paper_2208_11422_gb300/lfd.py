@@ -115,6 +115,9 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
     "lfd_quality_mip_static": (_I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
     "lfd_quality_mip": (_I, [_VP, _VP, ctypes.POINTER(_D), _VP]),
+    "lfd_rl_load": (_I, [_VP, _VP, _VP]),
+    "lfd_rl_step": (_I, [_VP, _VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
+    "lfd_rl_store": (_I, [_VP, _VP, _VP]),
     "lfd_split_load": (_I, [_VP, _VP, _VP]),
     "lfd_split_forward": (_I, [_VP, _VP, _VP]),
     "lfd_split_update": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
@@ -247,6 +250,25 @@ def lfd_rl_iterate(ctx, y, v, n: int, stop_at_predicted: bool = False, stream=No
                                  ctypes.byref(done), ctypes.byref(pred), ent, flux,
                                  _stream(stream)), ctx)
     return done.value, pred.value, list(ent), list(flux)
+
+
+def lfd_rl_load(ctx, v, stream=None):
+    """Puts the start volume v [Nz][H][W] into the context as its resident iterate."""
+    _check(load().lfd_rl_load(ctx, _ptr(v), _stream(stream)), ctx)
+
+
+def lfd_rl_step(ctx, y, n: int = 1, stream=None):
+    """n RL iterations of the resident iterate with image y; returns
+    (entropy list, flux list) of those iterations."""
+    ent = (_D * n)()
+    flux = (_D * n)()
+    _check(load().lfd_rl_step(ctx, _ptr(y), n, ent, flux, _stream(stream)), ctx)
+    return list(ent), list(flux)
+
+
+def lfd_rl_store(ctx, v, stream=None):
+    """Writes the resident iterate into v [Nz][H][W]."""
+    _check(load().lfd_rl_store(ctx, _ptr(v), _stream(stream)), ctx)
 
 
 def lfd_rl_iterate_batch(ctx, nframes: int, y, v, n: int, stop_at_predicted: bool = False,
