@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "tc_cgemm.h"
 #include "tc_ptx.h"
@@ -91,6 +92,8 @@ struct CgArgs {
     int* err;
     const int* lo_slot;  // adaptive lo planes: [bins][nkbc] compact slot, 0 = dropped
     int nkbc;            // 64-channel blocks of the PSF spectra
+    const int64_t* ustart;  // resident-data adjoint: first unit of each block (gridDim.x + 1
+                            // entries), or null for equal unit counts
 };
 
 template <bool ADJ, int NG, int MODE>
@@ -677,8 +680,8 @@ k_tc_cgemm_adjr(const __grid_constant__ CUtensorMap a0, const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_units = (int64_t)a.nbins * a.mtiles;
-    const int64_t u0 = (int64_t)blockIdx.x * n_units / gridDim.x;
-    const int64_t u1 = (int64_t)(blockIdx.x + 1) * n_units / gridDim.x;
+    const int64_t u0 = a.ustart ? a.ustart[blockIdx.x] : (int64_t)blockIdx.x * n_units / gridDim.x;
+    const int64_t u1 = a.ustart ? a.ustart[blockIdx.x + 1] : (int64_t)(blockIdx.x + 1) * n_units / gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -941,6 +944,8 @@ struct CgState {
     int sm_count = 0, ncolp = 16, nwidths = 1;
     int mode = MODE_SPLIT;
     int* err = nullptr;
+    int64_t* ustart = nullptr;  // cost-balanced unit ranges of the resident-data adjoint
+    int ugrid = 0;              // blocks they were made for
 };
 
 template <bool ADJ, int NG, int MODE>
@@ -981,6 +986,7 @@ cudaError_t launch(CgState* s, int ncol, cudaStream_t st) {
     if (ADJ && s->use_adjr && ncol <= 16) {
         a.nchunk = 1;
         const int grid = (int)std::min<int64_t>((int64_t)a.nbins * a.mtiles, s->sm_count);
+        a.ustart = grid == s->ugrid ? s->ustart : nullptr;
         const CUtensorMap* A = s->aa;
         switch (s->mode) {
             case MODE_BF16:
@@ -1262,6 +1268,39 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
         if (why) *why = "cuTensorMapEncodeTiled failed for the ratio planes";
         return cudaErrorInvalidValue;
     }
+    if (s->use_adjr && s->mode == MODE_ADAPTIVE) {
+        // Units with lo planes stream twice the PSF bytes of those without, and
+        // the lo tiles gather at the low frequencies, i.e. in a few ranges of
+        // the bin-major unit order: equal unit counts per block left the blocks
+        // holding those ranges running long after the others. Each block gets
+        // a contiguous range of about equal cost instead (cost of a unit: its
+        // PSF planes, 2 or 4 per k-block, plus its output, about half a plane).
+        const int64_t nu = (int64_t)g.nbins * g.mtiles;
+        const int grid = (int)std::min<int64_t>(nu, sm_count);
+        std::vector<int> slot((size_t)g.nbins * g.nkbc);
+        e = cudaMemcpy(slot.data(), g.lo_slot, slot.size() * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        std::vector<double> pre((size_t)nu + 1, 0.0);
+        for (int64_t u = 0; u < nu; ++u) {
+            const int bin = (int)(u / g.mtiles), mt = (int)(u % g.mtiles);
+            const int* ls = slot.data() + (size_t)bin * g.nkbc;
+            const bool lo = (2 * mt < g.nkbc && ls[2 * mt] != 0) || (2 * mt + 1 < g.nkbc && ls[2 * mt + 1] != 0);
+            pre[u + 1] = pre[u] + (lo ? 4.0 : 2.0) + 0.5;
+        }
+        std::vector<int64_t> st(grid + 1, 0);
+        int64_t u = 0;
+        for (int k = 1; k < grid; ++k) {
+            const double target = pre[nu] * k / grid;
+            while (u < nu && pre[u + 1] <= target) ++u;
+            st[k] = std::min(std::max(st[k - 1] + 1, u), nu - (grid - k));  // no block without units
+        }
+        st[grid] = nu;
+        if ((e = cudaMalloc(&s->ustart, sizeof(int64_t) * (grid + 1))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(s->ustart, st.data(), sizeof(int64_t) * (grid + 1), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return e;
+        s->ugrid = grid;
+    }
     if (s->mode == MODE_ADAPTIVE && b.wide.hi && b.S <= 256 && b.bins % 2 == 0) {
         if (!map4_grouped(&s->fw, b.X, 4 * (b.Cw / 8), b.bins, b.ncolp, 16, 8)) {
             if (why) *why = "cuTensorMapEncodeTiled failed for the wide units' data planes";
@@ -1313,6 +1352,7 @@ void cgemm_destroy(void* state) {
     CgState* s = static_cast<CgState*>(state);
     if (!s) return;
     if (s->err) cudaFree(s->err);
+    if (s->ustart) cudaFree(s->ustart);
     delete s;
 }
 
