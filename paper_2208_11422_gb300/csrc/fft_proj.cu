@@ -559,36 +559,50 @@ __global__ void __launch_bounds__(FftSize<F>::C2R_THREADS, FftSize<F>::C2R_MINB)
     // (fy + F/2, fx), stored into [channel][bin] as the column transform's
     // inputs: their sum in row fy and their difference times exp(2 pi i fy / F)
     // in row fy + F/2
+    // All of a thread's loads are issued before the first is used (their
+    // latency is paid once per block, not once per item).
     constexpr int GCH = Z::C2R_GCH;
     static_assert(CH % GCH == 0 && 8 % GCH == 0, "whole channel groups per block");
-    for (int e = threadIdx.x; e < HF * H2 * (CH / GCH); e += blockDim.x) {
-        const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + GCH * g;
-        const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
-        float2 v0[GCH], v1[GCH];
+    constexpr int NITEM = HF * H2 * (CH / GCH), NIT = (NITEM + Z::C2R_THREADS - 1) / Z::C2R_THREADS;
+    {
+        float4 w0[NIT][GCH / 2], w1[NIT][GCH / 2];
 #pragma unroll
-        for (int k = 0; k < GCH; ++k) v0[k] = v1[k] = make_float2(0.f, 0.f);
-        if (cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
-            const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
-                                    : in + (int64_t)tile * ldc + cg;
-            const int64_t bstride = GM ? 8 : (int64_t)ntile * ldc;  // float2 between bins
-            const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
-            const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
+        for (int it = 0; it < NIT; ++it) {
+            const int e = threadIdx.x + it * Z::C2R_THREADS;
+            const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + GCH * g;
+            const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
 #pragma unroll
-            for (int k = 0; k < GCH / 2; ++k) {
-                const float4 w0 = q0[k], w1 = q1[k];
-                v0[2 * k] = make_float2(w0.x, w0.y);
-                v0[2 * k + 1] = make_float2(w0.z, w0.w);
-                v1[2 * k] = make_float2(w1.x, w1.y);
-                v1[2 * k + 1] = make_float2(w1.z, w1.w);
+            for (int k = 0; k < GCH / 2; ++k) w0[it][k] = w1[it][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < NITEM && cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
+                const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
+                                        : in + (int64_t)tile * ldc + cg;
+                const int64_t bstride = GM ? 8 : (int64_t)ntile * ldc;  // float2 between bins
+                const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
+                const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
+#pragma unroll
+                for (int k = 0; k < GCH / 2; ++k) {
+                    w0[it][k] = q0[k];
+                    w1[it][k] = q1[k];
+                }
             }
         }
-        const float2 w = c_tw[fy * (64 / F)];  // conjugated below
 #pragma unroll
-        for (int k = 0; k < GCH; ++k) {
-            float2* dst = sm + (size_t)(GCH * g + k) * Z::BINS;
-            dst[b0] = cadd(v0[k], v1[k]);
-            const float2 d = csub(v0[k], v1[k]);
-            dst[b1] = make_float2(fmaf(d.x, w.x, d.y * w.y), fmaf(d.y, w.x, -d.x * w.y));
+        for (int it = 0; it < NIT; ++it) {
+            const int e = threadIdx.x + it * Z::C2R_THREADS;
+            if (e >= NITEM) break;
+            const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF);
+            const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
+            const float2 w = c_tw[fy * (64 / F)];  // conjugated below
+#pragma unroll
+            for (int k = 0; k < GCH; ++k) {
+                const float4 a = w0[it][k >> 1], b = w1[it][k >> 1];
+                const float2 v0 = (k & 1) ? make_float2(a.z, a.w) : make_float2(a.x, a.y);
+                const float2 v1 = (k & 1) ? make_float2(b.z, b.w) : make_float2(b.x, b.y);
+                float2* dst = sm + (size_t)(GCH * g + k) * Z::BINS;
+                dst[b0] = cadd(v0, v1);
+                const float2 d = csub(v0, v1);
+                dst[b1] = make_float2(fmaf(d.x, w.x, d.y * w.y), fmaf(d.y, w.x, -d.x * w.y));
+            }
         }
     }
     __syncthreads();
