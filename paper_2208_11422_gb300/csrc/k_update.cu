@@ -141,10 +141,17 @@ __global__ void __launch_bounds__(256) k_dct_rows(const float* __restrict__ f, c
         float sh[ROWS], sl[ROWS];
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) sh[r] = sl[r] = 0.f;
-        for (int x0 = lane; x0 < W; x0 += 128) {
-            float2 c[4];
+        // the basis values of the next four steps are loaded while the
+        // current ones are used
+        float2 c[4], cn[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) c[k] = x0 + 32 * k < W ? cb[x0 + 32 * k] : make_float2(0.f, 0.f);
+        for (int k = 0; k < 4; ++k) c[k] = lane + 32 * k < W ? cb[lane + 32 * k] : make_float2(0.f, 0.f);
+        for (int x0 = lane; x0 < W; x0 += 128) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int xn = x0 + 128 + 32 * k;
+                cn[k] = xn < W ? cb[xn] : make_float2(0.f, 0.f);
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int x = x0 + 32 * k;
@@ -160,6 +167,8 @@ __global__ void __launch_bounds__(256) k_dct_rows(const float* __restrict__ f, c
                     sh[r] = t;
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = cn[k];
         }
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
@@ -197,46 +206,74 @@ __global__ void k_dct_cols(const double* __restrict__ G, const double* __restric
 }
 
 // E = -(1/G_S) sum_S |p| log2 |p|, p = F / ||F||_2 (Eqs. 5, 6, 12), and the
-// flux total; single block, fixed reduction order.
-__global__ void k_entropy(const double* __restrict__ coef, const double* __restrict__ rowE2, int H,
-                          int XS, int YS, int l2_over_region, const double* __restrict__ flux_part,
-                          int nflux, double* __restrict__ out_entropy, double* __restrict__ out_flux,
-                          int out_stride) {
+// flux total, in two kernels. With N = ||F||_2 and, over the region S,
+// S1 = sum |F| log2 |F|, S2 = sum |F| (terms with F = 0 left out),
+//   sum_S p log2 p = (S1 - log2(N) S2) / N,
+// so the sums need no N and are split over kEntBlocks blocks per frame
+// (each a fixed slice: N^2 over the region, or the row energies of the whole
+// image; S1; S2; the flux partials), and one warp per frame adds the block
+// sums in a fixed order. All FP64.
+constexpr int kEntBlocks = 16;
+__global__ void k_entropy_part(const double* __restrict__ coef, const double* __restrict__ rowE2, int H,
+                               int XS, int YS, int l2_over_region, const double* __restrict__ flux_part,
+                               int nflux, double* __restrict__ part) {
     __shared__ double red[32];
-    {  // frame blockIdx.x
-        const int fr = blockIdx.x;
-        coef += (int64_t)fr * XS * YS;
-        rowE2 += (int64_t)fr * H;
-        if (flux_part) flux_part += (int64_t)fr * nflux;
-        out_entropy += (int64_t)fr * out_stride;
-        if (out_flux) out_flux += (int64_t)fr * out_stride;
-    }
+    const int fr = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+    coef += (int64_t)fr * XS * YS;
+    rowE2 += (int64_t)fr * H;
+    if (flux_part) flux_part += (int64_t)fr * nflux;
+    part += ((int64_t)fr * nb + b) * 4;
     const int n = XS * YS;
-    double a = 0.0;
-    if (l2_over_region) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a += coef[i] * coef[i];
-    } else {
-        for (int i = threadIdx.x; i < H; i += blockDim.x) a += rowE2[i];
-    }
-    const double norm = sqrt(block_sum(a, red));
-    double e = 0.0;
-    if (norm > 0.0) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int v = i / XS, u = i % XS;
-            if ((int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS) {
-                const double p = fabs(coef[i]) / norm;
-                if (p > 0.0) e += p * log2(p);
+    const int i0 = (int)((int64_t)b * n / nb), i1 = (int)((int64_t)(b + 1) * n / nb);
+    double a = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int v = i / XS, u = i % XS;
+        if ((int64_t)u * YS + (int64_t)v * XS < (int64_t)XS * YS) {
+            const double c = fabs(coef[i]);
+            if (l2_over_region) a += c * c;
+            if (c > 0.0) {
+                s1 += c * log2(c);
+                s2 += c;
             }
         }
     }
-    const double ent = block_sum(e, red);
-    double fl = 0.0;
-    for (int i = threadIdx.x; flux_part && i < nflux; i += blockDim.x) fl += flux_part[i];
-    const double flux = block_sum(fl, red);
-    if (threadIdx.x == 0) {
-        out_entropy[0] = norm > 0.0 ? -ent / (0.5 * (double)XS * (double)YS) : 0.0;
-        if (out_flux) out_flux[0] = flux;
+    if (!l2_over_region) {
+        const int y0 = (int)((int64_t)b * H / nb), y1 = (int)((int64_t)(b + 1) * H / nb);
+        for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) a += rowE2[y];
     }
+    double fl = 0.0;
+    if (flux_part) {
+        const int f0 = (int)((int64_t)b * nflux / nb), f1 = (int)((int64_t)(b + 1) * nflux / nb);
+        for (int i = f0 + threadIdx.x; i < f1; i += blockDim.x) fl += flux_part[i];
+    }
+    a = block_sum(a, red);
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    fl = block_sum(fl, red);
+    if (threadIdx.x == 0) {
+        part[0] = a;
+        part[1] = s1;
+        part[2] = s2;
+        part[3] = fl;
+    }
+}
+
+__global__ void k_entropy_fin(const double* __restrict__ part, int nb, int XS, int YS, int with_flux,
+                              double* __restrict__ out_entropy, double* __restrict__ out_flux, int out_stride) {
+    const int fr = blockIdx.x;
+    part += (int64_t)fr * nb * 4;
+    if (threadIdx.x != 0) return;
+    double a = 0.0, s1 = 0.0, s2 = 0.0, fl = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        a += part[4 * b];
+        s1 += part[4 * b + 1];
+        s2 += part[4 * b + 2];
+        fl += part[4 * b + 3];
+    }
+    const double norm = sqrt(a);
+    const double ent = norm > 0.0 ? (s1 - log2(norm) * s2) / norm : 0.0;
+    out_entropy[(int64_t)fr * out_stride] = norm > 0.0 ? -ent / (0.5 * (double)XS * (double)YS) : 0.0;
+    if (with_flux && out_flux) out_flux[(int64_t)fr * out_stride] = fl;
 }
 
 // r = y / (hv + eps) per pixel, 0 where hv + eps <= 0 (the ratio of an RL
@@ -320,9 +357,14 @@ cudaError_t launch_metric(const float* mip, const float2* cosW, const double* co
                   : rows == 2 ? launch(k_dct_rows<2>) : launch(k_dct_rows<1>);
     if (e != cudaSuccess) return e;
     k_dct_cols<<<dim3(XS, (YS + 7) / 8, nf), 256, 0, st>>>(G, cosH, H, XS, YS, coef);
-    k_entropy<<<nf, 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
-                                  out_entropy, out_flux, out_stride);
-    count_launch(3);
+    // the entropy's block sums go to the scratch past the frames' coefficients
+    static_assert(4 * kEntBlocks <= kMetricScratch, "entropy block sums exceed the metric scratch");
+    double* part = coef + (int64_t)nf * XS * YS;
+    k_entropy_part<<<dim3(kEntBlocks, nf), 256, 0, st>>>(coef, rowE2, H, XS, YS, l2_over_region, flux_part, nflux,
+                                                         part);
+    k_entropy_fin<<<nf, 32, 0, st>>>(part, kEntBlocks, XS, YS, flux_part != nullptr, out_entropy, out_flux,
+                                     out_stride);
+    count_launch(4);
     return cudaGetLastError();
 }
 

@@ -468,7 +468,7 @@ lfd_status lfd_create(const float* psf, int P, int Nnum, int Nz, int H, int W,
     CREATE_TRY(dalloc(ctx, &ctx->cosH, (int64_t)YS * g.H, false));
     CREATE_TRY(dalloc(ctx, &ctx->G, (int64_t)mf * g.H * XS, true));
     CREATE_TRY(dalloc(ctx, &ctx->rowE2, (int64_t)mf * g.H, true));
-    CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)mf * XS * YS, true));
+    CREATE_TRY(dalloc(ctx, &ctx->coef, (int64_t)mf * (XS * YS + kMetricScratch), true));
     CREATE_TRY(dalloc(ctx, &ctx->flux_part, (int64_t)mf * std::max<int64_t>(ctx->nflux, L2), true));
     CREATE_TRY(dalloc(ctx, &ctx->hist, 2LL * mf, true));
     CREATE_CK(cudaMallocHost((void**)&ctx->host_pinned, 4 * sizeof(double)));

@@ -242,6 +242,9 @@ cudaError_t launch_sum_doubles(const double* p, int64_t n, double* out, cudaStre
 // DCT entropy of nf frames' MIPs (frame-major arrays: mip H*W, G H*XS, rowE2 H,
 // coef XS*YS, flux_part nflux per frame); frame f writes out_entropy[f*out_stride]
 // and out_flux[f*out_stride]
+// launch_metric keeps kMetricScratch doubles per frame after the frames'
+// coefficients: coef must hold nf * (XS * YS + kMetricScratch) doubles
+constexpr int kMetricScratch = 64;
 cudaError_t launch_metric(const float* mip, const float2* cosW, const double* cosH,
                           int H, int W, int XS, int YS, int l2_over_region,
                           double* G, double* rowE2, double* coef,

@@ -165,7 +165,7 @@ int64_t job_layout(Job* j, char* base) {
     j->cosH = (double*)take(8 * (int64_t)j->YS * g.H);
     j->G = (double*)take(8 * (int64_t)g.H * j->XS);
     j->rowE2 = (double*)take(8 * (int64_t)g.H);
-    j->coef = (double*)take(8 * (int64_t)j->XS * j->YS);
+    j->coef = (double*)take(8 * ((int64_t)j->XS * j->YS + kMetricScratch));
     j->flux_part = (double*)take(8 * (int64_t)j->nflux);
     j->low = (int*)take(4 * vox);
     j->n_low = (int*)take(4);
