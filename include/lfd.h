@@ -101,7 +101,7 @@ typedef struct {
                              64-channel block) tiles whose largest hi value
                              reaches tau x the largest of all spectra; a dropped
                              lo part is below 2^-9 tau of that largest value.
-                             0 keeps every lo plane; default 2^-10; [0, 1)       */
+                             0 keeps every lo plane; default 2^-8; [0, 1)        */
     int contraction_cols; /* LFD_FFT on the tensor cores: the widest column chunk of
                              one contraction pass (16, 32 or 64 columns = frames x
                              tiles; every chunk streams the PSF spectra once); 0

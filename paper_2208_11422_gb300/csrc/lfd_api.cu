@@ -267,7 +267,7 @@ void lfd_default_options(lfd_options* opt) {
     opt->max_frames = 1;
     opt->use_graph = 1;
     opt->fft_size = 0;
-    opt->spectra_lo_tau = 0.0009765625f;  // 2^-10
+    opt->spectra_lo_tau = 0.00390625f;  // 2^-8
 }
 
 lfd_status lfd_region_size(int Nnum, int H, int W, double dML_um, double Q, double NA,

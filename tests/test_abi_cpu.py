@@ -93,6 +93,7 @@ def test_defaults():
     assert o.precision == lfd.LFD_FP32 and abs(o.eps - 1e-6) < 1e-12
     assert (o.dML_um, o.Q, o.NA, o.lambda_um) == (150.0, 40.0, 0.95, 0.525)
     assert o.l2_over_region == 1
+    assert o.spectra_lo_tau == 2.0 ** -8
 
 
 @pytest.mark.parametrize("N,H,W", [(5, 75, 75), (15, 615, 615), (15, 2025, 2025),

@@ -161,27 +161,31 @@ def test_fft_low_sensitivity_voxels_are_exact():
 
 def test_fft_adaptive_lo_planes_keep_split_bf16_accuracy():
     """Split BF16 keeps the PSF spectra's lo planes only where a (bin, 64-channel
-    block) tile reaches 2^-10 of the largest spectrum value: on the 2025 px
-    frame that drops more than half of them, and sampled projections stay
-    within the split-BF16 bound of the oracle, as with every lo plane kept."""
+    block) tile reaches tau of the largest spectrum value: on the 2025 px frame
+    2^-10 drops more than half of them and the default 2^-8 about two thirds,
+    and sampled projections stay within the split-BF16 bound of the oracle, as
+    with every lo plane kept."""
     from paper_2208_11422_gb300 import lfd
+    assert lfd.lfd_default_options().spectra_lo_tau == 2.0 ** -8
     g = synth.CONFIGS[2]
     psf = synth.make_psf(2)
     v = synth.beads(102, g.nz, g.H, g.W, g.beads, g.bead_radius, g.amp_lo).astype(np.float32)
     pix = synth.sample_indices(8, 128, (g.H, g.W))
     ref = oracle.forward_at(psf, g.nnum, v, pix)
     res = {}
-    for tau in (0.0, 2.0 ** -10):
+    for tau in (0.0, 2.0 ** -10, 2.0 ** -8):
         with Ctx(psf, g.nnum, g.H, g.W, variant="fft", precision="bf16x3", spectra_lo_tau=tau) as c:
             sp = lfd.lfd_get_spectra(c.ctx)
             hv = c.forward(v)
         res[tau] = (sp, rel_l2(hv[pix[:, 0], pix[:, 1]], ref))
         print("tau %g: spectra %s, sampled forward rel-L2 %.2e" % (tau, sp, res[tau][1]))
-    full, adapt = res[0.0][0], res[2.0 ** -10][0]
+    full, a10, a8 = res[0.0][0], res[2.0 ** -10][0], res[2.0 ** -8][0]
     assert full["lo_tiles_kept"] == full["lo_tiles"] > 0
-    assert 0 < adapt["lo_tiles_kept"] < 0.6 * adapt["lo_tiles"]
-    assert adapt["bytes"] < 0.85 * full["bytes"]
-    assert res[0.0][1] <= TOL_PROJ["bf16x3"] and res[2.0 ** -10][1] <= TOL_PROJ["bf16x3"]
+    assert 0 < a10["lo_tiles_kept"] < 0.6 * a10["lo_tiles"]
+    assert 0 < a8["lo_tiles_kept"] < a10["lo_tiles_kept"]
+    assert a8["bytes"] < a10["bytes"] < 0.85 * full["bytes"]
+    for tau in res:
+        assert res[tau][1] <= TOL_PROJ["bf16x3"]
 
 
 def test_fft_exact_correction_of_a_ratio_image():
