@@ -540,10 +540,12 @@ struct TabVolDst {
 //            extended by conjugate symmetry); the outputs go through shared
 //            memory so that dst sees consecutive j across lanes, one output
 //            row at a time.
-// Input: GM, the spectra group-major [ldc/8][ntile][BINS][8] (tensor-core
-// contraction), else [BINS][ntile][ldc] (CUDA-core contraction).
-// Grid: x = column, y = channel group.
-template <int F, class Dst, bool GM>
+// Input (LAYOUT): 0, [BINS][ntile][ldc] (CUDA-core contraction); the
+// tensor-core contraction's group-major outputs, 1 [ldc/8][ntile][BINS][8]
+// (forward) or 2 [ldc/8][BINS][ntile][8] (adjoint).
+// Grid: x = column, y = channel group (the blocks of one group that run
+// together read the columns of each bin together).
+template <int F, class Dst, int LAYOUT>
 __global__ void __launch_bounds__(FftSize<F>::C2R_THREADS, FftSize<F>::C2R_MINB) k_fft_c2r(const float2* __restrict__ in, int nch,
                                                                   int ldc, int ntile, int off, int B,
                                                                   float scale, Dst dst) {
@@ -574,9 +576,12 @@ __global__ void __launch_bounds__(FftSize<F>::C2R_THREADS, FftSize<F>::C2R_MINB)
 #pragma unroll
             for (int k = 0; k < GCH / 2; ++k) w0[it][k] = w1[it][k] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (e < NITEM && cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
-                const float2* base = GM ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
-                                        : in + (int64_t)tile * ldc + cg;
-                const int64_t bstride = GM ? 8 : (int64_t)ntile * ldc;  // float2 between bins
+                const float2* base =
+                    LAYOUT == 1   ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
+                    : LAYOUT == 2 ? in + ((int64_t)(cg >> 3) * Z::BINS * ntile + tile) * 8 + (cg & 7)
+                                  : in + (int64_t)tile * ldc + cg;
+                const int64_t bstride = LAYOUT == 1 ? 8 : LAYOUT == 2 ? (int64_t)ntile * 8
+                                                                      : (int64_t)ntile * ldc;  // float2 between bins
                 const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
                 const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
 #pragma unroll
@@ -1106,26 +1111,29 @@ cudaError_t r2c_grouped(const FftPlan& p, Src src, int nch, int ldc, int ntile,
     return p.F == 64 ? run_r2c<64>(src, nch, ldc, ntile, o, st) : run_r2c<32>(src, nch, ldc, ntile, o, st);
 }
 
-template <int F, bool GM, class Dst>
+template <int F, int LAYOUT, class Dst>
 cudaError_t run_c2r_l(const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
                       cudaStream_t st) {
     if (ldc % 8 != 0) return cudaErrorInvalidValue;  // whole 8-channel groups per row
     const size_t smem = fft_smem<F>(false);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fft_c2r<F, Dst, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)ntile, (unsigned)((nch + FftSize<F>::C2R_CH - 1) / FftSize<F>::C2R_CH));
-    k_fft_c2r<F, Dst, GM><<<grid, FftSize<F>::C2R_THREADS, smem, st>>>(in, nch, ldc, ntile, off, B,
-                                                                         1.0f / (F * F), dst);
+    k_fft_c2r<F, Dst, LAYOUT><<<grid, FftSize<F>::C2R_THREADS, smem, st>>>(in, nch, ldc, ntile, off, B,
+                                                                             1.0f / (F * F), dst);
     count_launch();
     return cudaGetLastError();
 }
-// gm: the spectra come group-major from the tensor-core contraction
+// tc: the spectra come group-major from the tensor-core contraction (the
+// forward's columns outer, the adjoint's bins outer), else complex64 from the
+// CUDA-core contraction
 template <int F, class Dst>
-cudaError_t run_c2r(bool gm, const float2* in, int nch, int ldc, int ntile, int off, int B, Dst dst,
-                    cudaStream_t st) {
-    return gm ? run_c2r_l<F, true>(in, nch, ldc, ntile, off, B, dst, st)
-              : run_c2r_l<F, false>(in, nch, ldc, ntile, off, B, dst, st);
+cudaError_t run_c2r(bool tc, bool adjoint, const float2* in, int nch, int ldc, int ntile, int off, int B,
+                    Dst dst, cudaStream_t st) {
+    if (!tc) return run_c2r_l<F, 0>(in, nch, ldc, ntile, off, B, dst, st);
+    return adjoint ? run_c2r_l<F, 2>(in, nch, ldc, ntile, off, B, dst, st)
+                   : run_c2r_l<F, 1>(in, nch, ldc, ntile, off, B, dst, st);
 }
 
 }  // namespace
@@ -1203,8 +1211,8 @@ cudaError_t fft_forward(const FftPlan& p, const Geo& g, const FftBuffers& b, int
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     HvDst dst{img_out, rcm, ycm, rimg, eps, g.N, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
               (int64_t)g.S * L2, (int64_t)g.H * g.W};
-    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, false, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, false, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
 }
 
 cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, int nf, const float* rcm,
@@ -1221,8 +1229,8 @@ cudaError_t fft_backward(const FftPlan& p, const Geo& g, const FftBuffers& b, in
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     VolDst dst{xcm, stack_out, g.N, g.S, g.H, g.W, g.Ly, g.Lx, p.B, p.tiles_x, p.ntile,
                (int64_t)g.C * L2, (int64_t)g.Nz * g.H * g.W};
-    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
-                     : run_c2r<32>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, true, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, true, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 static cudaError_t cm_copy(bool to, const float* src, const Geo& g, int planes, float* dst, cudaStream_t st) {
@@ -1296,8 +1304,8 @@ cudaError_t fft_forward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b,
     e = b.cg ? cgemm_forward(b.cg, ncol, st) : contract_fwd_all(p, g, b.Wf, b.Xh, b.Yh, ncol, st);
     if (e != cudaSuccess) return e;
     TabHvDst dst{fr, colf, col0, g.N, p.B, eps};
-    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
-                     : run_c2r<32>(b.cg != nullptr, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, false, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, false, b.Yh, g.S, p.Sf, ncol, 2 * p.h, p.B, dst, st);
 }
 
 cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b, const FrameCols* fr,
@@ -1309,8 +1317,8 @@ cudaError_t fft_backward_tab(const FftPlan& p, const Geo& g, const FftBuffers& b
     e = b.cg ? cgemm_adjoint(b.cg, ncol, st) : contract_adj_all(p, g, b.Wf, b.Yh, b.Xh, ncol, st);
     if (e != cudaSuccess) return e;
     TabVolDst dst{fr, colf, col0, g.N, g.S, p.B};
-    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
-                     : run_c2r<32>(b.cg != nullptr, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
+    return p.F == 64 ? run_c2r<64>(b.cg != nullptr, true, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st)
+                     : run_c2r<32>(b.cg != nullptr, true, b.Xh, g.C, p.Cf, ncol, 0, p.B, dst, st);
 }
 
 // one item per thread (no grid-stride tail), one flux partial per block

@@ -88,7 +88,7 @@ struct CgArgs {
     int nkb;           // k-blocks of 64 per unit
     int nrows;         // valid rows (S or C)
     int ld;            // row length of the output (Sf or Cf)
-    float2* out;       // [ld/8][ncol][bins][8] (group-major)
+    float2* out;       // forward [ld/8][ncol][bins][8], adjoint [ld/8][bins][ncol][8] (group-major)
     int* err;
     const int* lo_slot;  // adaptive lo planes: [bins][nkbc] compact slot, 0 = dropped
     int nkbc;            // 64-channel blocks of the PSF spectra
@@ -338,14 +338,21 @@ k_tc_cgemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUten
                         }
                     }
                     if (grow < a.nrows) {
-                        // group-major output [ld/8][ncol][bins][8]: the inverse
-                        // transform reads a column's bins of 8 rows as one run
-                        float2* o = a.out + (((int64_t)(grow >> 3) * a.ncol + col0) * a.nbins + bin) * 8 +
-                                    (grow & 7);
+                        // group-major outputs: forward [ld/8][ncol][bins][8] (the
+                        // inverse transform reads a column's bins of 8 rows as one
+                        // run), adjoint [ld/8][bins][ncol][8] (a unit's 16 columns
+                        // of a group are one 1 KB run, so its writes fill whole
+                        // lines; the inverse transform's blocks of one group read
+                        // the columns of a bin together)
+                        float2* o = ADJ ? a.out + (((int64_t)(grow >> 3) * a.nbins + bin) * a.ncol + col0) * 8 +
+                                              (grow & 7)
+                                        : a.out + (((int64_t)(grow >> 3) * a.ncol + col0) * a.nbins + bin) * 8 +
+                                              (grow & 7);
+                        const int64_t ts = ADJ ? 8 : (int64_t)a.nbins * 8;  // float2 between columns
 #pragma unroll
                         for (int t = 0; t < 16; ++t) {
                             if (col0 + t < a.ncol) {
-                                float* dst = reinterpret_cast<float*>(o + (int64_t)t * a.nbins * 8);
+                                float* dst = reinterpret_cast<float*>(o + t * ts);
                                 if (c0 == 0) *reinterpret_cast<float2*>(dst) = make_float2(re[t], im[t]);
                                 else red_add_v2(dst, re[t], im[t]);
                             }
@@ -866,11 +873,11 @@ k_tc_cgemm_adjr(const __grid_constant__ CUtensorMap a0, const __grid_constant__ 
                     im[t] = (__uint_as_float(x0[t]) + __uint_as_float(x1[t])) -
                             (__uint_as_float(x2[t]) + __uint_as_float(x3[t]));
             }
-            if (grow < a.nrows) {
-                float2* o = a.out + ((int64_t)(grow >> 3) * a.ncol * a.nbins + bin) * 8 + (grow & 7);
+            if (grow < a.nrows) {  // [ld/8][bins][ncol][8], as k_tc_cgemm<ADJ = true>
+                float2* o = a.out + ((int64_t)(grow >> 3) * a.nbins + bin) * a.ncol * 8 + (grow & 7);
 #pragma unroll
                 for (int t = 0; t < 16; ++t)
-                    if (t < a.ncol) o[(int64_t)t * a.nbins * 8] = make_float2(re[t], im[t]);
+                    if (t < a.ncol) o[t * 8] = make_float2(re[t], im[t]);
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);

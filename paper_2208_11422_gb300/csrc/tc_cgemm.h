@@ -45,7 +45,7 @@ struct CgemmBuffers {
     const __nv_bfloat16* X;   // [Cw/8][4 planes][ncolp][bins][8] volume spectra (forward input)
     const __nv_bfloat16* Y;   // [Sw/8][4 planes][ncolp][bins][8] ratio spectra (adjoint input)
     float2* Yout;             // [Sf/8][ncol][bins][8] forward output (group-major)
-    float2* Xout;             // [Cf/8][ncol][bins][8] adjoint output (group-major)
+    float2* Xout;             // [Cf/8][bins][ncol][8] adjoint output (group-major, columns inner)
     LoPlanes lo;              // adaptive lo planes (slot null otherwise)
     int max_cols;             // widest column chunk (16, 32 or 64); 0: up to 64
     WidePlanes wide;          // the forward's wide-unit copy (hi null: not used)
