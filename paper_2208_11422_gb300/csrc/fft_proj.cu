@@ -16,12 +16,13 @@
 //      [2h, F) for the convolution and [0, B) for the correlation.
 // The ratio r = y / (Hv + eps) is fused into the forward's C2R store.
 //
-// Transforms are radix-2 in registers: each lane holds one whole 32- or
-// 64-point 1-D transform (F/2 lanes per channel), with the channel's half
-// spectrum staged in shared memory between the row and column passes. The
-// contractions run on the tcgen05 tensor cores (split BF16 or BF16 PSF
-// spectra, tc_cgemm.cu) or, for LFD_FP32, on the CUDA cores in FP32 (below),
-// streaming the cached PSF spectra once per projection.
+// Transforms are radix-2 in registers: each F-point 1-D transform is split by
+// decimation in frequency over two lanes, each holding an F/2-point transform
+// (F lanes per channel), with the channel's half spectrum staged in shared
+// memory between the row and column passes. The contractions run on the
+// tcgen05 tensor cores (split BF16 or BF16 PSF spectra, tc_cgemm.cu) or, for
+// LFD_FP32, on the CUDA cores in FP32 (below), streaming the cached PSF
+// spectra once per projection.
 #include <algorithm>
 #include <cmath>
 #include <vector>
