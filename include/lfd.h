@@ -397,11 +397,18 @@ lfd_status lfd_get_spectra(const lfd_ctx* ctx, int64_t* bytes, int64_t* lo_tiles
  * piece holds voxels of one channel along one lenslet row or column in
  * increasing order within the piece and staging limits, that its PSF tile is
  * the voxel's (or its transposed copy), and the cost order. LFD_OK,
- * LFD_EINTERNAL on a violation, LFD_EINVAL for an invalid shape. */
+ * LFD_EINTERNAL on a violation, LFD_EINVAL for an invalid shape.
+ * lfd_selftest_balanced_ranges(seed, n, grid): host only; splits n seeded
+ * synthetic unit costs (stretches of units with and without lo planes, as in
+ * the adjoint contraction) into grid contiguous ranges the way the adjoint's
+ * blocks get theirs, and checks that they tile the units in order, that none
+ * is empty, and that none exceeds the mean by the largest unit cost. LFD_OK,
+ * LFD_EINTERNAL on a violation, LFD_EINVAL unless 1 <= grid <= n. */
 void lfd_debug_fail_allocs(int n);
 lfd_status lfd_selftest_bounded_wait(int64_t limit_ns, int* code);
 lfd_status lfd_selftest_freelist(int seed, int steps);
 lfd_status lfd_selftest_exact_runs(int seed, int Nnum, int Nz, int k, int L);
+lfd_status lfd_selftest_balanced_ranges(int seed, int n, int grid);
 
 /* Number of kernels the library has launched in this process (all contexts). */
 uint64_t lfd_launch_count(void);

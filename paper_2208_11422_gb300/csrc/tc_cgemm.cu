@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <random>
 #include <vector>
 
 #include "tc_cgemm.h"
@@ -935,6 +936,30 @@ bool map4_grouped(CUtensorMap* m, const void* ptr, uint64_t groups, uint64_t bin
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// Contiguous ranges of about equal cost: units st[k] .. st[k+1]-1 for block k
+// of `grid` (st[0] = 0, st[grid] = n), every block at least one unit when
+// n >= grid. Each boundary is placed where the running cost first passes
+// k / grid of the total, so a range exceeds total / grid by less than the
+// largest unit cost.
+std::vector<int64_t> balanced_ranges(const std::vector<double>& cost, int grid) {
+    const int64_t nu = (int64_t)cost.size();
+    std::vector<double> pre((size_t)nu + 1, 0.0);
+    for (int64_t u = 0; u < nu; ++u) pre[u + 1] = pre[u] + cost[u];
+    std::vector<int64_t> st((size_t)grid + 1, 0);
+    int64_t u = 0;
+    for (int k = 1; k < grid; ++k) {
+        const double target = pre[nu] * k / grid;
+        while (u < nu && pre[u + 1] <= target) ++u;
+        st[k] = std::min(std::max(st[k - 1] + 1, u), nu - (grid - k));  // no block without units
+    }
+    st[grid] = nu;
+    return st;
+}
+
+namespace {
+
 // column chunks of 16 x kNg[j] columns; a chunk is never wider than the planes
 constexpr int kNg[3] = {1, 2, 4};
 
@@ -1287,21 +1312,14 @@ cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::s
         std::vector<int> slot((size_t)g.nbins * g.nkbc);
         e = cudaMemcpy(slot.data(), g.lo_slot, slot.size() * sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return e;
-        std::vector<double> pre((size_t)nu + 1, 0.0);
+        std::vector<double> cost((size_t)nu);
         for (int64_t u = 0; u < nu; ++u) {
             const int bin = (int)(u / g.mtiles), mt = (int)(u % g.mtiles);
             const int* ls = slot.data() + (size_t)bin * g.nkbc;
             const bool lo = (2 * mt < g.nkbc && ls[2 * mt] != 0) || (2 * mt + 1 < g.nkbc && ls[2 * mt + 1] != 0);
-            pre[u + 1] = pre[u] + (lo ? 4.0 : 2.0) + 0.5;
+            cost[u] = (lo ? 4.0 : 2.0) + 0.5;
         }
-        std::vector<int64_t> st(grid + 1, 0);
-        int64_t u = 0;
-        for (int k = 1; k < grid; ++k) {
-            const double target = pre[nu] * k / grid;
-            while (u < nu && pre[u + 1] <= target) ++u;
-            st[k] = std::min(std::max(st[k - 1] + 1, u), nu - (grid - k));  // no block without units
-        }
-        st[grid] = nu;
+        const std::vector<int64_t> st = balanced_ranges(cost, grid);
         if ((e = cudaMalloc(&s->ustart, sizeof(int64_t) * (grid + 1))) != cudaSuccess) return e;
         if ((e = cudaMemcpy(s->ustart, st.data(), sizeof(int64_t) * (grid + 1), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
@@ -1364,3 +1382,35 @@ void cgemm_destroy(void* state) {
 }
 
 }  // namespace lfd
+
+// Host-only check of balanced_ranges on seeded synthetic unit costs shaped
+// like the adjoint's (runs of costly units with lo planes among cheaper ones):
+// the ranges tile 0 .. n-1 in order, none is empty when n >= grid, and none
+// exceeds total / grid by the largest unit cost or more.
+extern "C" lfd_status lfd_selftest_balanced_ranges(int seed, int n, int grid) {
+    if (n < 1 || grid < 1 || grid > n) return LFD_EINVAL;
+    std::mt19937_64 rng((uint64_t)seed);
+    std::vector<double> cost((size_t)n);
+    double total = 0.0, mx = 0.0;
+    int run = 0;
+    bool lo = false;
+    for (int u = 0; u < n; ++u) {
+        if (run == 0) {  // a stretch of units with or without lo planes
+            lo = rng() % 3 == 0;
+            run = 1 + (int)(rng() % 200);
+        }
+        --run;
+        cost[u] = (lo ? 4.0 : 2.0) + 0.5 + (double)(rng() % 100) * 1e-3;
+        total += cost[u];
+        mx = std::max(mx, cost[u]);
+    }
+    const std::vector<int64_t> st = lfd::balanced_ranges(cost, grid);
+    if ((int)st.size() != grid + 1 || st[0] != 0 || st[grid] != n) return LFD_EINTERNAL;
+    for (int k = 0; k < grid; ++k) {
+        if (st[k + 1] <= st[k]) return LFD_EINTERNAL;
+        double c = 0.0;
+        for (int64_t u = st[k]; u < st[k + 1]; ++u) c += cost[u];
+        if (c >= total / grid + mx) return LFD_EINTERNAL;
+    }
+    return LFD_OK;
+}

@@ -1,6 +1,7 @@
 // Split-BF16 complex contractions of the FFT variant on tcgen05 (tc_cgemm.cu).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "lfd_internal.h"
 
@@ -63,6 +64,10 @@ void cgemm_free_lo(LoPlanes* p);
 cudaError_t cgemm_build_wide(const CgemmBuffers& b, const LoPlanes& lo, cudaStream_t st, WidePlanes* out,
                              int64_t* bytes);
 void cgemm_free_wide(WidePlanes* p);
+
+// contiguous ranges of about equal total cost over units 0 .. cost.size()-1
+// for `grid` blocks: block k takes units [st[k], st[k+1]) (tc_cgemm.cu)
+std::vector<int64_t> balanced_ranges(const std::vector<double>& cost, int grid);
 
 cudaError_t cgemm_init(const CgemmBuffers& b, int sm_count, void** state, std::string* why);
 // ncol = frames x tiles of this call (<= ncolp)

@@ -138,6 +138,7 @@ _SIGS = {
     "lfd_selftest_bounded_wait": (_I, [ctypes.c_int64, ctypes.POINTER(_I)]),
     "lfd_selftest_freelist": (_I, [_I, _I]),
     "lfd_selftest_exact_runs": (_I, [_I, _I, _I, _I, _I]),
+    "lfd_selftest_balanced_ranges": (_I, [_I, _I, _I]),
     "lfd_server_default_options": (None, [ctypes.POINTER(lfd_server_options)]),
     "lfd_server_create": (_I, [ctypes.POINTER(lfd_server_options), ctypes.POINTER(_VP)]),
     "lfd_server_add_psf": (_I, [_VP, _VP, _I, _I, _I, _I, _I, ctypes.POINTER(_I)]),

@@ -80,6 +80,9 @@ def test_create_rejects_null_psf_and_bad_options(lib):
 
 
 def test_null_context_calls(lib):
+    assert lib.lfd_rl_load(None, None, None) == lfd.LFD_EINVAL
+    assert lib.lfd_rl_step(None, None, 1, None, None, None) == lfd.LFD_EINVAL
+    assert lib.lfd_rl_store(None, None, None) == lfd.LFD_EINVAL
     assert lib.lfd_forward(None, None, None, None) == lfd.LFD_EINVAL
     assert lib.lfd_backward(None, None, None, None) == lfd.LFD_EINVAL
     assert lib.lfd_rl_iterate(None, None, None, 1, 0, None, None, None, None, None) == lfd.LFD_EINVAL
@@ -206,3 +209,14 @@ def test_exact_runs_plan_rejects_bad_shapes(lib):
     assert lib.lfd_selftest_exact_runs(1, 4, 2, 5, 10) == lfd.LFD_EINVAL   # even Nnum
     assert lib.lfd_selftest_exact_runs(1, 5, 2, 4, 10) == lfd.LFD_EINVAL   # even k
     assert lib.lfd_selftest_exact_runs(1, 5, 0, 5, 10) == lfd.LFD_EINVAL
+
+
+@pytest.mark.parametrize("seed,n,grid", [(1, 190080, 152), (2, 1000, 152), (3, 152, 152), (4, 5, 1),
+                                         (5, 7000, 300)])
+def test_adjoint_balanced_ranges(lib, seed, n, grid):
+    assert lib.lfd_selftest_balanced_ranges(seed, n, grid) == lfd.LFD_OK
+
+
+def test_adjoint_balanced_ranges_rejects_bad_sizes(lib):
+    assert lib.lfd_selftest_balanced_ranges(1, 10, 11) == lfd.LFD_EINVAL
+    assert lib.lfd_selftest_balanced_ranges(1, 0, 1) == lfd.LFD_EINVAL
