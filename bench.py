@@ -309,8 +309,6 @@ NCU_TRAFFIC = {
     # the channels written (Cw = 1024 for the planes, C for the volume)
     ("lf_large_2025px_51z_psf345", "bf16x3", "forward volume transform"):
         (84.584e6 * 11475 / 900 + 213.216e6 * 11520 / 1024, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
-    ("lf_large_2025px_51z_psf345", "bf16x3", "backward volume transform"):
-        (244.476e6 * 11480 / 904 + 48.035e6 * 11475 / 900, "profiles/fft_lf_large_2025px_51z_psf345_bf16x3.md"),
 }
 
 

@@ -563,48 +563,51 @@ __global__ void __launch_bounds__(FftSize<F>::C2R_THREADS, FftSize<F>::C2R_MINB)
     // inputs: their sum in row fy and their difference times exp(2 pi i fy / F)
     // in row fy + F/2
     // All of a thread's loads are issued before the first is used (their
-    // latency is paid once per block, not once per item).
-    constexpr int GCH = Z::C2R_GCH;
+    // latency is paid once per block, not once per item). A sub-item is one
+    // 16-byte piece (two channels) of an item's two bins; the lanes of a warp
+    // take the pieces of 32 / PIECES items, lane L piece L / (32 / PIECES), so
+    // a warp's load touches as many 32-byte sectors as items (not lanes) and
+    // its 8-byte shared-memory stores split into half-warps without bank
+    // conflicts.
+    constexpr int GCH = Z::C2R_GCH, PIECES = GCH / 2, IPW = 32 / PIECES;
     static_assert(CH % GCH == 0 && 8 % GCH == 0, "whole channel groups per block");
-    constexpr int NITEM = HF * H2 * (CH / GCH), NIT = (NITEM + Z::C2R_THREADS - 1) / Z::C2R_THREADS;
+    constexpr int NITEM = HF * H2 * (CH / GCH), NSUB = NITEM * PIECES;
+    static_assert(NSUB % 32 == 0, "whole warps of sub-items");
+    constexpr int NIT = (NSUB + Z::C2R_THREADS - 1) / Z::C2R_THREADS;
     {
-        float4 w0[NIT][GCH / 2], w1[NIT][GCH / 2];
+        float4 w0[NIT], w1[NIT];
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
-            const int e = threadIdx.x + it * Z::C2R_THREADS;
+            const int sub = threadIdx.x + it * Z::C2R_THREADS;
+            const int e = (sub >> 5) * IPW + (sub & 31) % IPW, k = (sub & 31) / IPW;
             const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF), cg = c0 + GCH * g;
             const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
-#pragma unroll
-            for (int k = 0; k < GCH / 2; ++k) w0[it][k] = w1[it][k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e < NITEM && cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
+            w0[it] = w1[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sub < NSUB && cg < ldc) {  // ldc is a multiple of 8 (run_c2r checks)
                 const float2* base =
                     LAYOUT == 1   ? in + ((int64_t)(cg >> 3) * ntile + tile) * Z::BINS * 8 + (cg & 7)
                     : LAYOUT == 2 ? in + ((int64_t)(cg >> 3) * Z::BINS * ntile + tile) * 8 + (cg & 7)
                                   : in + (int64_t)tile * ldc + cg;
                 const int64_t bstride = LAYOUT == 1 ? 8 : LAYOUT == 2 ? (int64_t)ntile * 8
                                                                       : (int64_t)ntile * ldc;  // float2 between bins
-                const float4* q0 = reinterpret_cast<const float4*>(base + b0 * bstride);
-                const float4* q1 = reinterpret_cast<const float4*>(base + b1 * bstride);
-#pragma unroll
-                for (int k = 0; k < GCH / 2; ++k) {
-                    w0[it][k] = q0[k];
-                    w1[it][k] = q1[k];
-                }
+                w0[it] = reinterpret_cast<const float4*>(base + b0 * bstride)[k];
+                w1[it] = reinterpret_cast<const float4*>(base + b1 * bstride)[k];
             }
         }
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
-            const int e = threadIdx.x + it * Z::C2R_THREADS;
-            if (e >= NITEM) break;
+            const int sub = threadIdx.x + it * Z::C2R_THREADS;
+            const int e = (sub >> 5) * IPW + (sub & 31) % IPW, k = (sub & 31) / IPW;
+            if (sub >= NSUB) break;
             const int fx = e % H2, fy = (e / H2) % HF, g = e / (H2 * HF);
             const int b0 = fy * H2 + fx, b1 = b0 + HF * H2;
             const float2 w = c_tw[fy * (64 / F)];  // conjugated below
 #pragma unroll
-            for (int k = 0; k < GCH; ++k) {
-                const float4 a = w0[it][k >> 1], b = w1[it][k >> 1];
-                const float2 v0 = (k & 1) ? make_float2(a.z, a.w) : make_float2(a.x, a.y);
-                const float2 v1 = (k & 1) ? make_float2(b.z, b.w) : make_float2(b.x, b.y);
-                float2* dst = sm + (size_t)(GCH * g + k) * Z::BINS;
+            for (int j = 0; j < 2; ++j) {
+                const float4 a = w0[it], bb = w1[it];
+                const float2 v0 = j ? make_float2(a.z, a.w) : make_float2(a.x, a.y);
+                const float2 v1 = j ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
+                float2* dst = sm + (size_t)(GCH * g + 2 * k + j) * Z::BINS;
                 dst[b0] = cadd(v0, v1);
                 const float2 d = csub(v0, v1);
                 dst[b1] = make_float2(fmaf(d.x, w.x, d.y * w.y), fmaf(d.y, w.x, -d.x * w.y));
