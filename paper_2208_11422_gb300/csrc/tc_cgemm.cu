@@ -35,7 +35,14 @@
 // from shared memory) as one of N = 64, so the four data planes side by side
 // take a quarter of the instructions of one MMA per plane pair. The spectra
 // (all of Wf) are read once per projection while the columns fit one chunk:
-// the kernels are bound by HBM bandwidth.
+// the kernels are bound by HBM bandwidth. Single frames (up to 16 columns)
+// take two specialised kernels: the forward's wide units (k_tc_cgemm_wide,
+// two bins x both row tiles over a copy of the spectra in unit order) and the
+// adjoint with the ratio spectra resident in shared memory
+// (k_tc_cgemm_adjr, contiguous unit ranges of equal cost). The forward writes
+// its outputs group-major [S/8][ncol][bins][8]; the adjoints write theirs
+// [C/8][bins][ncol][8], so that a unit's 16 columns of a channel group are one
+// 1 KB run of whole lines.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
